@@ -1,0 +1,354 @@
+"""Benchmark of quantization-aware interpolation on GB300 (one JSON line).
+
+Workload: a 512^3 float32 Gaussian random field with P(k) ~ k^-11/3 (seeded
+FFT synthesis, normalised to [0, 1]), pre-quantized with eb = 1e-3 x range
+into int32 indices. One step = one qai_mitigate call over the whole field:
+boundary detection, both exact EDTs, sign propagation and the fused IDW
+compensation (Algorithm 4), inputs resident in HBM. The fields (512 MiB in,
+512 MiB out, 1.5 GiB of intermediates) are far larger than the 129 MB L2, so
+no flush is needed between steps.
+
+metric  mitigation GB/s of the fp32 field = 4 N bytes / step time, summed
+        over ranks (replicas only: each rank mitigates its own field)
+e2e     the same through qai_mitigate_host: pinned host q in, host D'' out,
+        both copies inside the timed region
+roofline  the dominant kernel's algorithmic bytes / its CUDA-event time vs the
+        measured HBM copy bandwidth
+cpu_baseline  the FP64 C oracle on the host cores, on a 128 x 512 x 512 slab
+
+``--impl reference`` times the oracle itself on that slab as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SHAPE = (512, 512, 512)
+REL_EB = 1e-3
+SEED = 2
+SAMPLE_Z = 128                      # oracle sample: the first 128 z-planes
+METRIC = "mitigation GB/s of fp32 field (detect+EDT+interp) vs HBM roofline; PSNR gain"
+WORKLOAD = "grf512_k-11/3_eb1e-3"
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
+
+
+def hbm_peak():
+    p = peaks().get("hbm_gbs")
+    return (float(p), "measured") if p else (6800.0, "fallback")
+
+
+def csrc_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2602_20097_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
+    None when the kernels changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except OSError:
+        return None
+    if rec.get("csrc_hash") != csrc_hash():
+        return None
+    k = rec.get("kernels", {}).get(kernel)
+    return None if k is None else k.get("dram_bytes_per_launch")
+
+
+class Clocks:
+    """nvidia-smi sampler (200 ms) running during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap,utilization.gpu")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        import statistics
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                util = float(r[6])
+                if util >= 50:
+                    sm.append(float(r[0]))
+                mx.append(float(r[1]))
+                for n, v in zip(names, r[2:6]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        if not mx:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(self.rows), "samples_under_load": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def make_field(device, seed, shape=SHAPE):
+    from paper_2602_20097_gb300 import synth
+    x = synth.grf(shape, slope=11.0 / 3.0, seed=seed, device=device)
+    eb = REL_EB * synth.value_range(x)
+    q = synth.quantize(x, eb)
+    return x, q, eb
+
+
+def psnr(x, y):
+    import torch
+    rng = float(x.max() - x.min())
+    mse = float(torch.mean((x.double() - y.double()) ** 2))
+    return 20.0 * __import__("math").log10(rng / mse ** 0.5)
+
+
+def time_oracle(q_sample, eb, min_s=10.0, max_s=30.0):
+    import oracle
+    oracle.build()
+    runs, t0 = 0, time.perf_counter()
+    while True:
+        oracle.mitigate(q_sample, eb, debug=False)
+        runs += 1
+        el = time.perf_counter() - t0
+        if el >= min_s or el * (runs + 1) / runs > max_s:
+            break
+    return runs, el
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle timed on the host cores."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    from paper_2602_20097_gb300 import synth
+    oracle.build()
+    x = synth.grf((SAMPLE_Z,) + SHAPE[1:], slope=11.0 / 3.0, seed=SEED).numpy()
+    eb = REL_EB * synth.value_range(x)
+    q = synth.quantize(x, eb)
+    for _ in range(args.warmup):
+        oracle.mitigate(q, eb, debug=False)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.mitigate(q, eb, debug=False)
+    el = time.perf_counter() - t0
+    gbs = q.size * 4 * args.steps / el / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "shape": list(SHAPE), "rel_eb": REL_EB,
+                   "sample": f"{SAMPLE_Z}x512x512 slab of the same synthesis"},
+        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": oracle.threads(), "kind": "oracle",
+                         "sample": f"{SAMPLE_Z}x512x512 GRF slab, {args.steps} runs"},
+        "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_e2e(q, eb, dev, stream, steps, barrier, world, ws):
+    """Same metric through qai_mitigate_host: H2D of q and D2H of D'' timed."""
+    import torch
+    import torch.distributed as dist
+    from paper_2602_20097_gb300 import qai
+    qh = q.cpu().pin_memory()
+    oh = torch.empty(tuple(q.shape), dtype=torch.float32).pin_memory()
+    del ws
+    wsh = qai.alloc_workspace(qai.workspace_size_host(tuple(q.shape)), dev)
+    for _ in range(2):
+        qai.mitigate_host(qh, eb, out_host=oh, workspace=wsh)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        qai.mitigate_host(qh, eb, out_host=oh, workspace=wsh)
+    e1.record(stream)
+    barrier()
+    t = torch.tensor([e0.elapsed_time(e1) / steps], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return q.numel() * 4 * world / (float(t.item()) * 1e-3) / 1e9
+
+
+def run_qai(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2602_20097_gb300 import qai
+
+    world, rank, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # replicas: each rank mitigates its own field (seed differs per rank)
+    shape = tuple(int(v) for v in args.shape.split(",")) if args.shape else SHAPE
+    x, q, eb = make_field(dev, SEED + rank, shape)
+    N = q.numel()
+    out = torch.empty_like(q, dtype=torch.float32)
+    ws = qai.alloc_workspace(qai.workspace_size(tuple(q.shape)), dev)
+    stream = torch.cuda.current_stream()
+    warm = max(3, args.warmup)
+    for _ in range(warm):
+        qai.mitigate(q, eb, out=out, workspace=ws)
+    qai.profile_read()
+    qai.profile_enable(True)
+    barrier()
+    n0 = qai.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            qai.mitigate(q, eb, out=out, workspace=ws)
+        ev1.record(stream)
+        barrier()
+    launches = qai.launch_count() - n0
+    kstats = qai.profile_read()
+    qai.profile_enable(False)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = N * 4 * world / (ms_max * 1e-3) / 1e9
+
+    # end to end from pinned host memory through the C ABI (copies timed)
+    if args.no_e2e:
+        e2e_value = None
+    else:
+        e2e_value = run_e2e(q, eb, dev, stream, args.steps, barrier, world, ws)
+        ws = None
+
+    # quality (untimed): PSNR gain and max error / eps of this field
+    psnr_q = psnr(x, q.double() * (2 * eb))
+    psnr_m = psnr(x, out)
+    max_err = float((x.double() - out.double()).abs().max()) / eb
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    peak, peak_src = hbm_peak()
+    dom = max(kstats.items(), key=lambda kv: kv[1][1]) if kstats else None
+    roof = None
+    if dom:
+        name, (nl, tot_ms, algo_bytes) = dom
+        achieved = algo_bytes / (tot_ms * 1e-3) / 1e9
+        traffic = ncu_traffic(name)
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": name,
+                "peak_source": f"{peak_src} hbm_gbs",
+                "algo_bytes_per_launch": algo_bytes / nl,
+                "kernel_ms_per_launch": tot_ms / nl}
+    kernels = {k: {"launches": v[0], "ms_per_launch": v[1] / v[0],
+                   "algo_gbs": v[2] / (v[1] * 1e-3) / 1e9,
+                   "share": v[1] / sum(s[1] for s in kstats.values())} for k, v in kstats.items()}
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        qs = q[:min(SAMPLE_Z, q.shape[0])].cpu().numpy()
+        import oracle
+        runs, el = time_oracle(qs, eb)
+        cpu = {"value": qs.size * 4 * runs / el / 1e9, "unit": "GB/s", "cores": oracle.threads(),
+               "kind": "oracle",
+               "sample": f"first {SAMPLE_Z} z-planes of the bench field ({SAMPLE_Z}x512x512), {runs} runs, {el:.1f} s"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": warm, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32+fp32", "data": "synthetic",
+        "config": {"workload": WORKLOAD if shape == SHAPE else f"grf{'x'.join(map(str, shape))}_k-11/3_eb1e-3",
+                   "shape": list(shape), "rel_eb": REL_EB, "eb": eb,
+                   "parallelism": f"replicas x{world}", "l2": "inputs > L2 (1 GiB per step), no flush"},
+        "roofline": roof,
+        "algo_roofline_frac": (8.0 * N / (ms_max * 1e-3) / 1e9) / peak,
+        "e2e": None if e2e_value is None else
+        {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": 4 * N},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+        "quality": {"psnr_dprime_db": psnr_q, "psnr_mitigated_db": psnr_m,
+                    "psnr_gain_db": psnr_m - psnr_q, "max_err_over_eps": max_err},
+        "kernels": kernels,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["qai", "reference"], default="qai")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--shape", default="", help="Z,Y,X override (profiling of smaller cases)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_qai(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,152 @@
+/*
+ * qai.h -- C ABI of libqai, GB300-native quantization-aware interpolation.
+ *
+ * The library implements the artifact-mitigation method of Jiao et al.,
+ * "Mitigating Artifacts in Pre-quantization Based Scientific Data Compressors
+ * with Quantization-aware Interpolation" (Sec. VI, Algorithm 4): given the
+ * int32 pre-quantization indices q of a field (Eq. 1, q = round(x / 2 eps))
+ * and the absolute error bound eps, it returns the compensated field
+ * D'' = D' + C with D' = 2 q eps, in fp32. All work runs in hand-written
+ * CUDA kernels for sm_103a; the host code only validates and launches.
+ *
+ * Conventions shared by every entry point:
+ *  - Fields are dense, C order (slowest axis first), rank 1..3. Extent-1 axes
+ *    are squeezed before the stencils (a 1 x ny x nx field is 2-D).
+ *  - Supported extents after squeezing: rank 1: n <= 32768; rank 2 and 3:
+ *    x (contiguous) <= 16383, y and z <= 4096; N = prod(dims) < 2^31.
+ *    Larger shapes return QAI_ERR_SHAPE.
+ *  - Pointers named d_* are device memory, h_* host memory; all of it is owned
+ *    by the caller and never freed by the library. Outputs must not alias
+ *    inputs or each other.
+ *  - Calls are asynchronous and stream-ordered on `stream` (0 = legacy
+ *    default stream). The returned status covers argument errors and launch
+ *    errors; faults inside kernels surface on a later synchronisation.
+ *  - On any error nothing is launched, and qai_last_error() returns a
+ *    one-line description (per host thread).
+ */
+#ifndef QAI_H
+#define QAI_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QAI_OK = 0,
+    QAI_ERR_INVALID_ARG = 1,  /* NULL pointer, bad eps/eta/p/rule, small workspace */
+    QAI_ERR_SHAPE = 2,        /* rank or extents outside the supported range       */
+    QAI_ERR_RANGE = 3,        /* reserved                                          */
+    QAI_ERR_CUDA = 4,         /* a CUDA runtime call or launch failed              */
+    QAI_ERR_OOM = 5,          /* internal workspace allocation failed              */
+    QAI_ERR_TIMEOUT = 6,      /* reserved for bounded device-side waits            */
+    QAI_ERR_INTERNAL = 7
+} qai_status;
+
+/* Method parameters. Defaults (qai_default_params) reproduce the paper. */
+typedef struct {
+    double eta;              /* compensation factor at boundaries, Sec. VI step E
+                                (paper: 0.9); finite, >= 0                         */
+    double idw_power;        /* exponent p of the inverse-distance weights:
+                                w = (1/k1^p) / (1/k1^p + 1/k2^p); paper: 1; > 0    */
+    int32_t grad_threshold;  /* Algorithm 2 fast-varying test on the central
+                                difference (q[+1]-q[-1])/2 >= 1, as the integer
+                                |q[+1]-q[-1]| >= grad_threshold; default 2, >= 1  */
+    int32_t sign_rule;       /* Algorithm 2 boundary sign: 0 = sgn of the sum of
+                                (q_nb - q) over the axis neighbours (default);
+                                1 = sgn(q_nb - q) of the first differing neighbour
+                                in the order z-, z+, y-, y+, x-, x+                */
+    int32_t b2_rule;         /* Algorithm 3 GetBoundary(S): 0 = a neighbour with
+                                the same q and a different S (default);
+                                1 = any neighbour with a different S               */
+    uint32_t flags;          /* reserved, must be 0                                */
+} qai_params;
+
+/* Optional per-step outputs of Algorithm 4 (debug and parity checking).
+ * Each pointer is a device array of N elements, or NULL to skip it.
+ * Distances are squared Euclidean distances in grid units; a point that no
+ * boundary reaches gets INT32_MAX. idx1 is the linear index of the nearest
+ * quantization boundary point, the smallest linear index among equally near
+ * ones, -1 if the field has no boundary; it needs the workspace sized with
+ * QAI_WS_INDEX. */
+typedef struct {
+    uint8_t* b1;     /* quantization boundary map B1 (Algorithm 2)          */
+    int8_t* sb;      /* boundary sign map S_B in {-1,0,1} (Algorithm 2)     */
+    int32_t* dist1;  /* Dist1, squared distance to B1 (step B)              */
+    int32_t* idx1;   /* I1, nearest boundary point (step B)                 */
+    int8_t* s;       /* propagated sign map S (Algorithm 3)                 */
+    uint8_t* b2;     /* sign-flipping boundary map B2 (Algorithm 3)         */
+    int32_t* dist2;  /* Dist2, squared distance to B2 (step D)              */
+} qai_debug_out;
+
+#define QAI_WS_INDEX 1u   /* workspace_size flag: room to carry idx1          */
+
+/* Fills *p with the paper's defaults: eta 0.9, p 1, threshold 2, rules 0. */
+void qai_default_params(qai_params* p);
+
+/* Bytes of device workspace qai_mitigate needs for this shape. flags: 0, or
+ * QAI_WS_INDEX when debug idx1 output is wanted. Returns QAI_ERR_SHAPE for an
+ * unsupported shape. */
+qai_status qai_workspace_size(int rank, const int64_t* dims, uint32_t flags, size_t* bytes);
+
+/* Algorithm 4 (Sec. VI, steps A-E) on a device-resident field.
+ *  d_q      int32[N] pre-quantization indices (Eq. 1), device
+ *  d_out    float[N] compensated field D'' = 2 q eps + C, device
+ *  rank, dims  rank 1..3 and its extents, slowest first (host array)
+ *  eb       absolute error bound eps > 0, finite
+ *  params   NULL for the defaults
+ *  d_ws, ws_bytes  device workspace of at least qai_workspace_size() bytes,
+ *           256-byte aligned; d_ws = NULL makes the call allocate and free it
+ *           stream-ordered (cudaMallocAsync / cudaFreeAsync)
+ *  stream   CUDA stream of every launch
+ *  dbg      NULL, or the per-step outputs wanted
+ * Error bound: |x - D''| <= (1 + eta) eps wherever |x - 2 q eps| <= eps. */
+qai_status qai_mitigate(const int32_t* d_q, float* d_out, int rank, const int64_t* dims,
+                        double eb, const qai_params* params, void* d_ws, size_t ws_bytes,
+                        cudaStream_t stream, const qai_debug_out* dbg);
+
+/* Bytes of device workspace qai_mitigate_host needs: the device copies of q
+ * and D'' plus qai_workspace_size(rank, dims, 0). */
+qai_status qai_workspace_size_host(int rank, const int64_t* dims, size_t* bytes);
+
+/* qai_mitigate end to end from host memory: copies h_q (int32[N], host) to the
+ * device, runs Algorithm 4, and copies D'' back into h_out (float[N], host),
+ * all on `stream`. Pinned host buffers make the copies asynchronous; the call
+ * returns before they finish, so synchronise `stream` before reading h_out.
+ * d_ws (>= qai_workspace_size_host bytes) is required. */
+qai_status qai_mitigate_host(const int32_t* h_q, float* h_out, int rank, const int64_t* dims,
+                             double eb, const qai_params* params, void* d_ws, size_t ws_bytes,
+                             cudaStream_t stream);
+
+/* Per-kernel timing. While enabled, every kernel the library launches is
+ * bracketed by CUDA events recorded on the launch stream. qai_profile_read
+ * waits for the recorded events, then reports, per kernel name, the launch
+ * count, the summed device time and the algorithmic bytes (the bytes the
+ * kernel must read and write: inputs and outputs, no halo re-reads), and
+ * resets the counters. Returns the number of kernel names (<= cap) filled. */
+typedef struct {
+    char name[48];
+    int64_t launches;
+    double total_ms;
+    double algo_bytes;   /* summed over the launches */
+} qai_kernel_stat;
+
+qai_status qai_profile_enable(int on);
+int qai_profile_read(qai_kernel_stat* out, int cap);
+
+/* Number of kernel launches made by the library since load (all entry points). */
+int64_t qai_launch_count(void);
+
+/* Human-readable name of a status code; a static string. */
+const char* qai_status_string(qai_status s);
+
+/* Detail of the last error on the calling host thread ("" if none). */
+const char* qai_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QAI_H */

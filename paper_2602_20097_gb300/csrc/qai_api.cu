@@ -1,0 +1,435 @@
+// qai_api.cu -- the C ABI of libqai (see include/qai.h): argument checks,
+// workspace layout and the stream-ordered launch sequence of Algorithm 4.
+#include <atomic>
+#include <cstdarg>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/qai.h"
+#include "qai_device.cuh"
+#include "qai_launch.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+qai_status fail(qai_status s, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+qai_status fail(qai_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+std::atomic<int64_t> g_launches{0};
+
+// ---- per-kernel timing ------------------------------------------------------
+struct Pending {
+    const char* name;
+    double bytes;
+    cudaEvent_t a, b;
+};
+struct Stat {
+    std::string name;
+    int64_t launches = 0;
+    double ms = 0, bytes = 0;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<Pending> g_pending;
+std::vector<Stat> g_stats;
+std::vector<cudaEvent_t> g_event_pool;
+
+cudaEvent_t take_event()
+{
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Launch one kernel through `fn`, counting it and, when profiling, timing it.
+template <class F>
+cudaError_t timed(const char* name, double algo_bytes, cudaStream_t st, F&& fn)
+{
+    cudaEvent_t a = nullptr, b = nullptr;
+    bool prof;
+    {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        prof = g_prof_on;
+        if (prof) {
+            a = take_event();
+            b = take_event();
+        }
+    }
+    if (prof && a && b) cudaEventRecord(a, st);
+    cudaError_t e = fn();
+    g_launches.fetch_add(1);
+    if (prof && a && b) {
+        cudaEventRecord(b, st);
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        g_pending.push_back({name, algo_bytes, a, b});
+    }
+    return e;
+}
+
+// ---- shapes -----------------------------------------------------------------
+struct Shape {
+    int rank;       // after squeezing extent-1 axes
+    int nz, ny, nx;
+    int64_t N;
+};
+
+constexpr int kMaxX = 16383, kMaxYZ = 4096, kMax1D = 32768;
+
+qai_status make_shape(int rank, const int64_t* dims, Shape* s)
+{
+    if (!dims) return fail(QAI_ERR_INVALID_ARG, "dims is NULL");
+    if (rank < 1 || rank > 3) return fail(QAI_ERR_SHAPE, "rank %d outside 1..3", rank);
+    int64_t kept[3];
+    int r = 0;
+    int64_t N = 1;
+    for (int a = 0; a < rank; ++a) {
+        if (dims[a] < 1) return fail(QAI_ERR_SHAPE, "dims[%d] = %lld < 1", a, (long long)dims[a]);
+        if (dims[a] > (1LL << 31)) return fail(QAI_ERR_SHAPE, "dims[%d] too large", a);
+        N *= dims[a];
+        if (N >= (1LL << 31)) return fail(QAI_ERR_SHAPE, "N >= 2^31 points");
+        if (dims[a] > 1) kept[r++] = dims[a];
+    }
+    if (r == 0) { kept[0] = 1; r = 1; }
+    s->rank = r;
+    s->N = N;
+    s->nz = r == 3 ? (int)kept[0] : 1;
+    s->ny = r >= 2 ? (int)kept[r - 2] : 1;
+    s->nx = (int)kept[r - 1];
+    if (r == 1 && s->nx > kMax1D)
+        return fail(QAI_ERR_SHAPE, "rank-1 length %d > %d", s->nx, kMax1D);
+    if (r >= 2 && s->nx > kMaxX)
+        return fail(QAI_ERR_SHAPE, "x extent %d > %d", s->nx, kMaxX);
+    if (r >= 2 && (s->ny > kMaxYZ || s->nz > kMaxYZ))
+        return fail(QAI_ERR_SHAPE, "y or z extent > %d", kMaxYZ);
+    return QAI_OK;
+}
+
+// ---- workspace layout -----------------------------------------------------------
+struct Layout {
+    size_t eqm, xw, yw, dist1, s, idx, total;
+};
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+Layout layout_for(const Shape& s, uint32_t flags)
+{
+    Layout l{};
+    const size_t N = (size_t)s.N;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
+    l.eqm = take(N);
+    l.dist1 = take(N * 4);
+    l.s = take(N);
+    l.xw = s.rank >= 2 ? take(N * 2) : 0;
+    l.yw = s.rank >= 3 ? take(N * 4) : 0;
+    l.idx = (flags & QAI_WS_INDEX) && s.rank >= 2 ? take(N * 4) : 0;
+    l.total = off;
+    return l;
+}
+
+qai_status check_params(const qai_params* p)
+{
+    if (!std::isfinite(p->eta) || p->eta < 0) return fail(QAI_ERR_INVALID_ARG, "eta must be finite and >= 0");
+    if (!std::isfinite(p->idw_power) || p->idw_power <= 0)
+        return fail(QAI_ERR_INVALID_ARG, "idw_power must be finite and > 0");
+    if (p->grad_threshold < 1) return fail(QAI_ERR_INVALID_ARG, "grad_threshold must be >= 1");
+    if (p->sign_rule != 0 && p->sign_rule != 1) return fail(QAI_ERR_INVALID_ARG, "sign_rule must be 0 or 1");
+    if (p->b2_rule != 0 && p->b2_rule != 1) return fail(QAI_ERR_INVALID_ARG, "b2_rule must be 0 or 1");
+    if (p->flags != 0) return fail(QAI_ERR_INVALID_ARG, "flags must be 0");
+    return QAI_OK;
+}
+
+qai::MethodArgs method_args(const qai_params* p, double eb)
+{
+    qai::MethodArgs m;
+    m.two_eb = (float)(2.0 * eb);
+    m.eta_eb = (float)(p->eta * eb);
+    m.idw_power = (float)p->idw_power;
+    m.idw_is_one = p->idw_power == 1.0;
+    m.grad_threshold = p->grad_threshold;
+    m.sign_rule = p->sign_rule;
+    m.b2_rule = p->b2_rule;
+    return m;
+}
+
+qai_status cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(QAI_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// The launch sequence of Algorithm 4 on a validated shape.
+qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const qai::MethodArgs& m,
+                        char* ws, const Layout& lay, cudaStream_t st, const qai_debug_out* dbg)
+{
+    const double N = (double)sh.N;
+    uint8_t* eqm = reinterpret_cast<uint8_t*>(ws + lay.eqm);
+    int32_t* dist1 = reinterpret_cast<int32_t*>(ws + lay.dist1);
+    int8_t* s = reinterpret_cast<int8_t*>(ws + lay.s);
+    uint16_t* xw = sh.rank >= 2 ? reinterpret_cast<uint16_t*>(ws + lay.xw) : nullptr;
+    uint32_t* yw = sh.rank >= 3 ? reinterpret_cast<uint32_t*>(ws + lay.yw) : nullptr;
+    int32_t* idx_tmp = lay.idx ? reinterpret_cast<int32_t*>(ws + lay.idx) : nullptr;
+    qai_debug_out none{};
+    const qai_debug_out& d = dbg ? *dbg : none;
+    cudaError_t e;
+
+    // Step A + EDT-x of B1 (rank 1: the whole first EDT).
+    qai::RowArgs r1{};
+    r1.rank = sh.rank; r1.nz = sh.nz; r1.ny = sh.ny; r1.nx = sh.nx;
+    r1.q = d_q; r1.eqm = eqm; r1.m = m;
+    r1.dbg_b1 = d.b1; r1.dbg_sb = d.sb;
+    const bool final1 = sh.rank == 1;
+    if (final1) { r1.dist1 = dist1; r1.s_out = s; r1.dbg_idx = d.idx1; }
+    else { r1.xw = xw; r1.dbg_idx = d.idx1 ? (sh.rank == 3 ? d.idx1 : idx_tmp) : nullptr; }
+    e = timed(final1 ? "rowpass1_final" : "rowpass1", N * (final1 ? 10.0 : 7.0), st,
+              [&] { return qai::launch_rowpass(1, final1, r1, st); });
+    if (e != cudaSuccess) return cuda_fail(e, "row pass 1");
+
+    // EDT1 along y (and z): Dist1 and the propagated sign S.
+    auto colpass = [&](int phase, int in_bytes, bool fin, qai::ColArgs& c, const char* name,
+                       double bytes_per_pt) -> qai_status {
+        qai::ColConfig cfg;
+        if (!qai::choose_colpass(c.L, in_bytes, &cfg))
+            return fail(QAI_ERR_SHAPE, "line length %d does not fit shared memory", c.L);
+        cudaError_t err = timed(name, N * bytes_per_pt, st,
+                                [&] { return qai::launch_colpass(phase, in_bytes, fin, c, cfg, st); });
+        if (err != cudaSuccess) return cuda_fail(err, name);
+        return QAI_OK;
+    };
+    auto y_args = [&](const void* in) {
+        qai::ColArgs c{};
+        c.in = in; c.L = sh.ny; c.C = sh.nx; c.P = sh.nz;
+        c.row_stride = sh.nx; c.plane_stride = (int64_t)sh.ny * sh.nx; c.m = m;
+        return c;
+    };
+    auto z_args = [&](const void* in) {
+        qai::ColArgs c{};
+        c.in = in; c.L = sh.nz; c.C = sh.ny * sh.nx; c.P = 1;
+        c.row_stride = (int64_t)sh.ny * sh.nx; c.plane_stride = 0; c.m = m;
+        return c;
+    };
+    qai_status st_;
+    if (sh.rank == 2) {
+        qai::ColArgs c = y_args(xw);
+        c.dist1 = dist1; c.s_out = s;
+        if (d.idx1) { c.dbg_idx_in = idx_tmp; c.dbg_idx_out = d.idx1; }
+        if ((st_ = colpass(1, 2, true, c, "colpass1_y_final", 2 + 4 + 1)) != QAI_OK) return st_;
+    } else if (sh.rank == 3) {
+        qai::ColArgs c = y_args(xw);
+        c.out_w = yw;
+        if (d.idx1) { c.dbg_idx_in = d.idx1; c.dbg_idx_out = idx_tmp; }
+        if ((st_ = colpass(1, 2, false, c, "colpass1_y", 2 + 4)) != QAI_OK) return st_;
+        qai::ColArgs cz = z_args(yw);
+        cz.dist1 = dist1; cz.s_out = s;
+        if (d.idx1) { cz.dbg_idx_in = idx_tmp; cz.dbg_idx_out = d.idx1; }
+        if ((st_ = colpass(1, 4, true, cz, "colpass1_z_final", 4 + 4 + 1)) != QAI_OK) return st_;
+    }
+    if (d.dist1 && (e = cudaMemcpyAsync(d.dist1, dist1, (size_t)sh.N * 4, cudaMemcpyDeviceToDevice, st)))
+        return cuda_fail(e, "copy dist1");
+    if (d.s && (e = cudaMemcpyAsync(d.s, s, (size_t)sh.N, cudaMemcpyDeviceToDevice, st)))
+        return cuda_fail(e, "copy s");
+
+    // B2 = GetBoundary(S) + EDT-x of B2 (rank 1: also step E).
+    qai::RowArgs r2{};
+    r2.rank = sh.rank; r2.nz = sh.nz; r2.ny = sh.ny; r2.nx = sh.nx;
+    r2.q = d_q; r2.eqm = eqm; r2.s_in = s; r2.m = m;
+    r2.dbg_b2 = d.b2;
+    if (final1) { r2.dist1_in = dist1; r2.out = d_out; r2.dbg_dist2 = d.dist2; }
+    else r2.xw = xw;
+    e = timed(final1 ? "rowpass2_final" : "rowpass2", N * (final1 ? 14.0 : 4.0), st,
+              [&] { return qai::launch_rowpass(2, final1, r2, st); });
+    if (e != cudaSuccess) return cuda_fail(e, "row pass 2");
+
+    // EDT2 along y (and z), the last pass fused with step E.
+    auto fuse_e = [&](qai::ColArgs& c) {
+        c.out = d_out; c.q = d_q; c.dist1_in = dist1; c.s_in = s; c.dbg_dist2 = d.dist2;
+    };
+    if (sh.rank == 2) {
+        qai::ColArgs c = y_args(xw);
+        fuse_e(c);
+        if ((st_ = colpass(2, 2, true, c, "colpass2_y_final", 2 + 4 + 1 + 4 + 4)) != QAI_OK) return st_;
+    } else if (sh.rank == 3) {
+        qai::ColArgs c = y_args(xw);
+        c.out_w = yw;
+        if ((st_ = colpass(2, 2, false, c, "colpass2_y", 2 + 4)) != QAI_OK) return st_;
+        qai::ColArgs cz = z_args(yw);
+        fuse_e(cz);
+        if ((st_ = colpass(2, 4, true, cz, "colpass2_z_final", 4 + 4 + 1 + 4 + 4)) != QAI_OK) return st_;
+    }
+    return QAI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void qai_default_params(qai_params* p)
+{
+    if (!p) return;
+    p->eta = 0.9;
+    p->idw_power = 1.0;
+    p->grad_threshold = 2;
+    p->sign_rule = 0;
+    p->b2_rule = 0;
+    p->flags = 0;
+}
+
+qai_status qai_workspace_size(int rank, const int64_t* dims, uint32_t flags, size_t* bytes)
+{
+    if (!bytes) return fail(QAI_ERR_INVALID_ARG, "bytes is NULL");
+    Shape sh;
+    qai_status s = make_shape(rank, dims, &sh);
+    if (s != QAI_OK) return s;
+    *bytes = layout_for(sh, flags).total;
+    return QAI_OK;
+}
+
+qai_status qai_mitigate(const int32_t* d_q, float* d_out, int rank, const int64_t* dims, double eb,
+                        const qai_params* params, void* d_ws, size_t ws_bytes, cudaStream_t stream,
+                        const qai_debug_out* dbg)
+{
+    g_last_error.clear();
+    if (!d_q || !d_out) return fail(QAI_ERR_INVALID_ARG, "d_q and d_out must be non-NULL");
+    if (!(eb > 0.0) || !std::isfinite(eb)) return fail(QAI_ERR_INVALID_ARG, "eb must be finite and > 0");
+    qai_params defaults;
+    qai_default_params(&defaults);
+    const qai_params* p = params ? params : &defaults;
+    qai_status s = check_params(p);
+    if (s != QAI_OK) return s;
+    Shape sh;
+    if ((s = make_shape(rank, dims, &sh)) != QAI_OK) return s;
+    const uint32_t wflags = (dbg && dbg->idx1) ? QAI_WS_INDEX : 0u;
+    const Layout lay = layout_for(sh, wflags);
+    bool owned = false;
+    if (d_ws) {
+        if (ws_bytes < lay.total)
+            return fail(QAI_ERR_INVALID_ARG, "workspace %zu bytes < %zu needed", ws_bytes, lay.total);
+        if (reinterpret_cast<uintptr_t>(d_ws) & 255)
+            return fail(QAI_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    } else {
+        cudaError_t e = cudaMallocAsync(&d_ws, lay.total, stream);
+        if (e != cudaSuccess) return fail(QAI_ERR_OOM, "cudaMallocAsync(%zu): %s", lay.total, cudaGetErrorString(e));
+        owned = true;
+    }
+    s = run_pipeline(d_q, d_out, sh, method_args(p, eb), static_cast<char*>(d_ws), lay, stream, dbg);
+    if (owned) cudaFreeAsync(d_ws, stream);
+    return s;
+}
+
+qai_status qai_workspace_size_host(int rank, const int64_t* dims, size_t* bytes)
+{
+    if (!bytes) return fail(QAI_ERR_INVALID_ARG, "bytes is NULL");
+    Shape sh;
+    qai_status s = make_shape(rank, dims, &sh);
+    if (s != QAI_OK) return s;
+    *bytes = align256((size_t)sh.N * 4) * 2 + layout_for(sh, 0).total;
+    return QAI_OK;
+}
+
+qai_status qai_mitigate_host(const int32_t* h_q, float* h_out, int rank, const int64_t* dims, double eb,
+                             const qai_params* params, void* d_ws, size_t ws_bytes, cudaStream_t stream)
+{
+    g_last_error.clear();
+    if (!h_q || !h_out || !d_ws) return fail(QAI_ERR_INVALID_ARG, "h_q, h_out and d_ws must be non-NULL");
+    Shape sh;
+    qai_status s = make_shape(rank, dims, &sh);
+    if (s != QAI_OK) return s;
+    const size_t fb = align256((size_t)sh.N * 4);
+    size_t need;
+    qai_workspace_size_host(rank, dims, &need);
+    if (ws_bytes < need) return fail(QAI_ERR_INVALID_ARG, "workspace %zu bytes < %zu needed", ws_bytes, need);
+    if (reinterpret_cast<uintptr_t>(d_ws) & 255)
+        return fail(QAI_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    char* base = static_cast<char*>(d_ws);
+    int32_t* d_q = reinterpret_cast<int32_t*>(base);
+    float* d_out = reinterpret_cast<float*>(base + fb);
+    cudaError_t e = cudaMemcpyAsync(d_q, h_q, (size_t)sh.N * 4, cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "copy q to device");
+    s = qai_mitigate(d_q, d_out, rank, dims, eb, params, base + 2 * fb, ws_bytes - 2 * fb, stream, nullptr);
+    if (s != QAI_OK) return s;
+    e = cudaMemcpyAsync(h_out, d_out, (size_t)sh.N * 4, cudaMemcpyDeviceToHost, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "copy D'' to host");
+    return QAI_OK;
+}
+
+qai_status qai_profile_enable(int on)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_on = on != 0;
+    return QAI_OK;
+}
+
+int qai_profile_read(qai_kernel_stat* out, int cap)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (const Pending& p : g_pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            Stat* st = nullptr;
+            for (Stat& s : g_stats)
+                if (s.name == p.name) st = &s;
+            if (!st) {
+                g_stats.push_back(Stat{});
+                st = &g_stats.back();
+                st->name = p.name;
+            }
+            st->launches += 1;
+            st->ms += ms;
+            st->bytes += p.bytes;
+        }
+        g_event_pool.push_back(p.a);
+        g_event_pool.push_back(p.b);
+    }
+    g_pending.clear();
+    int n = 0;
+    for (const Stat& s : g_stats) {
+        if (n >= cap || !out) break;
+        std::memset(&out[n], 0, sizeof(qai_kernel_stat));
+        std::strncpy(out[n].name, s.name.c_str(), sizeof(out[n].name) - 1);
+        out[n].launches = s.launches;
+        out[n].total_ms = s.ms;
+        out[n].algo_bytes = s.bytes;
+        ++n;
+    }
+    g_stats.clear();
+    return n;
+}
+
+int64_t qai_launch_count(void) { return g_launches.load(); }
+
+const char* qai_status_string(qai_status s)
+{
+    switch (s) {
+        case QAI_OK: return "QAI_OK";
+        case QAI_ERR_INVALID_ARG: return "QAI_ERR_INVALID_ARG";
+        case QAI_ERR_SHAPE: return "QAI_ERR_SHAPE";
+        case QAI_ERR_RANGE: return "QAI_ERR_RANGE";
+        case QAI_ERR_CUDA: return "QAI_ERR_CUDA";
+        case QAI_ERR_OOM: return "QAI_ERR_OOM";
+        case QAI_ERR_TIMEOUT: return "QAI_ERR_TIMEOUT";
+        case QAI_ERR_INTERNAL: return "QAI_ERR_INTERNAL";
+    }
+    return "QAI_ERR_UNKNOWN";
+}
+
+const char* qai_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,27 @@
+// qai_launch.h -- host-side launchers of the qai kernels (internal).
+#pragma once
+#include <cstddef>
+#include <cuda_runtime.h>
+
+#include "qai_device.cuh"
+
+namespace qai {
+
+// Row pass (qai_rowpass.cu): phase 1 = step A + EDT-x of B1,
+// phase 2 = GetBoundary(S) + EDT-x of B2; final = the field is rank 1.
+int rowpass_warps(int nx);
+size_t rowpass_smem(int nx, int warps);
+cudaError_t launch_rowpass(int phase, bool final_pass, const RowArgs& a, cudaStream_t st);
+
+// Column pass (qai_colpass.cu): EDT along y or z. in_bytes = 2 for an xword
+// input (the pass right after a row pass), 4 for a yword input.
+struct ColConfig {
+    int W;        // columns per CTA (power of two)
+    int B;        // bands per column
+    size_t smem;  // dynamic shared memory bytes
+};
+bool choose_colpass(int L, int in_bytes, ColConfig* cfg);
+cudaError_t launch_colpass(int phase, int in_bytes, bool final_pass, ColArgs& a,
+                           const ColConfig& cfg, cudaStream_t st);
+
+}  // namespace qai

@@ -1,0 +1,216 @@
+"""Python binding of ``libqai.so`` (ctypes; argument marshalling only).
+
+Every step of the method runs in the library's CUDA kernels; this module only
+passes device pointers, sizes and the current CUDA stream. PyTorch provides the
+device memory and the stream. There is no CPU fallback: if the library cannot
+be loaded, :func:`load` raises :class:`QAIError`.
+
+Names follow the C ABI in ``include/qai.h``:
+
+* :func:`mitigate` -- Algorithm 4 on a CUDA int32 tensor, returns D'' (float32);
+  ``debug=True`` also returns the per-step maps B1, S_B, Dist1, I1, S, B2, Dist2.
+* :func:`mitigate_host` -- the same from/to host (pinned) tensors, with the
+  copies made by the library on the stream.
+* :func:`workspace_size`, :func:`profile_enable`, :func:`profile_read`,
+  :func:`launch_count`.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+P = ctypes.c_void_p
+_lock = threading.Lock()
+_lib = None
+
+SIGN_SUM, SIGN_FIRST = 0, 1
+B2_SAME_Q, B2_LITERAL = 0, 1
+WS_INDEX = 1
+INF32 = 2 ** 31 - 1
+
+
+class QAIError(RuntimeError):
+    pass
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("eta", ctypes.c_double), ("idw_power", ctypes.c_double),
+                ("grad_threshold", ctypes.c_int32), ("sign_rule", ctypes.c_int32),
+                ("b2_rule", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+
+class DebugOut(ctypes.Structure):
+    _fields_ = [("b1", P), ("sb", P), ("dist1", P), ("idx1", P), ("s", P), ("b2", P), ("dist2", P)]
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64),
+                ("total_ms", ctypes.c_double), ("algo_bytes", ctypes.c_double)]
+
+
+# name -> (restype, argtypes) of every symbol include/qai.h declares
+SIGNATURES = {
+    "qai_default_params": (None, [ctypes.POINTER(Params)]),
+    "qai_workspace_size": (ctypes.c_int, [ctypes.c_int, P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_size_t)]),
+    "qai_mitigate": (ctypes.c_int, [P, P, ctypes.c_int, P, ctypes.c_double, ctypes.POINTER(Params),
+                                    P, ctypes.c_size_t, P, ctypes.POINTER(DebugOut)]),
+    "qai_workspace_size_host": (ctypes.c_int, [ctypes.c_int, P, ctypes.POINTER(ctypes.c_size_t)]),
+    "qai_mitigate_host": (ctypes.c_int, [P, P, ctypes.c_int, P, ctypes.c_double, ctypes.POINTER(Params),
+                                         P, ctypes.c_size_t, P]),
+    "qai_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+    "qai_profile_read": (ctypes.c_int, [ctypes.POINTER(KernelStat), ctypes.c_int]),
+    "qai_launch_count": (ctypes.c_int64, []),
+    "qai_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "qai_last_error": (ctypes.c_char_p, []),
+}
+
+
+def load(build_if_missing: bool = True):
+    """Load ``libqai.so`` (building it with nvcc first if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing and _build.stale():
+            try:
+                _build.build()
+            except Exception as e:  # noqa: BLE001 - re-raised with context
+                raise QAIError(f"libqai.so could not be built: {e}") from e
+        if not os.path.exists(path):
+            raise QAIError(f"libqai.so not found at {path}; run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _check(rc):
+    if rc != 0:
+        lib = load()
+        raise QAIError(f"{lib.qai_status_string(rc).decode()}: {lib.qai_last_error().decode()}")
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    load().qai_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if v is not None:
+            setattr(p, k, v)
+    return p
+
+
+def _dims(shape):
+    arr = (ctypes.c_int64 * len(shape))(*[int(s) for s in shape])
+    return arr
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def workspace_size(shape, with_index: bool = False) -> int:
+    n = ctypes.c_size_t()
+    _check(load().qai_workspace_size(len(shape), _dims(shape), WS_INDEX if with_index else 0,
+                                     ctypes.byref(n)))
+    return int(n.value)
+
+
+def workspace_size_host(shape) -> int:
+    n = ctypes.c_size_t()
+    _check(load().qai_workspace_size_host(len(shape), _dims(shape), ctypes.byref(n)))
+    return int(n.value)
+
+
+def alloc_workspace(nbytes: int, device=None) -> torch.Tensor:
+    """A device byte buffer of ``nbytes`` (the caching allocator aligns to 512 B)."""
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device or "cuda")
+
+
+def _params(eta, idw_power, grad_threshold, sign_rule, b2_rule):
+    return default_params(eta=eta, idw_power=idw_power, grad_threshold=grad_threshold,
+                          sign_rule=sign_rule, b2_rule=b2_rule)
+
+
+def mitigate(q: torch.Tensor, eb: float, eta: float = 0.9, idw_power: float = 1.0,
+             grad_threshold: int = 2, sign_rule: int = SIGN_SUM, b2_rule: int = B2_SAME_Q,
+             out: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+             debug: bool = False, stream=None):
+    """Algorithm 4 on a contiguous CUDA int32 tensor ``q`` (rank 1-3).
+
+    Returns D'' as a float32 tensor of ``q``'s shape, or ``(D'', maps)`` when
+    ``debug`` with ``maps`` = dict of the per-step outputs (device tensors).
+    """
+    lib = load()
+    if not (q.is_cuda and q.dtype == torch.int32 and q.is_contiguous()):
+        raise QAIError("q must be a contiguous CUDA int32 tensor")
+    shape = tuple(q.shape)
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float32, device=q.device)
+    dbg = None
+    maps = None
+    if debug:
+        maps = {k: torch.empty(shape, dtype=t, device=q.device) for k, t in
+                (("b1", torch.uint8), ("sb", torch.int8), ("dist1", torch.int32),
+                 ("idx1", torch.int32), ("s", torch.int8), ("b2", torch.uint8),
+                 ("dist2", torch.int32))}
+        dbg = DebugOut(**{k: v.data_ptr() for k, v in maps.items()})
+    if workspace is None:
+        workspace = alloc_workspace(workspace_size(shape, with_index=debug), q.device)
+    p = _params(eta, idw_power, grad_threshold, sign_rule, b2_rule)
+    rc = lib.qai_mitigate(q.data_ptr(), out.data_ptr(), len(shape), _dims(shape), float(eb),
+                          ctypes.byref(p), workspace.data_ptr(), workspace.numel(), _stream(stream),
+                          ctypes.byref(dbg) if dbg is not None else None)
+    _check(rc)
+    return (out, maps) if debug else out
+
+
+def mitigate_host(q_host: torch.Tensor, eb: float, out_host: torch.Tensor | None = None,
+                  workspace: torch.Tensor | None = None, stream=None, **kw):
+    """Algorithm 4 from host memory: the library copies q in and D'' out on
+    the stream. Pinned tensors keep the copies asynchronous; synchronise the
+    stream before reading the result."""
+    lib = load()
+    if q_host.is_cuda or q_host.dtype != torch.int32 or not q_host.is_contiguous():
+        raise QAIError("q_host must be a contiguous host int32 tensor")
+    shape = tuple(q_host.shape)
+    if out_host is None:
+        out_host = torch.empty(shape, dtype=torch.float32, pin_memory=q_host.is_pinned())
+    if workspace is None:
+        workspace = alloc_workspace(workspace_size_host(shape))
+    p = _params(kw.get("eta", 0.9), kw.get("idw_power", 1.0), kw.get("grad_threshold", 2),
+                kw.get("sign_rule", SIGN_SUM), kw.get("b2_rule", B2_SAME_Q))
+    rc = lib.qai_mitigate_host(q_host.data_ptr(), out_host.data_ptr(), len(shape), _dims(shape),
+                               float(eb), ctypes.byref(p), workspace.data_ptr(), workspace.numel(),
+                               _stream(stream))
+    _check(rc)
+    return out_host
+
+
+def profile_enable(on: bool = True):
+    _check(load().qai_profile_enable(1 if on else 0))
+
+
+def profile_read():
+    """Per-kernel {name: (launches, total_ms, algo_bytes)} since the last read."""
+    buf = (KernelStat * 64)()
+    n = load().qai_profile_read(buf, 64)
+    return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms, buf[i].algo_bytes)
+            for i in range(n)}
+
+
+def launch_count() -> int:
+    return int(load().qai_launch_count())

@@ -1,0 +1,98 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol that
+include/qai.h declares; host-side argument checks return status codes without
+launching anything (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2602_20097_gb300 import build, qai
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "qai.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(qai_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return qai.load()
+
+
+def test_library_builds_in_tree():
+    path = build.build()
+    assert os.path.exists(path) and path.startswith(os.path.join(ROOT, "paper_2602_20097_gb300"))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert "qai_mitigate" in names and len(names) >= 8
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(qai.SIGNATURES), "binding and header disagree"
+
+
+def test_default_params(lib):
+    p = qai.default_params()
+    assert (p.eta, p.idw_power, p.grad_threshold, p.sign_rule, p.b2_rule, p.flags) == (0.9, 1.0, 2, 0, 0, 0)
+
+
+def _ws(shape, flags=0):
+    n = ctypes.c_size_t()
+    rc = qai.load().qai_workspace_size(len(shape), qai._dims(shape), flags, ctypes.byref(n))
+    return rc, n.value
+
+
+def test_workspace_sizes():
+    rc, n3 = _ws((512, 512, 512))
+    assert rc == 0 and n3 >= 512 ** 3 * 12
+    rc, n3i = _ws((512, 512, 512), qai.WS_INDEX)
+    assert rc == 0 and n3i >= n3 + 512 ** 3 * 4
+    rc, n2 = _ws((1800, 3600))
+    assert rc == 0 and n2 >= 1800 * 3600 * 8
+    # squeezing: a 1 x ny x nx field needs the 2-D workspace
+    assert _ws((1, 1800, 3600))[1] == n2
+
+
+@pytest.mark.parametrize("shape,code", [((0, 4, 4), 2), ((4, 4, 20000), 2), ((5000, 4, 4), 2),
+                                        ((40000,), 2), ((2048, 2048, 1024), 2), ((3,) * 4, 2)])
+def test_unsupported_shapes(shape, code):
+    rc, _ = _ws(shape)
+    assert rc == code
+
+
+def _call(q=1, out=1, shape=(8, 8, 8), eb=0.1, params=None, ws=None, wsb=0):
+    lib = qai.load()
+    return lib.qai_mitigate(ctypes.c_void_p(q) if q else None, ctypes.c_void_p(out) if out else None,
+                            len(shape), qai._dims(shape), eb,
+                            ctypes.byref(params) if params is not None else None,
+                            ctypes.c_void_p(ws) if ws else None, wsb, None, None)
+
+
+def test_argument_errors_return_status():
+    lib = qai.load()
+    assert _call(q=0) == 1
+    assert _call(out=0) == 1
+    for bad in (0.0, -1.0, float("nan"), float("inf")):
+        assert _call(eb=bad) == 1
+    for field, val in (("eta", float("nan")), ("eta", -1.0), ("idw_power", 0.0),
+                       ("grad_threshold", 0), ("sign_rule", 2), ("b2_rule", -1), ("flags", 1)):
+        p = qai.default_params()
+        setattr(p, field, val)
+        assert _call(params=p) == 1, field
+    assert _call(shape=(8, 0, 8)) == 2
+    # a workspace that is too small or misaligned is rejected before any launch
+    assert _call(ws=256, wsb=16) == 1
+    assert _call(ws=257, wsb=1 << 30) == 1
+    assert lib.qai_status_string(1) == b"QAI_ERR_INVALID_ARG"
+    assert b"workspace" in lib.qai_last_error()
+
+
+def test_profile_counters_start_empty():
+    assert qai.profile_read() == {}
+    assert qai.launch_count() >= 0
