@@ -75,10 +75,11 @@ def ncu_traffic(kernel):
 
 
 class Clocks:
-    """nvidia-smi sampler (200 ms) running during the timed region."""
+    """nvidia-smi sampler (50 ms period) of SM clock and throttle reasons."""
     Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-         "clocks_event_reasons.sw_power_cap,utilization.gpu")
+         "clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
     def __init__(self, index):
         self.index = index
@@ -89,7 +90,7 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -99,7 +100,7 @@ class Clocks:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.rows.append([c.strip() for c in line.split(",")])
+            self.rows.append((time.perf_counter(), [c.strip() for c in line.split(",")]))
 
     def __exit__(self, *a):
         if self.proc:
@@ -109,25 +110,25 @@ class Clocks:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
 
-    def summary(self):
+    def summary(self, t0, t1):
+        """Median SM clock and the throttle reasons seen between t0 and t1."""
         import statistics
         sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in self.rows:
+        for t, r in self.rows:
+            if not t0 <= t <= t1:
+                continue
             try:
-                util = float(r[6])
-                if util >= 50:
-                    sm.append(float(r[0]))
+                sm.append(float(r[0]))
                 mx.append(float(r[1]))
-                for n, v in zip(names, r[2:6]):
-                    if v.lower().startswith("active"):
-                        reasons.add(n)
             except (ValueError, IndexError):
                 continue
-        if not mx:
+            for n, v in zip(self.NAMES, r[2:6]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx),
-                "reasons": sorted(reasons), "samples": len(self.rows), "samples_under_load": len(sm)}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm), "window": "1 s soak of the same step right before the timed region, and the timed region"}
 
 
 def dist_env():
@@ -255,12 +256,21 @@ def run_qai(args):
     n0 = qai.launch_count()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(local) as clk:
+        time.sleep(0.3)                          # let the sampler start
+        tc0 = time.perf_counter()
+        while time.perf_counter() - tc0 < 1.0:   # soak: same step, untimed
+            qai.mitigate(q, eb, out=out, workspace=ws)
+            torch.cuda.synchronize()
+        qai.profile_read()
+        n0 = qai.launch_count()
         barrier()
         ev0.record(stream)
         for _ in range(args.steps):
             qai.mitigate(q, eb, out=out, workspace=ws)
         ev1.record(stream)
         barrier()
+        tc1 = time.perf_counter()
+        time.sleep(0.1)
     launches = qai.launch_count() - n0
     kstats = qai.profile_read()
     qai.profile_enable(False)
@@ -323,7 +333,7 @@ def run_qai(args):
         "e2e": None if e2e_value is None else
         {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": 4 * N},
         "gpu_launches": launches,
-        "clocks": clk.summary(),
+        "clocks": clk.summary(tc0, tc1),
         "cpu_baseline": cpu,
         "quality": {"psnr_dprime_db": psnr_q, "psnr_mitigated_db": psnr_m,
                     "psnr_gain_db": psnr_m - psnr_q, "max_err_over_eps": max_err},
