@@ -121,6 +121,35 @@ qai_status qai_mitigate_host(const int32_t* h_q, float* h_out, int rank, const i
                              double eb, const qai_params* params, void* d_ws, size_t ws_bytes,
                              cudaStream_t stream);
 
+/* Largest field (points, after squeezing) that qai_mitigate_static accepts. */
+#define QAI_STATIC_MAX_POINTS 2097152
+
+/* qai_mitigate for callers that cannot allocate device memory at all: code
+ * running inside a host framework that owns every device allocation and
+ * forbids new ones while it executes (a plugin's execute callback, for one),
+ * or a latency-critical path that cannot afford cudaMalloc's implicit
+ * synchronisation and has no workspace of its own to hand over. The paper has
+ * no counterpart; it is a deployment convenience of this library.
+ *
+ * Instead of a workspace it uses one scratch array compiled into the library
+ * (a 256-byte aligned __device__ array of 12 * QAI_STATIC_MAX_POINTS + 1280
+ * bytes, about 24 MiB). Every GPU that loads the library holds that array
+ * until the process exits. The call itself allocates nothing: no cudaMalloc,
+ * no cudaFree, no library routine that allocates.
+ *  d_q, d_out, rank, dims, eb, params, stream: as for qai_mitigate (the
+ *          caller still passes the input and the output buffers).
+ * Fields larger than QAI_STATIC_MAX_POINTS points return QAI_ERR_SHAPE before
+ * any CUDA call. The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture. Every call shares the array, which keeps
+ * the last call's contents; no part of it needs to start at zero, because
+ * each kernel writes its slice of the array in full before any kernel reads
+ * it. Calls whose work overlaps on the GPU (two streams, or two host threads)
+ * race on the array and corrupt each other's results: serialise them, for
+ * example on one stream. No per-step (debug) outputs. */
+qai_status qai_mitigate_static(const int32_t* d_q, float* d_out, int rank, const int64_t* dims,
+                               double eb, const qai_params* params, cudaStream_t stream);
+
 /* Per-kernel timing. While enabled, every kernel the library launches is
  * bracketed by CUDA events recorded on the launch stream. qai_profile_read
  * waits for the recorded events, then reports, per kernel name, the launch

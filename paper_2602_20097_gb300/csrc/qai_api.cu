@@ -279,6 +279,8 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
 
 }  // namespace
 
+void qai::set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
 extern "C" {
 
 void qai_default_params(qai_params* p)

@@ -24,4 +24,7 @@ bool choose_colpass(int L, int in_bytes, ColConfig* cfg);
 cudaError_t launch_colpass(int phase, int in_bytes, bool final_pass, ColArgs& a,
                            const ColConfig& cfg, cudaStream_t st);
 
+// Records `msg` as qai_last_error() of the calling host thread.
+void set_last_error(const char* msg);
+
 }  // namespace qai

@@ -1,0 +1,78 @@
+// qai_static.cu -- qai_mitigate_static: the whole method on a fixed scratch
+// array that is part of the library, for callers that cannot allocate device
+// memory (see include/qai.h). Nothing here allocates: the array is a
+// file-scope __device__ variable, and its device address is looked up once
+// per device.
+#include <cstdio>
+#include <mutex>
+
+#include "../../include/qai.h"
+#include "qai_launch.h"
+
+namespace {
+
+// Workspace of the largest accepted field: at most 12 bytes per point (the
+// rank-3 layout: equal-q mask 1, Dist1 4, S 1, xwords 2, ywords 4) plus the
+// 256-byte alignment of its five slices.
+constexpr int64_t kMaxPoints = QAI_STATIC_MAX_POINTS;
+constexpr size_t kScratchBytes = (size_t)12 * (size_t)kMaxPoints + 5 * 256;
+
+__device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 256;
+std::mutex g_mu;
+void* g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of g_scratch on the current device. In host code the name
+// g_scratch is a host-side stand-in, never a device address.
+qai_status scratch_address(void** out)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        char msg[160];
+        snprintf(msg, sizeof msg, "qai_mitigate_static: no usable current device (%s)",
+                 cudaGetErrorString(e));
+        qai::set_last_error(msg);
+        return QAI_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_scratch_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_scratch);
+        if (e != cudaSuccess || !p) {
+            char msg[160];
+            snprintf(msg, sizeof msg, "qai_mitigate_static: cudaGetSymbolAddress failed: %s",
+                     cudaGetErrorString(e));
+            qai::set_last_error(msg);
+            return QAI_ERR_CUDA;
+        }
+        g_scratch_ptr[dev] = p;
+    }
+    *out = g_scratch_ptr[dev];
+    return QAI_OK;
+}
+
+}  // namespace
+
+extern "C" qai_status qai_mitigate_static(const int32_t* d_q, float* d_out, int rank,
+                                          const int64_t* dims, double eb, const qai_params* params,
+                                          cudaStream_t stream)
+{
+    size_t need = 0;
+    qai_status s = qai_workspace_size(rank, dims, 0, &need);  // validates rank and dims
+    if (s != QAI_OK) return s;
+    int64_t n = 1;
+    for (int a = 0; a < rank; ++a) n *= dims[a];
+    if (n > kMaxPoints || need > kScratchBytes) {
+        char msg[200];
+        snprintf(msg, sizeof msg,
+                 "qai_mitigate_static: %lld points exceed the static scratch limit of %lld points",
+                 (long long)n, (long long)kMaxPoints);
+        qai::set_last_error(msg);
+        return QAI_ERR_SHAPE;
+    }
+    void* ws = nullptr;
+    if ((s = scratch_address(&ws)) != QAI_OK) return s;
+    return qai_mitigate(d_q, d_out, rank, dims, eb, params, ws, kScratchBytes, stream, nullptr);
+}

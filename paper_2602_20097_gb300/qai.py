@@ -62,6 +62,8 @@ SIGNATURES = {
     "qai_workspace_size_host": (ctypes.c_int, [ctypes.c_int, P, ctypes.POINTER(ctypes.c_size_t)]),
     "qai_mitigate_host": (ctypes.c_int, [P, P, ctypes.c_int, P, ctypes.c_double, ctypes.POINTER(Params),
                                          P, ctypes.c_size_t, P]),
+    "qai_mitigate_static": (ctypes.c_int, [P, P, ctypes.c_int, P, ctypes.c_double,
+                                           ctypes.POINTER(Params), P]),
     "qai_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "qai_profile_read": (ctypes.c_int, [ctypes.POINTER(KernelStat), ctypes.c_int]),
     "qai_launch_count": (ctypes.c_int64, []),
@@ -198,6 +200,27 @@ def mitigate_host(q_host: torch.Tensor, eb: float, out_host: torch.Tensor | None
                                _stream(stream))
     _check(rc)
     return out_host
+
+
+STATIC_MAX_POINTS = 2097152
+
+
+def mitigate_static(q: torch.Tensor, eb: float, out: torch.Tensor | None = None, stream=None, **kw):
+    """Algorithm 4 without any device allocation by the library: for callers
+    that cannot allocate device memory. Uses the scratch array compiled into
+    libqai (fields up to STATIC_MAX_POINTS points); calls that overlap on the
+    GPU race on that array, so keep them on one stream."""
+    lib = load()
+    if not (q.is_cuda and q.dtype == torch.int32 and q.is_contiguous()):
+        raise QAIError("q must be a contiguous CUDA int32 tensor")
+    shape = tuple(q.shape)
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float32, device=q.device)
+    p = _params(kw.get("eta", 0.9), kw.get("idw_power", 1.0), kw.get("grad_threshold", 2),
+                kw.get("sign_rule", SIGN_SUM), kw.get("b2_rule", B2_SAME_Q))
+    _check(lib.qai_mitigate_static(q.data_ptr(), out.data_ptr(), len(shape), _dims(shape),
+                                   float(eb), ctypes.byref(p), _stream(stream)))
+    return out
 
 
 def profile_enable(on: bool = True):
