@@ -9,7 +9,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/qai.h"
+#include "qai.h"
 #include "qai_device.cuh"
 #include "qai_launch.h"
 
@@ -189,6 +189,9 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
     int32_t* idx_tmp = lay.idx ? reinterpret_cast<int32_t*>(ws + lay.idx) : nullptr;
     qai_debug_out none{};
     const qai_debug_out& d = dbg ? *dbg : none;
+    const bool debug = d.b1 || d.sb || d.dist1 || d.idx1 || d.s || d.b2 || d.dist2;
+    const int64_t gx = (int64_t)(sh.nx - 1) * (sh.nx - 1);           // max g after the x pass
+    const int64_t gxy = gx + (int64_t)(sh.ny - 1) * (sh.ny - 1);     // after the y pass
     cudaError_t e;
 
     // Step A + EDT-x of B1 (rank 1: the whole first EDT).
@@ -200,17 +203,18 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
     if (final1) { r1.dist1 = dist1; r1.s_out = s; r1.dbg_idx = d.idx1; }
     else { r1.xw = xw; r1.dbg_idx = d.idx1 ? (sh.rank == 3 ? d.idx1 : idx_tmp) : nullptr; }
     e = timed(final1 ? "rowpass1_final" : "rowpass1", N * (final1 ? 10.0 : 7.0), st,
-              [&] { return qai::launch_rowpass(1, final1, r1, st); });
+              [&] { return qai::launch_rowpass(1, final1, r1, debug, st); });
     if (e != cudaSuccess) return cuda_fail(e, "row pass 1");
 
     // EDT1 along y (and z): Dist1 and the propagated sign S.
     auto colpass = [&](int phase, int in_bytes, bool fin, qai::ColArgs& c, const char* name,
                        double bytes_per_pt) -> qai_status {
+        const int64_t max_g = in_bytes == 2 ? gx : gxy;
         qai::ColConfig cfg;
         if (!qai::choose_colpass(c.L, in_bytes, &cfg))
             return fail(QAI_ERR_SHAPE, "line length %d does not fit shared memory", c.L);
         cudaError_t err = timed(name, N * bytes_per_pt, st,
-                                [&] { return qai::launch_colpass(phase, in_bytes, fin, c, cfg, st); });
+                                [&] { return qai::launch_colpass(phase, in_bytes, fin, c, cfg, debug, max_g, st); });
         if (err != cudaSuccess) return cuda_fail(err, name);
         return QAI_OK;
     };
@@ -255,7 +259,7 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
     if (final1) { r2.dist1_in = dist1; r2.out = d_out; r2.dbg_dist2 = d.dist2; }
     else r2.xw = xw;
     e = timed(final1 ? "rowpass2_final" : "rowpass2", N * (final1 ? 14.0 : 4.0), st,
-              [&] { return qai::launch_rowpass(2, final1, r2, st); });
+              [&] { return qai::launch_rowpass(2, final1, r2, debug, st); });
     if (e != cudaSuccess) return cuda_fail(e, "row pass 2");
 
     // EDT2 along y (and z), the last pass fused with step E.

@@ -3,8 +3,8 @@
 //
 // A CTA owns W adjacent columns (lanes = columns, so every row access is
 // coalesced) and all L rows of them. The tile of input words is staged in
-// shared memory; the L rows are cut into B bands, one thread per
-// (column, band):
+// shared memory with cp.async vector copies; the L rows are cut into B bands,
+// one thread per (column, band):
 //   build   each thread runs Algorithm 1's envelope construction (the
 //           RemoveEDT stack) over its band alone; the stack holds row numbers
 //           h, the values g come from the staged tile;
@@ -13,15 +13,17 @@
 //           envelope and from the head of band k only while band k has fewer
 //           than two accepted entries: after that every triple is one band k
 //           already checked;
-//   query   each thread finds the envelope parabola of its first row by binary
-//           search (the index of the minimiser never decreases with the row),
-//           then walks its rows as Algorithm 1's query loop does, moving on
-//           only when the next parabola is strictly lower, so ties keep the
-//           earlier (smaller) row -- the nearest site with the smallest linear
-//           index once the passes run x, then y, then z.
+//   query   each thread finds the envelope parabola of its first row (first
+//           the band that holds it, then a binary search: the index of the
+//           minimiser never decreases with the row), then walks its rows as
+//           Algorithm 1's query loop does, moving on only when the next
+//           parabola is strictly lower, so ties keep the earlier (smaller)
+//           row -- the nearest site with the smallest linear index once the
+//           passes run x, then y, then z.
 // Phase 1 carries the sign code of the nearest boundary; its last pass writes
 // Dist1 and S = S_B[I1] (Algorithm 3's propagation). Phase 2's last pass fuses
 // step E: Dist2 goes straight into the compensation and never to memory.
+#include <cstdlib>
 #include <type_traits>
 
 #include "qai_device.cuh"
@@ -30,7 +32,8 @@
 namespace qai {
 namespace {
 
-constexpr int kMaxBands = 16;
+constexpr int kMaxBands = 32;
+constexpr int kWinMaxG = 24;   // outward-scan fast path: every finite g <= 24
 
 template <int PHASE, int IN>
 __device__ __forceinline__ int gval(uint32_t w)
@@ -43,18 +46,57 @@ __device__ __forceinline__ int gval(uint32_t w)
 }
 
 // RemoveEDT of Algorithm 1: parabola (g2, h2) lies strictly above the lower
-// envelope of (g1, h1) and the new one (f, i), i.e. c g2 - b g1 - a f - a b c
-// > 0 with a = h2 - h1, b = i - h2, c = i - h1, written as
-// c (g2 - f) - b (g1 - f) - (a b) c with 32-bit operands, 64-bit products.
+// envelope of (g1, h1) and the new one (f, i): c g2 - b g1 - a f - a b c > 0
+// with a = h2 - h1, b = i - h2, c = i - h1, written as
+// c (g2 - f) - b (g1 - f) - (a b) c. NARROW: every term fits 32 bits (the
+// host checks 2 L max(g) + L^3 < 2^31); otherwise 64-bit products.
+template <bool NARROW>
 __device__ __forceinline__ bool hidden(int g1, int g2, int f, int h1, int h2, int i)
 {
     const int a = h2 - h1, b = i - h2, c = i - h1;
-    const long long v = (long long)c * (g2 - f) - (long long)b * (g1 - f) - (long long)(a * b) * c;
-    return v > 0;
+    if (NARROW) return c * (g2 - f) - b * (g1 - f) - (a * b) * c > 0;
+    return (long long)c * (g2 - f) - (long long)b * (g1 - f) - (long long)(a * b) * c > 0;
 }
 
-template <int PHASE, int IN, bool FINAL>
-__global__ void __launch_bounds__(512) k_colpass(ColArgs a)
+__device__ __forceinline__ void cp_async(void* dst, const void* src, int bytes)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    if (bytes == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(src) : "memory");
+    else if (bytes == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(src) : "memory");
+}
+
+// Writes the result of one point: `val` is its squared distance, `w` the
+// input word of the winning row (phase 1: carries the sign code), `src` the
+// element index of that row in the same column (phase 1 index carry).
+template <int PHASE, int IN, bool FINAL, bool DEBUG, class Word>
+__device__ __forceinline__ void emit_point(const ColArgs& a, int idx, int src, int val, Word w, bool valid)
+{
+    if (PHASE == 1) {
+        const int code = valid ? (int)(w & 3u) : 0;
+        if (!FINAL) {
+            static_cast<uint32_t*>(a.out_w)[idx] = valid ? ((uint32_t)val << 2) | (uint32_t)code : kInf32;
+        } else {
+            a.dist1[idx] = valid ? val : kDistInf;
+            a.s_out[idx] = (int8_t)sign_of_code(code);
+        }
+        if (DEBUG && a.dbg_idx_out) a.dbg_idx_out[idx] = valid ? a.dbg_idx_in[src] : -1;
+    } else {
+        const int32_t d = valid ? val : kDistInf;
+        if (!FINAL) {
+            static_cast<uint32_t*>(a.out_w)[idx] = valid ? (uint32_t)val : kInf32;
+        } else {
+            a.out[idx] = compensate(__ldg(a.q + idx), __ldg(a.dist1_in + idx), d, __ldg(a.s_in + idx), a.m);
+            if (DEBUG && a.dbg_dist2) a.dbg_dist2[idx] = d;
+        }
+    }
+}
+
+template <int PHASE, int IN, bool FINAL, bool DEBUG, bool NARROW>
+__global__ void __launch_bounds__(512, IN == 2 ? 3 : 2) k_colpass(ColArgs a)
 {
     using Word = std::conditional_t<IN == 2, uint16_t, uint32_t>;
     constexpr Word kWInf = IN == 2 ? (Word)kInf16 : (Word)kInf32;
@@ -63,213 +105,351 @@ __global__ void __launch_bounds__(512) k_colpass(ColArgs a)
     const int col = threadIdx.x, band = threadIdx.y;
     const int tid = band * W + col, nthr = W * B;
     const int L = a.L;
-    Word* tile = reinterpret_cast<Word*>(smem);                       // [L][W]
-    uint16_t* stk = reinterpret_cast<uint16_t*>(tile + (size_t)L * W);  // [L][W]
-    uint16_t* segA = stk + (size_t)L * W;                               // [B][W]
+    Word* tile = reinterpret_cast<Word*>(smem);                       // [L][W] input words
+    uint16_t* stk = reinterpret_cast<uint16_t*>(tile + (size_t)L * W);  // [L][W] band stacks (rows h)
+    uint16_t* segA = stk + (size_t)L * W;                               // [B][W] kept range of each band
     uint16_t* segE = segA + B * W;                                      // [B][W]
-    uint16_t* segO = segE + B * W;                                      // [B][W]
-    uint16_t* nsum = segO + B * W;                                      // [W]
+    uint16_t* lstb = segE + B * W;                                      // [B][W] bands of the envelope, in order
+    uint16_t* nlst = lstb + B * W;                                      // [W] number of such bands
 
     const int tiles_per_plane = (a.C + W - 1) / W;
     const int p = blockIdx.x / tiles_per_plane;
     const int c0 = (blockIdx.x - p * tiles_per_plane) * W;
-    const int64_t pbase = (int64_t)p * a.plane_stride;
-    const int wshift = __ffs(W) - 1;
+    const int pbase = p * a.plane_stride;
+    const int RS = a.row_stride;
     const Word* in = static_cast<const Word*>(a.in);
 
+    __shared__ int s_gmax;  // largest g of the tile (the fast-path test below)
+    if (tid == 0) s_gmax = 0;
+
     // ---- stage the tile ----------------------------------------------------
-#pragma unroll 4
-    for (int e = tid; e < L * W; e += nthr) {
-        const int r = e >> wshift, c = c0 + (e & (W - 1));
-        tile[e] = c < a.C ? in[pbase + (int64_t)r * a.row_stride + c] : kWInf;
+    {
+        const int cols = min(W, a.C - c0);
+        const int vb = a.load_bytes;
+        if (vb) {
+            const int row_bytes = W * IN;
+            const int cpr = row_bytes / vb, vcpr = cols * IN / vb;
+            const char* gsrc = reinterpret_cast<const char*>(in + pbase + c0);
+            for (int e = tid; e < L * cpr; e += nthr) {
+                const int r = e / cpr, k = e - r * cpr;
+                char* dst = reinterpret_cast<char*>(tile) + r * row_bytes + k * vb;
+                if (k < vcpr) {
+                    cp_async(dst, gsrc + (size_t)r * RS * IN + k * vb, vb);
+                } else {
+                    for (int b = 0; b < vb; b += 4) *reinterpret_cast<uint32_t*>(dst + b) = 0xFFFFFFFFu;
+                }
+            }
+            asm volatile("cp.async.wait_all;\n" ::: "memory");
+        } else {
+            const int wshift = __ffs(W) - 1;
+            for (int e = tid; e < L * W; e += nthr) {
+                const int r = e >> wshift, c = e & (W - 1);
+                tile[e] = c < cols ? in[pbase + r * RS + c0 + c] : kWInf;
+            }
+        }
     }
     __syncthreads();
 
-    // ---- build: Algorithm 1's envelope over this band ------------------------
     const int Lb = (L + B - 1) / B;
     const int r0 = min(L, band * Lb), r1 = min(L, r0 + Lb);
+    const int c = c0 + col;
+    const Word* tcol = tile + col;  // element (r, col) at tcol[r * W]
+    auto gat = [&](int r) { return gval<PHASE, IN>(tcol[r * W]); };
+
+    // ---- small-distance fast path ------------------------------------------
+    // Row r's minimiser r' satisfies (r - r')^2 <= best value found so far, so
+    // an outward scan r, r-1, r+1, r-2, r+2, ... can stop at the first k with
+    // k^2 > best. Taking r - k on ties (<=) and r + k only when strictly lower
+    // returns exactly Algorithm 1's answer (the smallest r' among equal minima).
+    // The scan is short when every finite g in the tile is at most kWinMaxG
+    // and no column has three INF rows in a row (an INF row then lies within
+    // two rows of a finite one); otherwise the tile takes the envelope path.
     {
-        int n = 0, h1 = 0, h2 = 0, g1 = 0, g2 = 0;
+        int gm = 0;
+        if (c < a.C) {
+            int run = 0;
+            for (int r = max(0, r0 - 2); r < r1; ++r) {
+                const Word w = tcol[r * W];
+                if (w == kWInf) {
+                    if (++run >= 3 && r >= r0) gm = 0x7FFFFFFF;
+                } else {
+                    run = 0;
+                    if (r >= r0) gm = max(gm, gval<PHASE, IN>(w));
+                }
+            }
+        }
+        if (gm > kWinMaxG) atomicMax(&s_gmax, gm);
+        __syncthreads();
+        if (s_gmax <= kWinMaxG) {
+            if (c >= a.C) return;
+            for (int r = r0; r < r1; ++r) {
+                // k = 0
+                Word bw = tcol[r * W];
+                int bh = bw != kWInf ? r : -1;
+                int best = bw != kWInf ? gval<PHASE, IN>(bw) : 0x7FFFFFFF;
+                for (int k = 1; k < L && k * k <= best; ++k) {
+                    if (r - k >= 0) {
+                        const Word w = tcol[(r - k) * W];
+                        const int v = gval<PHASE, IN>(w) + k * k;
+                        if (w != kWInf && v <= best) { best = v; bh = r - k; bw = w; }
+                    }
+                    if (r + k < L) {
+                        const Word w = tcol[(r + k) * W];
+                        const int v = gval<PHASE, IN>(w) + k * k;
+                        if (w != kWInf && v < best) { best = v; bh = r + k; bw = w; }
+                    }
+                }
+                emit_point<PHASE, IN, FINAL, DEBUG>(a, pbase + r * RS + c, pbase + max(bh, 0) * RS + c,
+                                                    best, bw, bh >= 0);
+            }
+            return;
+        }
+    }
+
+    // ---- build: Algorithm 1's envelope over this band ------------------------
+    uint16_t* scol = stk + col;  // stack entry i of this column at scol[i * W]
+    {
+        // the three top entries live in registers (h2, g2 on top); after a pop
+        // the load of the new third entry overlaps the next RemoveEDT test
+        int n = 0, h0 = 0, g0 = 0, h1 = 0, g1 = 0, h2 = 0, g2 = 0;
         for (int r = r0; r < r1; ++r) {
-            const Word w = tile[r * W + col];
+            const Word w = tcol[r * W];
             if (w == kWInf) continue;
             const int f = gval<PHASE, IN>(w);
-            while (n >= 2 && hidden(g1, g2, f, h1, h2, r)) {
+            while (n >= 2 && hidden<NARROW>(g1, g2, f, h1, h2, r)) {
                 --n;
                 h2 = h1;
                 g2 = g1;
-                if (n >= 2) {
-                    h1 = stk[(r0 + n - 2) * W + col];
-                    g1 = gval<PHASE, IN>(tile[h1 * W + col]);
+                h1 = h0;
+                g1 = g0;
+                if (n >= 3) {
+                    h0 = scol[(r0 + n - 3) * W];
+                    g0 = gat(h0);
                 }
             }
-            stk[(r0 + n) * W + col] = (uint16_t)r;
+            scol[(r0 + n) * W] = (uint16_t)r;
+            h0 = h1;
+            g0 = g1;
             h1 = h2;
             g1 = g2;
             h2 = r;
             g2 = f;
             ++n;
         }
-        segE[band * W + col] = (uint16_t)n;  // count; the merge turns it into an end
+        segA[band * W + col] = (uint16_t)r0;  // the band's stack: rows r0 .. r0 + n
+        segE[band * W + col] = (uint16_t)(r0 + n);
     }
     __syncthreads();
 
-    // ---- merge the band envelopes of each column --------------------------
-    if (band == 0) {
-        int lst[kMaxBands];
-        int nl = 0, total = 0;
-        auto entry_h = [&](int pos) { return (int)stk[pos * W + col]; };
-        auto entry_g = [&](int h) { return gval<PHASE, IN>(tile[h * W + col]); };
-        for (int k = 0; k < B; ++k) {
-            const int kb = min(L, k * Lb);
-            const int cnt = segE[k * W + col];
-            int A = kb;
-            const int E = kb + cnt;
-            if (cnt == 0) {
-                segA[k * W + col] = (uint16_t)kb;
-                segE[k * W + col] = (uint16_t)kb;
-                continue;
-            }
-            for (int cur = A; cur < E && cur - A < 2; ++cur) {
-                const int hf = entry_h(cur), gf = entry_g(hf);
-                for (;;) {
-                    const int lenb = cur - A;
-                    int ht1, ht2;
-                    if (lenb == 1) {
-                        if (nl == 0) break;
-                        ht1 = entry_h(A);
-                        ht2 = entry_h(segE[lst[nl - 1] * W + col] - 1);
-                    } else {
-                        if (total < 2) break;
-                        const int kl = lst[nl - 1];
-                        const int e = segE[kl * W + col], s = segA[kl * W + col];
-                        ht1 = entry_h(e - 1);
-                        ht2 = (e - s >= 2) ? entry_h(e - 2)
-                                           : entry_h(segE[lst[nl - 2] * W + col] - 1);
+    // ---- merge the band envelopes of each column, as a tree -----------------
+    // Round j splices the envelopes of adjacent groups of 2^j bands, all pairs
+    // at once: Maurer's stack construction continued with the right group's
+    // entries pops the left group's tail and the right group's head, and
+    // stops once two right entries stand (every later triple was already
+    // checked inside the right group). A band keeps its surviving entries as
+    // the range [segA, segE) of its stack. The result equals Algorithm 1's
+    // envelope up to parabolas that only touch it at one point, which never
+    // win a query (a neighbour with a smaller row ties there).
+    for (int span = 1; span < B; span <<= 1) {
+        if ((band & (2 * span - 1)) == 0 && band + span < B) {
+            const int g0 = band, gm = band + span, g1 = min(B, band + 2 * span);
+            auto A_ = [&](int k) { return (int)segA[k * W + col]; };
+            auto E_ = [&](int k) { return (int)segE[k * W + col]; };
+            // left group: last two entries e1 (band k1, pos p1) and e2 (k2, p2)
+            int nleft = 0;
+            for (int k = g0; k < gm; ++k) nleft += E_(k) - A_(k);
+            int k1 = gm - 1;
+            while (k1 >= g0 && A_(k1) == E_(k1)) --k1;
+            int kr = gm;
+            while (kr < g1 && A_(kr) == E_(kr)) ++kr;
+            if (k1 >= g0 && kr < g1) {
+                int p1 = E_(k1) - 1, k2 = k1, p2 = p1 - 1;
+                if (p2 < A_(k2)) {
+                    k2 = k1 - 1;
+                    while (k2 >= g0 && A_(k2) == E_(k2)) --k2;
+                    p2 = k2 >= g0 ? E_(k2) - 1 : 0;
+                }
+                int e1h = scol[p1 * W], e2h = nleft >= 2 ? scol[p2 * W] : 0;
+                int e1g = gat(e1h), e2g = nleft >= 2 ? gat(e2h) : 0;
+                // right group: candidates in order, from band kc position pc
+                int kc = kr, pc = A_(kr);
+                int acc = 0, bh = 0, bg = 0, bk = 0, bp = 0;  // first accepted right entry
+                while (kc < g1 && acc < 2) {
+                    const int fh = scol[pc * W], fg = gat(fh);
+                    for (;;) {
+                        if (acc == 1) {
+                            if (nleft == 0 || !hidden<NARROW>(e1g, bg, fg, e1h, bh, fh)) break;
+                            segA[bk * W + col] = (uint16_t)(bp + 1);  // pop the right entry
+                            acc = 0;
+                        } else {
+                            if (nleft < 2 || !hidden<NARROW>(e2g, e1g, fg, e2h, e1h, fh)) break;
+                            segE[k1 * W + col] = (uint16_t)p1;  // pop the left group's last entry
+                            --nleft;
+                            k1 = k2;
+                            p1 = p2;
+                            e1h = e2h;
+                            e1g = e2g;
+                            if (nleft >= 2) {
+                                p2 = p1 - 1;
+                                if (p2 < A_(k2)) {
+                                    k2 = k2 - 1;
+                                    while (k2 >= g0 && A_(k2) == E_(k2)) --k2;
+                                    p2 = E_(k2) - 1;
+                                }
+                                e2h = scol[p2 * W];
+                                e2g = gat(e2h);
+                            }
+                        }
                     }
-                    if (!hidden(entry_g(ht2), entry_g(ht1), gf, ht2, ht1, hf)) break;
-                    if (lenb == 1) {
-                        A = cur;  // band k's only accepted entry is popped
-                    } else {
-                        const int kl = lst[nl - 1];
-                        const int e = segE[kl * W + col] - 1;
-                        segE[kl * W + col] = (uint16_t)e;
-                        --total;
-                        if (e == segA[kl * W + col]) --nl;
+                    if (acc == 0) { bh = fh; bg = fg; bk = kc; bp = pc; }
+                    ++acc;
+                    if (++pc >= E_(kc)) {
+                        ++kc;
+                        while (kc < g1 && A_(kc) == E_(kc)) ++kc;
+                        if (kc < g1) pc = A_(kc);
                     }
                 }
             }
-            segA[k * W + col] = (uint16_t)A;
-            segE[k * W + col] = (uint16_t)E;
-            lst[nl++] = k;
-            total += E - A;
         }
-        int off = 0;
-        for (int k = 0; k < B; ++k) {
-            segO[k * W + col] = (uint16_t)off;
-            off += segE[k * W + col] - segA[k * W + col];
-        }
-        nsum[col] = (uint16_t)off;
+        __syncthreads();
+    }
+    if (band == 0) {  // the envelope's bands, in order
+        uint16_t* lst = lstb + col;
+        int nl = 0;
+        for (int k = 0; k < B; ++k)
+            if (segA[k * W + col] != segE[k * W + col]) lst[(nl++) * W] = (uint16_t)k;
+        nlst[col] = (uint16_t)nl;
     }
     __syncthreads();
 
     // ---- query -------------------------------------------------------------
-    const int c = c0 + col;
+    // The envelope is the concatenation of the kept ranges of the bands
+    // lst[0 .. nl), in order.
     if (c >= a.C || r0 >= r1) return;
-    const int ns = nsum[col];
-
-    auto emit = [&](int r, int val, Word w, int h, bool valid) {
-        const int64_t idx = pbase + (int64_t)r * a.row_stride + c;
-        if (PHASE == 1) {
-            const int code = valid ? (int)(w & 3u) : 0;
-            if (!FINAL) {
-                static_cast<uint32_t*>(a.out_w)[idx] = valid ? ((uint32_t)val << 2) | (uint32_t)code
-                                                             : kInf32;
-            } else {
-                a.dist1[idx] = valid ? val : kDistInf;
-                a.s_out[idx] = (int8_t)sign_of_code(code);
-            }
-            if (a.dbg_idx_out)
-                a.dbg_idx_out[idx] =
-                    valid ? a.dbg_idx_in[pbase + (int64_t)h * a.row_stride + c] : -1;
-        } else {
-            const int32_t d = valid ? val : kDistInf;
-            if (!FINAL) {
-                static_cast<uint32_t*>(a.out_w)[idx] = valid ? (uint32_t)val : kInf32;
-            } else {
-                a.out[idx] = compensate(a.q[idx], a.dist1_in[idx], d, a.s_in[idx], a.m);
-                if (a.dbg_dist2) a.dbg_dist2[idx] = d;
-            }
-        }
-    };
-
-    if (ns == 0) {
-        for (int r = r0; r < r1; ++r) emit(r, 0, 0, 0, false);
+    const uint16_t* lst = lstb + col;
+    const int nl = nlst[col];
+    if (nl == 0) {  // empty column: no site reaches it
+        for (int r = r0; r < r1; ++r)
+            emit_point<PHASE, IN, FINAL, DEBUG>(a, pbase + r * RS + c, 0, 0, (Word)0, false);
         return;
     }
-    // global envelope position -> stack position
-    auto locate = [&](int m, int* kout) {
-        for (int k = 0; k < B; ++k) {
-            const int o = segO[k * W + col];
-            const int len = segE[k * W + col] - segA[k * W + col];
-            if (m >= o && m < o + len) {
-                *kout = k;
-                return segA[k * W + col] + (m - o);
-            }
-        }
-        *kout = 0;
-        return 0;  // not reached for 0 <= m < ns
+    auto val_at = [&](int pos, int r) {
+        const int hh = scol[pos * W];
+        return gat(hh) + (hh - r) * (hh - r);
     };
-    auto value = [&](int m, int r) {
-        int k;
-        const int h = stk[locate(m, &k) * W + col];
-        return gval<PHASE, IN>(tile[h * W + col]) + (h - r) * (h - r);
-    };
-    int lo = 0, hi = ns - 1;
+    // envelope entry of row r0: the first entry that the next one does not
+    // beat at r0 (the minimiser's index never decreases with the row); first
+    // the band that holds it, then the entry inside that band
+    int lo = 0, hi = nl - 1;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (value(mid, r0) > value(mid + 1, r0)) lo = mid + 1;
+        const int kl = lst[mid * W], kr = lst[(mid + 1) * W];
+        if (val_at(segE[kl * W + col] - 1, r0) > val_at(segA[kr * W + col], r0)) lo = mid + 1;
         else hi = mid;
     }
-    int m = lo, k;
-    int pos = locate(m, &k);
-    int h = stk[pos * W + col];
-    Word w = tile[h * W + col];
+    int li = lo;
+    int k = lst[li * W];
+    int endk = segE[k * W + col];
+    lo = segA[k * W + col];
+    hi = endk - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (val_at(mid, r0) > val_at(mid + 1, r0)) lo = mid + 1;
+        else hi = mid;
+    }
+    int pos = lo;
+    int h = scol[pos * W];
+    Word w = tcol[h * W];
     int g = gval<PHASE, IN>(w);
+    // next entry: (li_n, pos_n), pos_n < 0 when there is none
+    int li_n = li, pos_n = pos + 1;
+    if (pos_n >= endk) pos_n = li + 1 < nl ? segA[lst[(++li_n) * W] * W + col] : -1;
+    int hn = pos_n >= 0 ? scol[pos_n * W] : 0;
+    Word wn = pos_n >= 0 ? tcol[hn * W] : (Word)0;
+    int gn = gval<PHASE, IN>(wn);
+
+    // the last phase-2 pass loads step E's operands one row ahead, so their
+    // latency overlaps the walk
+    constexpr bool kFuseE = PHASE == 2 && FINAL;
+    int idx = pbase + r0 * RS + c;
+    int pq = 0, pd1 = 0, ps = 0;
+    if (kFuseE) {
+        pq = __ldg(a.q + idx);
+        pd1 = __ldg(a.dist1_in + idx);
+        ps = __ldg(a.s_in + idx);
+    }
     for (int r = r0; r < r1; ++r) {
-        while (m + 1 < ns) {
-            int kn = k, pn = pos + 1;
-            if (pn >= segE[k * W + col]) {
-                do { ++kn; } while (kn < B - 1 && segE[kn * W + col] == segA[kn * W + col]);
-                pn = segA[kn * W + col];
+        int nq = 0, nd1 = 0, nsg = 0;
+        if (kFuseE && r + 1 < r1) {
+            nq = __ldg(a.q + idx + RS);
+            nd1 = __ldg(a.dist1_in + idx + RS);
+            nsg = __ldg(a.s_in + idx + RS);
+        }
+        while (pos_n >= 0 && g + (h - r) * (h - r) > gn + (hn - r) * (hn - r)) {
+            if (li_n != li) {
+                li = li_n;
+                endk = segE[lst[li * W] * W + col];
             }
-            const int hn = stk[pn * W + col];
-            const Word wn = tile[hn * W + col];
-            const int gn = gval<PHASE, IN>(wn);
-            if (g + (h - r) * (h - r) > gn + (hn - r) * (hn - r)) {
-                ++m;
-                k = kn;
-                pos = pn;
-                h = hn;
-                w = wn;
-                g = gn;
-            } else {
-                break;
+            pos = pos_n;
+            h = hn;
+            w = wn;
+            g = gn;
+            pos_n = pos + 1;
+            if (pos_n >= endk) pos_n = li + 1 < nl ? segA[lst[(++li_n) * W] * W + col] : -1;
+            if (pos_n >= 0) {
+                hn = scol[pos_n * W];
+                wn = tcol[hn * W];
+                gn = gval<PHASE, IN>(wn);
             }
         }
-        emit(r, g + (h - r) * (h - r), w, h, true);
+        const int val = g + (h - r) * (h - r);
+        if (kFuseE) {
+            a.out[idx] = compensate(pq, pd1, val, ps, a.m);
+            if (DEBUG && a.dbg_dist2) a.dbg_dist2[idx] = val;
+            pq = nq;
+            pd1 = nd1;
+            ps = nsg;
+        } else {
+            emit_point<PHASE, IN, FINAL, DEBUG>(a, idx, pbase + h * RS + c, val, w, true);
+        }
+        idx += RS;
     }
+}
+
+template <int PHASE, int IN, bool FINAL>
+cudaError_t go(ColArgs& a, bool debug, bool narrow, dim3 grid, dim3 block, size_t smem, cudaStream_t st)
+{
+    auto run = [&](auto kern) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<grid, block, smem, st>>>(a);
+        return cudaGetLastError();
+    };
+    if (debug) return narrow ? run(k_colpass<PHASE, IN, FINAL, true, true>)
+                             : run(k_colpass<PHASE, IN, FINAL, true, false>);
+    return narrow ? run(k_colpass<PHASE, IN, FINAL, false, true>)
+                  : run(k_colpass<PHASE, IN, FINAL, false, false>);
 }
 
 }  // namespace
 
+// Rows per band and the largest column count per CTA; QAI_COL_ROWS_PER_BAND
+// and QAI_COL_MAX_W override them (tuning experiments).
+static int env_int(const char* name, int dflt)
+{
+    const char* v = getenv(name);
+    return v && *v ? atoi(v) : dflt;
+}
+
 bool choose_colpass(int L, int in_bytes, ColConfig* cfg)
 {
-    int B = (L + 47) / 48;
+    static const int rows_per_band = env_int("QAI_COL_ROWS_PER_BAND", 32);
+    static const int max_w = env_int("QAI_COL_MAX_W", 16);
+    int B = (L + rows_per_band - 1) / rows_per_band;
     B = B < 2 ? 2 : (B > kMaxBands ? kMaxBands : B);
     if (B > L) B = L < 1 ? 1 : L;
     const size_t budget = 200 * 1024;
-    for (int W = 32; W >= 4; W >>= 1) {
+    for (int W = max_w; W >= 4; W >>= 1) {
         const size_t smem = (size_t)L * W * (in_bytes + 2) + (size_t)3 * B * W * 2 + (size_t)W * 2;
         if (smem <= budget) {
             cfg->W = W;
@@ -281,25 +461,31 @@ bool choose_colpass(int L, int in_bytes, ColConfig* cfg)
     return false;
 }
 
-cudaError_t launch_colpass(int phase, int in_bytes, bool final_pass, ColArgs& a,
-                           const ColConfig& cfg, cudaStream_t st)
+cudaError_t launch_colpass(int phase, int in_bytes, bool final_pass, ColArgs& a, const ColConfig& cfg,
+                           bool debug, int64_t max_g, cudaStream_t st)
 {
     a.bands = cfg.B;
+    // cp.async granularity: every tile row segment must start 'vb'-aligned
+    a.load_bytes = 0;
+    for (int vb = 16; vb >= 4; vb >>= 1) {
+        const bool ok = ((int64_t)a.row_stride * in_bytes) % vb == 0 &&
+                        ((int64_t)a.plane_stride * in_bytes) % vb == 0 &&
+                        ((int64_t)a.C * in_bytes) % vb == 0 && (cfg.W * in_bytes) % vb == 0 &&
+                        (reinterpret_cast<uintptr_t>(a.in) % vb) == 0;
+        if (ok) { a.load_bytes = vb; break; }
+    }
+    const int64_t L = a.L;
+    const bool narrow = 2 * L * max_g + L * L * L < (int64_t)0x7FFFFFFF;
     const int tiles = ((a.C + cfg.W - 1) / cfg.W) * a.P;
     const dim3 grid(tiles), block(cfg.W, cfg.B);
-    auto go = [&](auto kern) -> cudaError_t {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)cfg.smem);
-        if (e != cudaSuccess) return e;
-        kern<<<grid, block, cfg.smem, st>>>(a);
-        return cudaGetLastError();
-    };
     if (phase == 1) {
-        if (in_bytes == 2) return final_pass ? go(k_colpass<1, 2, true>) : go(k_colpass<1, 2, false>);
-        return go(k_colpass<1, 4, true>);
+        if (in_bytes == 2) return final_pass ? go<1, 2, true>(a, debug, narrow, grid, block, cfg.smem, st)
+                                             : go<1, 2, false>(a, debug, narrow, grid, block, cfg.smem, st);
+        return go<1, 4, true>(a, debug, narrow, grid, block, cfg.smem, st);
     }
-    if (in_bytes == 2) return final_pass ? go(k_colpass<2, 2, true>) : go(k_colpass<2, 2, false>);
-    return go(k_colpass<2, 4, true>);
+    if (in_bytes == 2) return final_pass ? go<2, 2, true>(a, debug, narrow, grid, block, cfg.smem, st)
+                                         : go<2, 2, false>(a, debug, narrow, grid, block, cfg.smem, st);
+    return go<2, 4, true>(a, debug, narrow, grid, block, cfg.smem, st);
 }
 
 }  // namespace qai

@@ -69,6 +69,7 @@ struct ColArgs {
     int P;                   // planes
     int64_t row_stride, plane_stride;
     int bands;               // B, rows are split in B bands of ceil(L / B)
+    int load_bytes;          // cp.async width of the tile staging (16, 8, 4; 0 = plain loads)
     void* out_w;             // non-final output words (yword)
     int32_t* dist1;          // phase 1 final
     int8_t* s_out;           // phase 1 final
@@ -82,34 +83,55 @@ struct ColArgs {
     MethodArgs m;
 };
 
+// PTX approximate square root, reciprocal, log2 and exp2 (a few ulp each;
+// the weights they feed are compared at 1e-6 of the value range).
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float y;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2_approx(float x)
+{
+    float y;
+    asm("lg2.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Step E for one point: C = S * w * eta * eps with the inverse-distance weight
 // w = k2^p / (k1^p + k2^p) of the distances k1 = sqrt(Dist1), k2 = sqrt(Dist2);
 // a point on B1 gets w = 1 (this takes precedence), a point on B2 gets w = 0,
 // and a field without B2 gives w = 1 (the limit k2 -> infinity).
+// For p = 1, w = k2 / (k1 + k2) = Dist2 / (sqrt(Dist1 Dist2) + Dist2); for
+// other p, w = 1 / (1 + 2^(p/2 (log2 Dist1 - log2 Dist2))). No branches: the
+// special cases are selects, and S = 0 zeroes C through the product.
 __device__ __forceinline__ float compensate(int32_t q, int32_t d1, int32_t d2, int s,
                                             const MethodArgs& m)
 {
-    float c = 0.0f;
-    if (s != 0) {
-        float w;
-        if (d1 == 0) {
-            w = 1.0f;
-        } else if (d2 == 0) {
-            w = 0.0f;
-        } else if (d2 == kDistInf) {
-            w = 1.0f;
-        } else {
-            float k1 = sqrtf((float)d1), k2 = sqrtf((float)d2);
-            if (m.idw_is_one) {
-                w = k2 / (k1 + k2);
-            } else {
-                float a = powf(k1, m.idw_power), b = powf(k2, m.idw_power);
-                w = b / (a + b);
-            }
-        }
-        c = (float)s * w * m.eta_eb;
+    const float f1 = (float)d1, f2 = (float)d2;
+    float w;
+    if (m.idw_is_one) {
+        w = f2 * rcp_approx(sqrt_approx(f1 * f2) + f2);
+    } else {
+        const float t = ex2_approx(0.5f * m.idw_power * (lg2_approx(f1) - lg2_approx(f2)));
+        w = rcp_approx(1.0f + t);
     }
-    return fmaf((float)q, m.two_eb, c);
+    w = d2 == kDistInf ? 1.0f : w;
+    w = d2 == 0 ? 0.0f : w;
+    w = d1 == 0 ? 1.0f : w;
+    return fmaf((float)q, m.two_eb, (float)s * w * m.eta_eb);
 }
 
 }  // namespace qai

@@ -11,7 +11,8 @@ namespace qai {
 // phase 2 = GetBoundary(S) + EDT-x of B2; final = the field is rank 1.
 int rowpass_warps(int nx);
 size_t rowpass_smem(int nx, int warps);
-cudaError_t launch_rowpass(int phase, bool final_pass, const RowArgs& a, cudaStream_t st);
+// debug: also write the per-step outputs named in `a`.
+cudaError_t launch_rowpass(int phase, bool final_pass, const RowArgs& a, bool debug, cudaStream_t st);
 
 // Column pass (qai_colpass.cu): EDT along y or z. in_bytes = 2 for an xword
 // input (the pass right after a row pass), 4 for a yword input.
@@ -21,8 +22,10 @@ struct ColConfig {
     size_t smem;  // dynamic shared memory bytes
 };
 bool choose_colpass(int L, int in_bytes, ColConfig* cfg);
+// max_g bounds the squared distances carried by the input words; it decides
+// whether RemoveEDT can run on 32-bit products.
 cudaError_t launch_colpass(int phase, int in_bytes, bool final_pass, ColArgs& a,
-                           const ColConfig& cfg, cudaStream_t st);
+                           const ColConfig& cfg, bool debug, int64_t max_g, cudaStream_t st);
 
 // Records `msg` as qai_last_error() of the calling host thread.
 void set_last_error(const char* msg);

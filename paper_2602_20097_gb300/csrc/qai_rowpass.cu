@@ -4,17 +4,25 @@
 // Phase 1 = step A (Algorithm 2, GetBoundaryAndSignMap) on the int32 index
 // field q, then the x pass of the EDT of B1 (Algorithm 1 along x; with a
 // binary input every parabola has g = 0, so the lower envelope reduces to the
-// nearest site on the left and on the right, found by warp prefix scans).
+// nearest site on the left and on the right).
 // Phase 2 = GetBoundary(S) of Algorithm 3 (the sign-flipping boundary B2),
 // then the x pass of the EDT of B2.
 // For a rank-1 field the x pass is the last pass: phase 1 then writes Dist1
 // and the propagated sign S (Algorithm 3), phase 2 writes D'' (step E).
 //
-// One warp owns one x-row. Three sweeps over the row, 32 points per step:
-//   1. detect sites, keep a site byte per point in shared memory;
-//   2. left to right: inclusive prefix max of site positions -> left site;
-//   3. right to left: suffix min -> right site; the nearer one wins, the left
-//      one on a tie (the smaller index, as Algorithm 1's strict query gives).
+// One warp owns one x-row and walks it in segments of 128 points, each lane
+// holding 4 consecutive points (128-bit loads of q, 32-bit loads of the sign
+// bytes). Two sweeps:
+//   A  detect the sites of the segment; keep, per lane, a 4-bit site nibble
+//      and the four 2-bit sign codes in shared memory, and the first and last
+//      site of the segment;
+//   B  nearest site to the left and to the right of every point: inside the
+//      lane by a chain over its nibble, across lanes by a ballot and one
+//      shuffle, across segments by carries (the right carry comes from a
+//      backward scan over the segment summaries). The nearer site wins, the
+//      left one on a tie (the smaller index, as Algorithm 1's strict query).
+// Arithmetic on q is 32-bit; a warp whose loaded values reach |q| >= 2^27
+// (where a sum of six differences could overflow) takes a 64-bit path.
 #include "qai_device.cuh"
 #include "qai_launch.h"
 
@@ -22,8 +30,151 @@ namespace qai {
 namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kSeg = 128;                 // points per warp step
+constexpr int kNoneL = -(1 << 20);        // "no site on the left" position
+constexpr int kNoneR = (1 << 20);         // "no site on the right" position
+constexpr int kNoRef = (int)0x80000000;   // segment without a site
 
-template <int PHASE, bool FINAL>
+// Shared memory of one warp: three int arrays of segment summaries and the
+// per-lane site nibbles / sign codes (one u16 per 4 points).
+__host__ __device__ inline size_t smem_per_warp(int nx)
+{
+    const size_t nseg = (size_t)((nx + kSeg - 1) / kSeg);
+    return ((nseg * 3 * 4 + nseg * 32 * 2) + 15) & ~(size_t)15;
+}
+
+// A site reference packs the position and the 2-bit sign code.
+__device__ __forceinline__ int make_ref(int pos, int code) { return (pos << 2) | code; }
+
+struct RowSmem {
+    uint16_t* info;   // [nseg * 32]: bits 0..3 site nibble, 4..11 sign codes
+    int* sfirst;      // [nseg] first site ref of the segment (kNoRef if none)
+    int* slast;       // [nseg] last site ref
+    int* nextr;       // [nseg] first site ref right of the segment
+};
+
+__device__ __forceinline__ void load4_i32(const int32_t* p, int x0, int nx, bool vec, int v[4])
+{
+    if (vec) {
+        if (x0 < nx) {
+            const int4 t = __ldg(reinterpret_cast<const int4*>(p + x0));
+            v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+        } else {
+            v[0] = v[1] = v[2] = v[3] = 0;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[j] = (x0 + j < nx) ? __ldg(p + x0 + j) : 0;
+    }
+}
+
+__device__ __forceinline__ uint32_t load4_u8(const void* base, int x0, int nx, bool vec)
+{
+    const uint8_t* p = static_cast<const uint8_t*>(base);
+    if (vec) return x0 < nx ? __ldg(reinterpret_cast<const uint32_t*>(p + x0)) : 0u;
+    uint32_t w = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (x0 + j < nx) w |= (uint32_t)__ldg(p + x0 + j) << (8 * j);
+    return w;
+}
+
+// Step A for one point: the equal-q neighbour mask (bits z-, z+, y-, y+, x-,
+// x+; absent axes count as equal), whether it is a boundary, its sign code.
+template <int RANK, bool WIDE>
+__device__ __forceinline__ void detect_point(int q0, int zl, int zr, int yl, int yr, int xl, int xr,
+                                             bool inner, const MethodArgs& m, unsigned& mask,
+                                             bool& site, int& code)
+{
+    mask = (unsigned)(xl == q0) << 4 | (unsigned)(xr == q0) << 5;
+    if (RANK >= 2) mask |= (unsigned)(yl == q0) << 2 | (unsigned)(yr == q0) << 3;
+    else mask |= 0xCu;
+    if (RANK >= 3) mask |= (unsigned)(zl == q0) | (unsigned)(zr == q0) << 1;
+    else mask |= 0x3u;
+    site = inner && mask != 0x3Fu;
+    int sg, first = 0;
+    bool fast;
+    if (!WIDE) {
+        int sum = (xl - q0) + (xr - q0);
+        const unsigned thm1 = (unsigned)m.grad_threshold - 1u, lim = 2u * thm1;
+        fast = (unsigned)(xr - xl + (int)thm1) > lim;
+        if (RANK >= 2) { sum += (yl - q0) + (yr - q0); fast |= (unsigned)(yr - yl + (int)thm1) > lim; }
+        if (RANK >= 3) { sum += (zl - q0) + (zr - q0); fast |= (unsigned)(zr - zl + (int)thm1) > lim; }
+        sg = (sum > 0) - (sum < 0);
+        if (m.sign_rule == 1) {
+            // first differing neighbour in the order z-, z+, y-, y+, x-, x+
+            first = xr != q0 ? (xr > q0 ? 1 : -1) : 0;
+            first = xl != q0 ? (xl > q0 ? 1 : -1) : first;
+            if (RANK >= 2) {
+                first = yr != q0 ? (yr > q0 ? 1 : -1) : first;
+                first = yl != q0 ? (yl > q0 ? 1 : -1) : first;
+            }
+            if (RANK >= 3) {
+                first = zr != q0 ? (zr > q0 ? 1 : -1) : first;
+                first = zl != q0 ? (zl > q0 ? 1 : -1) : first;
+            }
+        }
+    } else {
+        const int64_t Q = q0;
+        int64_t sum = ((int64_t)xl - Q) + ((int64_t)xr - Q);
+        auto gr = [&](int lo, int hi) {
+            int64_t g = (int64_t)hi - lo;
+            return (g < 0 ? -g : g) >= (int64_t)m.grad_threshold;
+        };
+        fast = gr(xl, xr);
+        if (RANK >= 2) { sum += ((int64_t)yl - Q) + ((int64_t)yr - Q); fast |= gr(yl, yr); }
+        if (RANK >= 3) { sum += ((int64_t)zl - Q) + ((int64_t)zr - Q); fast |= gr(zl, zr); }
+        sg = (sum > 0) - (sum < 0);
+        if (m.sign_rule == 1) {
+            first = xr != q0 ? (xr > q0 ? 1 : -1) : 0;
+            first = xl != q0 ? (xl > q0 ? 1 : -1) : first;
+            if (RANK >= 2) {
+                first = yr != q0 ? (yr > q0 ? 1 : -1) : first;
+                first = yl != q0 ? (yl > q0 ? 1 : -1) : first;
+            }
+            if (RANK >= 3) {
+                first = zr != q0 ? (zr > q0 ? 1 : -1) : first;
+                first = zl != q0 ? (zl > q0 ? 1 : -1) : first;
+            }
+        }
+    }
+    if (m.sign_rule == 1) sg = first;
+    code = (site && !fast) ? sign_code(sg) : 0;
+}
+
+// The common case of detect_point: sign rule SUM and every |q| < 2^27, so
+// that the sum of the neighbour differences fits 32 bits.
+template <int RANK>
+__device__ __forceinline__ void detect_sum32(int q0, int zl, int zr, int yl, int yr, int xl, int xr,
+                                             bool inner, int thm1, unsigned lim, unsigned& mask,
+                                             unsigned& site, unsigned& code)
+{
+    unsigned mk = (xl == q0 ? 0x10u : 0u) | (xr == q0 ? 0x20u : 0u);
+    int sum = xl + xr;
+    bool fast = (unsigned)(xr - xl + thm1) > lim;
+    if (RANK >= 2) {
+        mk |= (yl == q0 ? 0x4u : 0u) | (yr == q0 ? 0x8u : 0u);
+        sum += yl + yr;
+        fast |= (unsigned)(yr - yl + thm1) > lim;
+    } else {
+        mk |= 0xCu;
+    }
+    if (RANK >= 3) {
+        mk |= (zl == q0 ? 0x1u : 0u) | (zr == q0 ? 0x2u : 0u);
+        sum += zl + zr;
+        fast |= (unsigned)(zr - zl + thm1) > lim;
+    } else {
+        mk |= 0x3u;
+    }
+    sum -= 2 * RANK * q0;
+    const bool s = inner && mk != 0x3Fu;
+    const unsigned cd = sum > 0 ? 1u : (sum < 0 ? 2u : 0u);
+    code = (s && !fast) ? cd : 0u;
+    site = s ? 1u : 0u;
+    mask = mk;
+}
+
+template <int PHASE, int RANK, bool FINAL, bool DEBUG, bool VEC>
 __global__ void __launch_bounds__(256) k_rowpass(RowArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -31,168 +182,292 @@ __global__ void __launch_bounds__(256) k_rowpass(RowArgs a)
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     const int nx = a.nx;
-    const int nxp = (nx + 31) & ~31;
-    uint16_t* left = reinterpret_cast<uint16_t*>(smem) + warp * nxp;
-    uint8_t* site = reinterpret_cast<uint8_t*>(reinterpret_cast<uint16_t*>(smem) + nwarps * nxp) +
-                    warp * nxp;
-
+    const int nseg = (nx + kSeg - 1) / kSeg;
+    RowSmem sm;
+    {
+        unsigned char* base = smem + (size_t)warp * smem_per_warp(nx);
+        sm.sfirst = reinterpret_cast<int*>(base);
+        sm.slast = sm.sfirst + nseg;
+        sm.nextr = sm.slast + nseg;
+        sm.info = reinterpret_cast<uint16_t*>(sm.nextr + nseg);
+    }
     const int row = blockIdx.x * nwarps + warp;
     if (row >= a.nz * a.ny) return;  // whole warp leaves; only warp-level sync below
     const int z = row / a.ny;
     const int y = row - z * a.ny;
-    const int base = row * nx;
+    const int rbase = row * nx;
     const int plane = a.ny * nx;
     bool row_inner = true;
-    if (a.rank >= 2) row_inner = (y >= 1 && y <= a.ny - 2);
-    if (a.rank >= 3) row_inner = row_inner && (z >= 1 && z <= a.nz - 2);
+    if (RANK >= 2) row_inner = (y >= 1 && y <= a.ny - 2);
+    if (RANK >= 3) row_inner = row_inner && (z >= 1 && z <= a.nz - 2);
 
-    // ---- sweep 1: site detection ------------------------------------------
-    for (int x0 = 0; x0 < nx; x0 += 32) {
-        const int x = x0 + lane;
-        if (x >= nx) continue;
-        const int i = base + x;
-        const bool inner = row_inner && x >= 1 && x <= nx - 2;
-        uint8_t f = 0;
+    // ---- sweep A: sites of each segment ------------------------------------
+    int carry_prev = 0;  // value left of the segment (phase 1: q, phase 2: S byte)
+    for (int seg = 0; seg < nseg; ++seg) {
+        const int x0 = seg * kSeg + 4 * lane;
+        unsigned nib = 0, codes = 0;
         if (PHASE == 1) {
-            uint8_t mask = 0;
-            if (inner) {
-                const int32_t q0 = a.q[i];
-                int64_t sum = 0;
-                int first = 0;
-                bool differs = false, fast = false;
-                // neighbours in the order z-, z+, y-, y+, x-, x+ (mask bits 0..5)
-                auto visit = [&](int32_t lo, int32_t hi, int bit) {
-                    const int64_t dl = (int64_t)lo - q0, dh = (int64_t)hi - q0;
-                    if (dl == 0) mask |= (uint8_t)(1u << bit);
-                    else { differs = true; if (!first) first = dl > 0 ? 1 : -1; }
-                    if (dh == 0) mask |= (uint8_t)(1u << (bit + 1));
-                    else { differs = true; if (!first) first = dh > 0 ? 1 : -1; }
-                    sum += dl + dh;
-                    int64_t g = (int64_t)hi - lo;
-                    g = g < 0 ? -g : g;
-                    if (g >= a.m.grad_threshold) fast = true;
-                };
-                if (a.rank >= 3) visit(a.q[i - plane], a.q[i + plane], 0);
-                if (a.rank >= 2) visit(a.q[i - nx], a.q[i + nx], 2);
-                visit(a.q[i - 1], a.q[i + 1], 4);
-                if (differs) {
-                    int sg = a.m.sign_rule == 1 ? first : (sum > 0) - (sum < 0);
-                    if (fast) sg = 0;
-                    f = (uint8_t)(1u | (sign_code(sg) << 1));
+            int c[4], yl[4] = {0, 0, 0, 0}, yr[4] = {0, 0, 0, 0}, zl[4] = {0, 0, 0, 0},
+                      zr[4] = {0, 0, 0, 0};
+            load4_i32(a.q + rbase, x0, nx, VEC, c);
+            int xm = __shfl_up_sync(kFull, c[3], 1);
+            int xp = __shfl_down_sync(kFull, c[0], 1);
+            const int last_c3 = __shfl_sync(kFull, c[3], 31);
+            if (lane == 0) xm = carry_prev;
+            if (lane == 31) xp = (x0 + 4 < nx) ? __ldg(a.q + rbase + x0 + 4) : 0;
+            carry_prev = last_c3;
+            unsigned eq = 0;
+            if (row_inner) {
+                if (RANK >= 2) {
+                    load4_i32(a.q + rbase - nx, x0, nx, VEC, yl);
+                    load4_i32(a.q + rbase + nx, x0, nx, VEC, yr);
+                }
+                if (RANK >= 3) {
+                    load4_i32(a.q + rbase - plane, x0, nx, VEC, zl);
+                    load4_i32(a.q + rbase + plane, x0, nx, VEC, zr);
+                }
+                // 32-bit arithmetic is exact while every |q| < 2^27
+                unsigned acc = (unsigned)(xm ^ (xm >> 31)) | (unsigned)(xp ^ (xp >> 31));
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    acc |= (unsigned)(c[j] ^ (c[j] >> 31)) | (unsigned)(yl[j] ^ (yl[j] >> 31)) |
+                           (unsigned)(yr[j] ^ (yr[j] >> 31)) | (unsigned)(zl[j] ^ (zl[j] >> 31)) |
+                           (unsigned)(zr[j] ^ (zr[j] >> 31));
+                }
+                const bool wide = __any_sync(kFull, acc >= (1u << 27));
+                if (!wide && a.m.sign_rule == 0) {
+                    const int thm1 = a.m.grad_threshold - 1;
+                    const unsigned lim = 2u * (unsigned)thm1;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int x = x0 + j;
+                        const bool inner = x >= 1 && x <= nx - 2;
+                        unsigned mk, st, cd;
+                        detect_sum32<RANK>(c[j], zl[j], zr[j], yl[j], yr[j], j == 0 ? xm : c[j - 1],
+                                           j == 3 ? xp : c[j + 1], inner, thm1, lim, mk, st, cd);
+                        eq |= mk << (8 * j);
+                        nib |= st << j;
+                        codes |= cd << (2 * j);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int x = x0 + j;
+                        const bool inner = x >= 1 && x <= nx - 2;
+                        const int l = j == 0 ? xm : c[j - 1];
+                        const int r = j == 3 ? xp : c[j + 1];
+                        unsigned mk;
+                        bool site;
+                        int code;
+                        if (!wide)
+                            detect_point<RANK, false>(c[j], zl[j], zr[j], yl[j], yr[j], l, r, inner, a.m, mk, site, code);
+                        else
+                            detect_point<RANK, true>(c[j], zl[j], zr[j], yl[j], yr[j], l, r, inner, a.m, mk, site, code);
+                        eq |= mk << (8 * j);
+                        nib |= (unsigned)site << j;
+                        codes |= (unsigned)code << (2 * j);
+                    }
+                }
+                if (VEC) {
+                    if (x0 < nx) *reinterpret_cast<uint32_t*>(a.eqm + rbase + x0) = eq;
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (x0 + j < nx) a.eqm[rbase + x0 + j] = (uint8_t)(eq >> (8 * j));
                 }
             }
-            a.eqm[i] = mask;
-            if (a.dbg_b1) a.dbg_b1[i] = f & 1u;
-            if (a.dbg_sb) a.dbg_sb[i] = (int8_t)sign_of_code(f >> 1);
+            if (DEBUG) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (x0 + j >= nx) continue;
+                    if (a.dbg_b1) a.dbg_b1[rbase + x0 + j] = (nib >> j) & 1u;
+                    if (a.dbg_sb) a.dbg_sb[rbase + x0 + j] = (int8_t)sign_of_code((codes >> (2 * j)) & 3u);
+                }
+            }
         } else {
-            if (inner) {
-                const int s0 = a.s_in[i];
-                const unsigned mask = a.eqm[i];
+            // GetBoundary(S): B2 where an axis neighbour (with the same q under
+            // SAME_Q) has a different S; four points per 32-bit word.
+            const uint32_t cw = load4_u8(a.s_in + rbase, x0, nx, VEC);
+            uint32_t xmw = __shfl_up_sync(kFull, cw, 1);
+            uint32_t xpw = __shfl_down_sync(kFull, cw, 1);
+            const uint32_t last_w = __shfl_sync(kFull, cw, 31);
+            if (lane == 0) xmw = (uint32_t)carry_prev;
+            if (lane == 31) xpw = (x0 + 4 < nx) ? (uint32_t)__ldg(reinterpret_cast<const uint8_t*>(a.s_in) + rbase + x0 + 4) : 0u;
+            carry_prev = (int)last_w;
+            if (row_inner) {
+                const uint32_t eqw = load4_u8(a.eqm + rbase, x0, nx, VEC);
                 const bool literal = a.m.b2_rule == 1;
-                bool b2 = false;
-                auto check = [&](int sn, int bit) {
-                    if ((literal || ((mask >> bit) & 1u)) && sn != s0) b2 = true;
+                // byte k of sel(bit) = 0xFF if bit `bit` of eqm byte k is set
+                auto sel = [&](int bit) -> uint32_t {
+                    return literal ? 0xFFFFFFFFu : __vcmpne4(eqw & (0x01010101u << bit), 0u);
                 };
-                if (a.rank >= 3) { check(a.s_in[i - plane], 0); check(a.s_in[i + plane], 1); }
-                if (a.rank >= 2) { check(a.s_in[i - nx], 2); check(a.s_in[i + nx], 3); }
-                check(a.s_in[i - 1], 4);
-                check(a.s_in[i + 1], 5);
-                f = b2 ? 1 : 0;
+                uint32_t b2 = (__vcmpne4(__byte_perm(xmw, cw, 0x6543), cw) & sel(4)) |
+                              (__vcmpne4(__byte_perm(cw, xpw, 0x4321), cw) & sel(5));
+                if (RANK >= 2) {
+                    b2 |= (__vcmpne4(load4_u8(a.s_in + rbase - nx, x0, nx, VEC), cw) & sel(2)) |
+                          (__vcmpne4(load4_u8(a.s_in + rbase + nx, x0, nx, VEC), cw) & sel(3));
+                }
+                if (RANK >= 3) {
+                    b2 |= (__vcmpne4(load4_u8(a.s_in + rbase - plane, x0, nx, VEC), cw) & sel(0)) |
+                          (__vcmpne4(load4_u8(a.s_in + rbase + plane, x0, nx, VEC), cw) & sel(1));
+                }
+                // gather the top bit of each byte into a nibble
+                nib = ((b2 & 0x80808080u) * 0x00204081u) >> 28;
+                // interior along x
+                if (x0 == 0) nib &= ~1u;
+                if (x0 + 4 > nx - 1) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (x0 + j > nx - 2) nib &= ~(1u << j);
+                }
             }
-            if (a.dbg_b2) a.dbg_b2[i] = f;
+            if (DEBUG && a.dbg_b2) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (x0 + j < nx) a.dbg_b2[rbase + x0 + j] = (nib >> j) & 1u;
+            }
         }
-        site[x] = f;
+        sm.info[seg * 32 + lane] = (uint16_t)(nib | (codes << 4));
+        const unsigned H = __ballot_sync(kFull, nib != 0);
+        const int my_first = nib ? make_ref(x0 + __ffs(nib) - 1, (codes >> (2 * (__ffs(nib) - 1))) & 3u) : 0;
+        const int my_last = nib ? make_ref(x0 + 31 - __clz(nib), (codes >> (2 * (31 - __clz(nib)))) & 3u) : 0;
+        const int f = __shfl_sync(kFull, my_first, H ? __ffs(H) - 1 : 0);
+        const int l = __shfl_sync(kFull, my_last, H ? 31 - __clz(H) : 0);
+        if (lane == 0) {
+            sm.sfirst[seg] = H ? f : kNoRef;
+            sm.slast[seg] = H ? l : kNoRef;
+        }
+    }
+    __syncwarp();
+    if (lane == 0) {
+        int nxt = kNoRef;
+        for (int seg = nseg - 1; seg >= 0; --seg) {
+            sm.nextr[seg] = nxt;
+            if (sm.sfirst[seg] != kNoRef) nxt = sm.sfirst[seg];
+        }
     }
     __syncwarp();
 
-    // ---- sweep 2: nearest site at or left of x -----------------------------
-    int carry = -1;
-    for (int x0 = 0; x0 < nx; x0 += 32) {
-        const int x = x0 + lane;
-        int v = (x < nx && (site[x] & 1u)) ? x : -1;
+    // ---- sweep B: nearest site on both sides; emit -------------------------
+    const unsigned lt = (1u << lane) - 1u;
+    const unsigned gt = ~((2u << lane) - 1u);
+    int carry_l = kNoRef;
+    for (int seg = 0; seg < nseg; ++seg) {
+        const int x0 = seg * kSeg + 4 * lane;
+        const unsigned v = sm.info[seg * 32 + lane];
+        const unsigned nib = v & 15u, codes = v >> 4;
+        const unsigned H = __ballot_sync(kFull, nib != 0);
+        const int my_first = nib ? make_ref(x0 + __ffs(nib) - 1, (codes >> (2 * (__ffs(nib) - 1))) & 3u) : 0;
+        const int my_last = nib ? make_ref(x0 + 31 - __clz(nib), (codes >> (2 * (31 - __clz(nib)))) & 3u) : 0;
+        const unsigned below = H & lt, above = H & gt;
+        const int lsrc = below ? 31 - __clz(below) : lane;
+        const int rsrc = above ? __ffs(above) - 1 : lane;
+        const int lv = __shfl_sync(kFull, my_last, lsrc);
+        const int rv = __shfl_sync(kFull, my_first, rsrc);
+        int lref = below ? lv : carry_l;
+        int rref = above ? rv : sm.nextr[seg];
+        if (H) carry_l = sm.slast[seg];
+        // chains over the lane's own four points
+        int L[4], R[4];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(kFull, v, o);
-            if (lane >= o) v = max(v, t);
+        for (int j = 0; j < 4; ++j) {
+            if ((nib >> j) & 1u) lref = make_ref(x0 + j, (codes >> (2 * j)) & 3u);
+            L[j] = lref;
         }
-        v = max(v, carry);
-        if (x < nx) left[x] = v < 0 ? kInf16 : (uint16_t)v;
-        carry = __shfl_sync(kFull, v, 31);
+#pragma unroll
+        for (int j = 3; j >= 0; --j) {
+            if ((nib >> j) & 1u) rref = make_ref(x0 + j, (codes >> (2 * j)) & 3u);
+            R[j] = rref;
+        }
+        uint32_t packed[2] = {0u, 0u};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int x = x0 + j;
+            const int lp = L[j] == kNoRef ? kNoneL : (L[j] >> 2);
+            const int rp = R[j] == kNoRef ? kNoneR : (R[j] >> 2);
+            const int dl = x - lp, dr = rp - x;
+            const bool left = dl <= dr;
+            const int d = left ? dl : dr;
+            const int ref = left ? L[j] : R[j];
+            const bool valid = d < (1 << 19);
+            const int code = ref & 3;
+            if (PHASE == 1) {
+                if (!FINAL) {
+                    const uint32_t w = valid ? (uint32_t)((d << 2) | code) : kInf16;
+                    packed[j >> 1] |= w << (16 * (j & 1));
+                } else if (x < nx) {
+                    a.dist1[rbase + x] = valid ? d * d : kDistInf;
+                    a.s_out[rbase + x] = (int8_t)sign_of_code(valid ? code : 0);
+                }
+                if (DEBUG && a.dbg_idx && x < nx) a.dbg_idx[rbase + x] = valid ? rbase + (ref >> 2) : -1;
+            } else {
+                if (!FINAL) {
+                    const uint32_t w = valid ? (uint32_t)d : kInf16;
+                    packed[j >> 1] |= w << (16 * (j & 1));
+                } else if (x < nx) {
+                    const int32_t d2 = valid ? d * d : kDistInf;
+                    a.out[rbase + x] = compensate(a.q[rbase + x], a.dist1_in[rbase + x], d2,
+                                                  a.s_in[rbase + x], a.m);
+                    if (DEBUG && a.dbg_dist2) a.dbg_dist2[rbase + x] = d2;
+                }
+            }
+        }
+        if (!FINAL) {
+            if (VEC) {
+                if (x0 < nx) *reinterpret_cast<uint2*>(a.xw + rbase + x0) = make_uint2(packed[0], packed[1]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (x0 + j < nx) a.xw[rbase + x0 + j] = (uint16_t)(packed[j >> 1] >> (16 * (j & 1)));
+            }
+        }
     }
-    __syncwarp();
+}
 
-    // ---- sweep 3: nearest site at or right of x; emit ----------------------
-    constexpr int kBig = 0x7FFFFFFF;
-    carry = kBig;
-    for (int x0 = (nx - 1) & ~31; x0 >= 0; x0 -= 32) {
-        const int x = x0 + lane;
-        int v = (x < nx && (site[x] & 1u)) ? x : kBig;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_down_sync(kFull, v, o);
-            if (lane + o < 32) v = min(v, t);
-        }
-        v = min(v, carry);
-        carry = __shfl_sync(kFull, v, 0);
-        if (x >= nx) continue;
-        const int i = base + x;
-        const int lft = left[x];
-        const int dl = lft != kInf16 ? x - lft : kBig;
-        const int dr = v != kBig ? v - x : kBig;
-        const bool valid = dl != kBig || dr != kBig;
-        const int s = dl <= dr ? lft : v;   // tie -> left (smaller index)
-        const int d = dl <= dr ? dl : dr;
-        if (PHASE == 1) {
-            const int code = valid ? (site[s] >> 1) & 3 : 0;
-            if (!FINAL) {
-                a.xw[i] = valid ? (uint16_t)((d << 2) | code) : kInf16;
-            } else {
-                a.dist1[i] = valid ? d * d : kDistInf;
-                a.s_out[i] = (int8_t)sign_of_code(code);
-            }
-            if (a.dbg_idx) a.dbg_idx[i] = valid ? base + s : -1;
-        } else {
-            if (!FINAL) {
-                a.xw[i] = valid ? (uint16_t)d : kInf16;
-            } else {
-                const int32_t d2 = valid ? d * d : kDistInf;
-                a.out[i] = compensate(a.q[i], a.dist1_in[i], d2, a.s_in[i], a.m);
-                if (a.dbg_dist2) a.dbg_dist2[i] = d2;
-            }
-        }
-    }
+template <int PHASE, int RANK, bool FINAL>
+cudaError_t go(const RowArgs& a, bool debug, bool vec, dim3 grid, dim3 block, size_t smem,
+               cudaStream_t st)
+{
+    auto run = [&](auto kern) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<grid, block, smem, st>>>(a);
+        return cudaGetLastError();
+    };
+    if (debug) return vec ? run(k_rowpass<PHASE, RANK, FINAL, true, true>)
+                          : run(k_rowpass<PHASE, RANK, FINAL, true, false>);
+    return vec ? run(k_rowpass<PHASE, RANK, FINAL, false, true>)
+               : run(k_rowpass<PHASE, RANK, FINAL, false, false>);
 }
 
 }  // namespace
 
 int rowpass_warps(int nx)
 {
-    const int nxp = (nx + 31) & ~31;
-    int w = (200 * 1024) / (3 * nxp);
+    const size_t per = smem_per_warp(nx);
+    int w = (int)((96 * 1024) / per);
     return w < 1 ? 1 : (w > 8 ? 8 : w);
 }
 
-size_t rowpass_smem(int nx, int warps)
-{
-    const size_t nxp = (size_t)((nx + 31) & ~31);
-    return (size_t)warps * nxp * 3;
-}
+size_t rowpass_smem(int nx, int warps) { return (size_t)warps * smem_per_warp(nx); }
 
-cudaError_t launch_rowpass(int phase, bool final_pass, const RowArgs& a, cudaStream_t st)
+cudaError_t launch_rowpass(int phase, bool final_pass, const RowArgs& a, bool debug, cudaStream_t st)
 {
     const int warps = rowpass_warps(a.nx);
     const size_t smem = rowpass_smem(a.nx, warps);
     const int rows = a.nz * a.ny;
     const dim3 grid((rows + warps - 1) / warps), block(32 * warps);
-    auto go = [&](auto kern) -> cudaError_t {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        kern<<<grid, block, smem, st>>>(a);
-        return cudaGetLastError();
-    };
-    if (phase == 1) return final_pass ? go(k_rowpass<1, true>) : go(k_rowpass<1, false>);
-    return final_pass ? go(k_rowpass<2, true>) : go(k_rowpass<2, false>);
+    // 128-bit / 32-bit accesses need 4 | nx and 16-byte aligned base pointers
+    auto al = [](const void* p, int b) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) % b) == 0; };
+    const bool vec = (a.nx % 4 == 0) && al(a.q, 16) && al(a.eqm, 4) && al(a.s_in, 4) && al(a.xw, 8);
+    if (phase == 1) {
+        if (final_pass) return go<1, 1, true>(a, debug, vec, grid, block, smem, st);
+        if (a.rank == 2) return go<1, 2, false>(a, debug, vec, grid, block, smem, st);
+        return go<1, 3, false>(a, debug, vec, grid, block, smem, st);
+    }
+    if (final_pass) return go<2, 1, true>(a, debug, vec, grid, block, smem, st);
+    if (a.rank == 2) return go<2, 2, false>(a, debug, vec, grid, block, smem, st);
+    return go<2, 3, false>(a, debug, vec, grid, block, smem, st);
 }
 
 }  // namespace qai

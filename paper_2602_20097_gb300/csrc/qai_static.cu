@@ -6,7 +6,7 @@
 #include <cstdio>
 #include <mutex>
 
-#include "../../include/qai.h"
+#include "qai.h"
 #include "qai_launch.h"
 
 namespace {
