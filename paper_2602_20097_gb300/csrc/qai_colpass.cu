@@ -33,7 +33,7 @@ namespace qai {
 namespace {
 
 constexpr int kMaxBands = 32;
-constexpr int kWinMaxG = 24;   // outward-scan fast path: every finite g <= 24
+constexpr int kScanMax = 5;    // outward-scan fast path: rows settled within 5 rows
 
 template <int PHASE, int IN>
 __device__ __forceinline__ int gval(uint32_t w)
@@ -110,7 +110,8 @@ __global__ void __launch_bounds__(512, IN == 2 ? 3 : 2) k_colpass(ColArgs a)
     uint16_t* segA = stk + (size_t)L * W;                               // [B][W] kept range of each band
     uint16_t* segE = segA + B * W;                                      // [B][W]
     uint16_t* lstb = segE + B * W;                                      // [B][W] bands of the envelope, in order
-    uint16_t* nlst = lstb + B * W;                                      // [W] number of such bands
+    uint16_t* lmap = lstb + B * W;                                      // [B][W] band -> its position in lst
+    uint16_t* nlst = lmap + B * W;                                      // [W] number of such bands
 
     const int tiles_per_plane = (a.C + W - 1) / W;
     const int p = blockIdx.x / tiles_per_plane;
@@ -119,8 +120,8 @@ __global__ void __launch_bounds__(512, IN == 2 ? 3 : 2) k_colpass(ColArgs a)
     const int RS = a.row_stride;
     const Word* in = static_cast<const Word*>(a.in);
 
-    __shared__ int s_gmax;  // largest g of the tile (the fast-path test below)
-    if (tid == 0) s_gmax = 0;
+    __shared__ int s_fail;  // the fast path below could not settle a row
+    if (tid == 0) s_fail = 0;
 
     // ---- stage the tile ----------------------------------------------------
     {
@@ -161,33 +162,18 @@ __global__ void __launch_bounds__(512, IN == 2 ? 3 : 2) k_colpass(ColArgs a)
     // an outward scan r, r-1, r+1, r-2, r+2, ... can stop at the first k with
     // k^2 > best. Taking r - k on ties (<=) and r + k only when strictly lower
     // returns exactly Algorithm 1's answer (the smallest r' among equal minima).
-    // The scan is short when every finite g in the tile is at most kWinMaxG
-    // and no column has three INF rows in a row (an INF row then lies within
-    // two rows of a finite one); otherwise the tile takes the envelope path.
+    // The scan is tried first with k <= kScanMax: a row is settled when its
+    // best is below (kScanMax + 1)^2, since no farther row can reach that. If
+    // any row of the tile is not settled, the whole tile takes the envelope
+    // path below, which rewrites every output of the tile (same rows per thread).
     {
-        int gm = 0;
+        volatile int* vfail = &s_fail;  // any thread of the tile failed: all stop
         if (c < a.C) {
-            int run = 0;
-            for (int r = max(0, r0 - 2); r < r1; ++r) {
-                const Word w = tcol[r * W];
-                if (w == kWInf) {
-                    if (++run >= 3 && r >= r0) gm = 0x7FFFFFFF;
-                } else {
-                    run = 0;
-                    if (r >= r0) gm = max(gm, gval<PHASE, IN>(w));
-                }
-            }
-        }
-        if (gm > kWinMaxG) atomicMax(&s_gmax, gm);
-        __syncthreads();
-        if (s_gmax <= kWinMaxG) {
-            if (c >= a.C) return;
-            for (int r = r0; r < r1; ++r) {
-                // k = 0
+            for (int r = r0; r < r1 && !*vfail; ++r) {
                 Word bw = tcol[r * W];
                 int bh = bw != kWInf ? r : -1;
                 int best = bw != kWInf ? gval<PHASE, IN>(bw) : 0x7FFFFFFF;
-                for (int k = 1; k < L && k * k <= best; ++k) {
+                for (int k = 1; k <= kScanMax && k * k <= best; ++k) {
                     if (r - k >= 0) {
                         const Word w = tcol[(r - k) * W];
                         const int v = gval<PHASE, IN>(w) + k * k;
@@ -199,11 +185,15 @@ __global__ void __launch_bounds__(512, IN == 2 ? 3 : 2) k_colpass(ColArgs a)
                         if (w != kWInf && v < best) { best = v; bh = r + k; bw = w; }
                     }
                 }
-                emit_point<PHASE, IN, FINAL, DEBUG>(a, pbase + r * RS + c, pbase + max(bh, 0) * RS + c,
-                                                    best, bw, bh >= 0);
+                if (best >= (kScanMax + 1) * (kScanMax + 1)) {
+                    *vfail = 1;
+                    break;
+                }
+                emit_point<PHASE, IN, FINAL, DEBUG>(a, pbase + r * RS + c, pbase + bh * RS + c, best, bw, true);
             }
-            return;
         }
+        __syncthreads();
+        if (!s_fail) return;
     }
 
     // ---- build: Algorithm 1's envelope over this band ------------------------
@@ -313,11 +303,14 @@ __global__ void __launch_bounds__(512, IN == 2 ? 3 : 2) k_colpass(ColArgs a)
         }
         __syncthreads();
     }
-    if (band == 0) {  // the envelope's bands, in order
+    if (band == 0) {  // the envelope's bands, in order; each band's first entry in lst at or after it
         uint16_t* lst = lstb + col;
         int nl = 0;
-        for (int k = 0; k < B; ++k)
+        for (int k = 0; k < B; ++k) {
+            lmap[k * W + col] = (uint16_t)nl;
             if (segA[k * W + col] != segE[k * W + col]) lst[(nl++) * W] = (uint16_t)k;
+        }
+        for (int k = B - 1; k >= 0 && lmap[k * W + col] >= nl; --k) lmap[k * W + col] = (uint16_t)(nl > 0 ? nl - 1 : 0);
         nlst[col] = (uint16_t)nl;
     }
     __syncthreads();
@@ -333,31 +326,48 @@ __global__ void __launch_bounds__(512, IN == 2 ? 3 : 2) k_colpass(ColArgs a)
             emit_point<PHASE, IN, FINAL, DEBUG>(a, pbase + r * RS + c, 0, 0, (Word)0, false);
         return;
     }
-    auto val_at = [&](int pos, int r) {
-        const int hh = scol[pos * W];
+    // envelope entry of row r0: the first entry that the next one does not
+    // beat at r0 (the minimiser's index never decreases with the row). Start
+    // at this band's first kept entry (or the last entry before it) and step
+    // left or right; the entry is rarely more than a band away.
+    int li = lmap[band * W + col];
+    int k = lst[li * W];
+    int pos = k >= band ? segA[k * W + col] : segE[k * W + col] - 1;
+    auto val_at = [&](int ps, int r) {
+        const int hh = scol[ps * W];
         return gat(hh) + (hh - r) * (hh - r);
     };
-    // envelope entry of row r0: the first entry that the next one does not
-    // beat at r0 (the minimiser's index never decreases with the row); first
-    // the band that holds it, then the entry inside that band
-    int lo = 0, hi = nl - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        const int kl = lst[mid * W], kr = lst[(mid + 1) * W];
-        if (val_at(segE[kl * W + col] - 1, r0) > val_at(segA[kr * W + col], r0)) lo = mid + 1;
-        else hi = mid;
+    auto next_of = [&](int l, int ps, int& ln, int& pn) {  // pn < 0: none
+        ln = l;
+        pn = ps + 1;
+        if (pn >= segE[lst[l * W] * W + col]) pn = l + 1 < nl ? segA[lst[(++ln) * W] * W + col] : -1;
+    };
+    auto prev_of = [&](int l, int ps, int& lp, int& pp) {  // pp < 0: none
+        lp = l;
+        pp = ps - 1;
+        if (pp < segA[lst[l * W] * W + col]) pp = l > 0 ? segE[lst[(--lp) * W] * W + col] - 1 : -1;
+    };
+    {
+        int ln, pn;
+        next_of(li, pos, ln, pn);
+        if (pn >= 0 && val_at(pos, r0) > val_at(pn, r0)) {
+            do {  // move right while the next entry is strictly lower
+                li = ln;
+                pos = pn;
+                next_of(li, pos, ln, pn);
+            } while (pn >= 0 && val_at(pos, r0) > val_at(pn, r0));
+        } else {
+            int lp, pp;
+            prev_of(li, pos, lp, pp);
+            while (pp >= 0 && !(val_at(pp, r0) > val_at(pos, r0))) {  // move left
+                li = lp;
+                pos = pp;
+                prev_of(li, pos, lp, pp);
+            }
+        }
     }
-    int li = lo;
-    int k = lst[li * W];
+    k = lst[li * W];
     int endk = segE[k * W + col];
-    lo = segA[k * W + col];
-    hi = endk - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (val_at(mid, r0) > val_at(mid + 1, r0)) lo = mid + 1;
-        else hi = mid;
-    }
-    int pos = lo;
     int h = scol[pos * W];
     Word w = tcol[h * W];
     int g = gval<PHASE, IN>(w);
@@ -450,7 +460,7 @@ bool choose_colpass(int L, int in_bytes, ColConfig* cfg)
     if (B > L) B = L < 1 ? 1 : L;
     const size_t budget = 200 * 1024;
     for (int W = max_w; W >= 4; W >>= 1) {
-        const size_t smem = (size_t)L * W * (in_bytes + 2) + (size_t)3 * B * W * 2 + (size_t)W * 2;
+        const size_t smem = (size_t)L * W * (in_bytes + 2) + (size_t)4 * B * W * 2 + (size_t)W * 2;
         if (smem <= budget) {
             cfg->W = W;
             cfg->B = B;

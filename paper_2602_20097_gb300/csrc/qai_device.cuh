@@ -131,7 +131,8 @@ __device__ __forceinline__ float compensate(int32_t q, int32_t d1, int32_t d2, i
     w = d2 == kDistInf ? 1.0f : w;
     w = d2 == 0 ? 0.0f : w;
     w = d1 == 0 ? 1.0f : w;
-    return fmaf((float)q, m.two_eb, (float)s * w * m.eta_eb);
+    const float fs = s > 0 ? 1.0f : (s < 0 ? -1.0f : 0.0f);
+    return fmaf((float)q, m.two_eb, fs * w * m.eta_eb);
 }
 
 }  // namespace qai
