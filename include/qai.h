@@ -62,8 +62,10 @@ typedef struct {
     int32_t b2_rule;         /* Algorithm 3 GetBoundary(S): 0 = a neighbour with
                                 the same q and a different S (default);
                                 1 = any neighbour with a different S               */
-    uint32_t flags;          /* reserved, must be 0                                */
+    uint32_t flags;          /* 0, or QAI_FLAG_OUTPUT_C                            */
 } qai_params;
+
+#define QAI_FLAG_OUTPUT_C 1u  /* write the compensation C (step E) instead of D''  */
 
 /* Optional per-step outputs of Algorithm 4 (debug and parity checking).
  * Each pointer is a device array of N elements, or NULL to skip it.
@@ -120,6 +122,47 @@ qai_status qai_workspace_size_host(int rank, const int64_t* dims, size_t* bytes)
 qai_status qai_mitigate_host(const int32_t* h_q, float* h_out, int rank, const int64_t* dims,
                              double eb, const qai_params* params, void* d_ws, size_t ws_bytes,
                              cudaStream_t stream);
+
+/* ---- Adjoint of step E (no counterpart in the paper) ----------------------
+ * With the EDT assignment held fixed (Dist1, Dist2 and S as Algorithm 4
+ * computes them), D'' = D' + S w eta eps is linear in D' and eta; for a loss
+ * L with G = dL/dD'':
+ *   dL/dD' = G,  dL/deta = sum G S w eps,
+ *   dL/dp  = sum G S eta eps w (1 - w) (ln k2 - ln k1),  w = 1/(1 + (k1/k2)^p)
+ * (dw/dp = 0 where k1 = 0, k2 = 0 or no B2 exists). Stored mode keeps Dist1,
+ * Dist2 and S from the forward (9 bytes per point); recompute mode re-runs the
+ * forward pipeline in the backward call and keeps nothing in between. */
+
+/* Bytes of the saved state of the stored mode (256-byte aligned buffer). */
+qai_status qai_saved_size(int rank, const int64_t* dims, size_t* bytes);
+
+/* qai_mitigate that also fills d_saved (qai_saved_size bytes, device,
+ * 256-byte aligned) with Dist1, Dist2 and S for qai_mitigate_backward. */
+qai_status qai_mitigate_save(const int32_t* d_q, float* d_out, int rank, const int64_t* dims,
+                             double eb, const qai_params* params, void* d_saved, void* d_ws,
+                             size_t ws_bytes, cudaStream_t stream);
+
+/* Device workspace of qai_mitigate_backward: 32 KiB of block partial sums
+ * (stored mode), plus, with recompute != 0, the forward workspace and two
+ * field-sized arrays. */
+qai_status qai_workspace_size_backward(int rank, const int64_t* dims, int recompute, size_t* bytes);
+
+/* Adjoint of step E.
+ *  d_q            int32[N] indices the forward ran on, device
+ *  d_grad_out     float[N] G = dL/dD'', device
+ *  d_grad_dprime  float[N] receives dL/dD' (= G), device, or NULL
+ *  d_grad_params  double[2] receives (dL/deta, dL/dp), device
+ *  eb, params     as given to the forward
+ *  d_saved        the forward's saved state (stored mode), or NULL to
+ *                 recompute it from d_q
+ *  d_ws, ws_bytes qai_workspace_size_backward(rank, dims, d_saved == NULL)
+ *                 bytes, device, 256-byte aligned
+ * Sums run in fp32 with compensation, folded into FP64 in a fixed order (the
+ * same result on every run). Asynchronous on `stream` like every other call. */
+qai_status qai_mitigate_backward(const int32_t* d_q, const float* d_grad_out, float* d_grad_dprime,
+                                 double* d_grad_params, int rank, const int64_t* dims, double eb,
+                                 const qai_params* params, const void* d_saved, void* d_ws,
+                                 size_t ws_bytes, cudaStream_t stream);
 
 /* Largest field (points, after squeezing) that qai_mitigate_static accepts. */
 #define QAI_STATIC_MAX_POINTS 2097152

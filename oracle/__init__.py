@@ -13,6 +13,8 @@ Functions (numpy in, numpy out):
 * :func:`edt` -- exact squared EDT with the nearest-site linear index
   (Algorithm 1 along x, then y, then z).
 * :func:`boundary_and_sign` -- Algorithm 2 alone.
+* :func:`grad_params` -- adjoint of step E with respect to eta and the IDW
+  exponent p, the EDT assignment held fixed (no counterpart in the paper).
 """
 from __future__ import annotations
 
@@ -70,6 +72,9 @@ def _load():
                                                      ctypes.POINTER(_Params), P, P]
         lib.qai_oracle_boundary_and_sign.restype = None
         lib.qai_oracle_threads.restype = ctypes.c_int
+        lib.qai_oracle_grad_params.argtypes = [P, ctypes.c_int, P, ctypes.c_double,
+                                               ctypes.POINTER(_Params), P, P]
+        lib.qai_oracle_grad_params.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -120,6 +125,23 @@ def mitigate(q, eb, eta=0.9, idw_power=1.0, grad_threshold=2,
     if rc != 0:
         raise ValueError(f"oracle rejected the arguments (rc={rc})")
     return res
+
+
+def grad_params(q, eb, grad_out, eta=0.9, idw_power=1.0, grad_threshold=2,
+                sign_rule=SIGN_SUM, b2_rule=B2_SAME_Q):
+    """Adjoint of step E with the EDT assignment fixed: (dL/deta, dL/dp) for
+    dL/dD'' = grad_out (FP64). dL/dD' is grad_out itself."""
+    q = np.ascontiguousarray(q, dtype=np.int32)
+    g = np.ascontiguousarray(grad_out, dtype=np.float64)
+    if g.shape != q.shape:
+        raise ValueError("grad_out must have q's shape")
+    out = np.zeros(2, np.float64)
+    p = _params(eta, idw_power, grad_threshold, sign_rule, b2_rule)
+    rc = _load().qai_oracle_grad_params(_ptr(q), q.ndim, _ptr(_dims(q.shape)), float(eb),
+                                        ctypes.byref(p), _ptr(g), _ptr(out))
+    if rc != 0:
+        raise ValueError(f"oracle rejected the arguments (rc={rc})")
+    return float(out[0]), float(out[1])
 
 
 def edt(sites):

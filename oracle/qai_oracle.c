@@ -300,3 +300,42 @@ done:
     free(B1); free(SB); free(S); free(B2); free(D1); free(I1); free(D2); free(I2);
     return rc;
 }
+
+/* ---- Adjoint of step E (no counterpart in the paper) ---------------------
+ * With the EDT assignment held fixed (Dist1, Dist2, S from Algorithm 4),
+ * D'' = D' + S w(k1, k2; p) eta eps. For a loss L with dL/dD'' = G:
+ *   dL/deta = sum_i G_i S_i w_i eps
+ *   dL/dp   = sum_i G_i S_i eta eps dw_i/dp,
+ *   dw/dp   = w (1 - w) (ln k2 - ln k1) for finite k1, k2 > 0, else 0
+ * (w = 1 / (1 + (k1/k2)^p)). dL/dD' = G. FP64 throughout. */
+int qai_oracle_grad_params(const int32_t* Q, int rank, const int64_t* dims, double eb,
+                           const qai_oracle_params* p, const double* G, double* grad /*[2]*/)
+{
+    shape3 s;
+    if (make_shape(rank, dims, &s)) return -1;
+    size_t N = (size_t)s.N;
+    int32_t* d1 = (int32_t*)malloc(N * 4);
+    int32_t* d2 = (int32_t*)malloc(N * 4);
+    int8_t* S = (int8_t*)malloc(N);
+    int rc = 0;
+    if (!d1 || !d2 || !S) { rc = -2; goto done; }
+    rc = qai_oracle_mitigate(Q, rank, dims, eb, p, NULL, NULL, NULL, d1, NULL, S, NULL, d2, NULL);
+    if (rc) goto done;
+    double ge = 0.0, gp = 0.0;
+    for (int64_t i = 0; i < s.N; i++) {
+        if (S[i] == 0) continue;
+        int64_t a = d1[i] == INT32_MAX ? ORC_INF : d1[i];
+        int64_t b = d2[i] == INT32_MAX ? ORC_INF : d2[i];
+        double w = idw_weight(a, b, p->idw_power);
+        ge += G[i] * S[i] * w * eb;
+        if (a > 0 && b > 0 && a != ORC_INF && b != ORC_INF) {
+            double dw = w * (1.0 - w) * (0.5 * log((double)b) - 0.5 * log((double)a));
+            gp += G[i] * S[i] * p->eta * eb * dw;
+        }
+    }
+    grad[0] = ge;
+    grad[1] = gp;
+done:
+    free(d1); free(d2); free(S);
+    return rc;
+}

@@ -154,7 +154,7 @@ qai_status check_params(const qai_params* p)
     if (p->grad_threshold < 1) return fail(QAI_ERR_INVALID_ARG, "grad_threshold must be >= 1");
     if (p->sign_rule != 0 && p->sign_rule != 1) return fail(QAI_ERR_INVALID_ARG, "sign_rule must be 0 or 1");
     if (p->b2_rule != 0 && p->b2_rule != 1) return fail(QAI_ERR_INVALID_ARG, "b2_rule must be 0 or 1");
-    if (p->flags != 0) return fail(QAI_ERR_INVALID_ARG, "flags must be 0");
+    if (p->flags & ~QAI_FLAG_OUTPUT_C) return fail(QAI_ERR_INVALID_ARG, "unknown bits in flags");
     return QAI_OK;
 }
 
@@ -168,6 +168,7 @@ qai::MethodArgs method_args(const qai_params* p, double eb)
     m.grad_threshold = p->grad_threshold;
     m.sign_rule = p->sign_rule;
     m.b2_rule = p->b2_rule;
+    m.output_c = (p->flags & QAI_FLAG_OUTPUT_C) ? 1 : 0;
     return m;
 }
 
@@ -373,6 +374,110 @@ qai_status qai_mitigate_host(const int32_t* h_q, float* h_out, int rank, const i
     if (s != QAI_OK) return s;
     e = cudaMemcpyAsync(h_out, d_out, (size_t)sh.N * 4, cudaMemcpyDeviceToHost, stream);
     if (e != cudaSuccess) return cuda_fail(e, "copy D'' to host");
+    return QAI_OK;
+}
+
+qai_status qai_saved_size(int rank, const int64_t* dims, size_t* bytes)
+{
+    if (!bytes) return fail(QAI_ERR_INVALID_ARG, "bytes is NULL");
+    Shape sh;
+    qai_status s = make_shape(rank, dims, &sh);
+    if (s != QAI_OK) return s;
+    *bytes = align256((size_t)sh.N * 4) * 2 + align256((size_t)sh.N);
+    return QAI_OK;
+}
+
+// Saved state of the adjoint: Dist1 (int32), Dist2 (int32), S (int8).
+static qai_debug_out saved_views(void* d_saved, int64_t N)
+{
+    char* b = static_cast<char*>(d_saved);
+    qai_debug_out d{};
+    d.dist1 = reinterpret_cast<int32_t*>(b);
+    d.dist2 = reinterpret_cast<int32_t*>(b + align256((size_t)N * 4));
+    d.s = reinterpret_cast<int8_t*>(b + 2 * align256((size_t)N * 4));
+    return d;
+}
+
+qai_status qai_mitigate_save(const int32_t* d_q, float* d_out, int rank, const int64_t* dims, double eb,
+                             const qai_params* params, void* d_saved, void* d_ws, size_t ws_bytes,
+                             cudaStream_t stream)
+{
+    g_last_error.clear();
+    if (!d_saved) return fail(QAI_ERR_INVALID_ARG, "d_saved must be non-NULL");
+    if (reinterpret_cast<uintptr_t>(d_saved) & 255) return fail(QAI_ERR_INVALID_ARG, "d_saved must be 256-byte aligned");
+    Shape sh;
+    qai_status s = make_shape(rank, dims, &sh);
+    if (s != QAI_OK) return s;
+    const qai_debug_out d = saved_views(d_saved, sh.N);
+    return qai_mitigate(d_q, d_out, rank, dims, eb, params, d_ws, ws_bytes, stream, &d);
+}
+
+qai_status qai_workspace_size_backward(int rank, const int64_t* dims, int recompute, size_t* bytes)
+{
+    if (!bytes) return fail(QAI_ERR_INVALID_ARG, "bytes is NULL");
+    Shape sh;
+    qai_status s = make_shape(rank, dims, &sh);
+    if (s != QAI_OK) return s;
+    const size_t partials = align256(2 * sizeof(double) * qai::kBackwardMaxBlocks);
+    *bytes = partials + (recompute ? layout_for(sh, 0).total + 2 * align256((size_t)sh.N * 4) : 0);
+    return QAI_OK;
+}
+
+qai_status qai_mitigate_backward(const int32_t* d_q, const float* d_grad_out, float* d_grad_dprime,
+                                 double* d_grad_params, int rank, const int64_t* dims, double eb,
+                                 const qai_params* params, const void* d_saved, void* d_ws,
+                                 size_t ws_bytes, cudaStream_t stream)
+{
+    g_last_error.clear();
+    if (!d_q || !d_grad_out || !d_grad_params)
+        return fail(QAI_ERR_INVALID_ARG, "d_q, d_grad_out and d_grad_params must be non-NULL");
+    if (!(eb > 0.0) || !std::isfinite(eb)) return fail(QAI_ERR_INVALID_ARG, "eb must be finite and > 0");
+    qai_params defaults;
+    qai_default_params(&defaults);
+    const qai_params* p = params ? params : &defaults;
+    qai_status s = check_params(p);
+    if (s != QAI_OK) return s;
+    Shape sh;
+    if ((s = make_shape(rank, dims, &sh)) != QAI_OK) return s;
+    qai::BackArgs b{};
+    b.N = sh.N;
+    b.grad_out = d_grad_out;
+    b.grad_dprime = d_grad_dprime;
+    b.grad_params = d_grad_params;
+    b.p = (float)p->idw_power;
+    b.eta = p->eta;
+    b.eb = eb;
+    size_t need = 0;
+    qai_workspace_size_backward(rank, dims, d_saved ? 0 : 1, &need);
+    if (!d_ws || ws_bytes < need)
+        return fail(QAI_ERR_INVALID_ARG, "the adjoint needs a workspace of %zu bytes", need);
+    if (reinterpret_cast<uintptr_t>(d_ws) & 255) return fail(QAI_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    const size_t partials = align256(2 * sizeof(double) * qai::kBackwardMaxBlocks);
+    b.partials = static_cast<double*>(d_ws);
+    if (d_saved) {
+        const qai_debug_out v = saved_views(const_cast<void*>(d_saved), sh.N);
+        b.dist1 = v.dist1;
+        b.dist2 = v.dist2;
+        b.s = v.s;
+    } else {
+        // recompute Dist1, S and Dist2 from q with the forward pipeline
+        const Layout lay = layout_for(sh, 0);
+        char* ws = static_cast<char*>(d_ws) + partials;
+        int32_t* dist2 = reinterpret_cast<int32_t*>(ws + lay.total);
+        float* scratch_out = reinterpret_cast<float*>(ws + lay.total + align256((size_t)sh.N * 4));
+        qai_debug_out d{};
+        d.dist2 = dist2;
+        qai_params pc = *p;
+        pc.flags |= QAI_FLAG_OUTPUT_C;
+        s = run_pipeline(d_q, scratch_out, sh, method_args(&pc, eb), ws, lay, stream, &d);
+        if (s != QAI_OK) return s;
+        b.dist1 = reinterpret_cast<int32_t*>(ws + lay.dist1);
+        b.s = reinterpret_cast<int8_t*>(ws + lay.s);
+        b.dist2 = dist2;
+    }
+    cudaError_t e = timed("backward", (double)sh.N * (4 + 1 + 4 + 4 + (d_grad_dprime ? 4 : 0)), stream,
+              [&] { return qai::launch_backward(b, stream); });
+    if (e != cudaSuccess) return cuda_fail(e, "backward");
     return QAI_OK;
 }
 

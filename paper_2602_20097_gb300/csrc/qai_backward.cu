@@ -1,0 +1,121 @@
+// qai_backward.cu -- adjoint of step E with the EDT assignment held fixed.
+//
+// D'' = D' + S w eta eps with w = 1 / (1 + (k1/k2)^p), k = sqrt(Dist). For a
+// loss with dL/dD'' = G:
+//   dL/dD'  = G
+//   dL/deta = sum G S w eps
+//   dL/dp   = sum G S eta eps w (1 - w) (ln k2 - ln k1)
+// (w is constant where k1 = 0, k2 = 0 or k2 is infinite, so dw/dp = 0 there).
+// One grid-stride pass: each thread sums its terms in fp32 with Kahan
+// compensation and folds them into FP64 every 64 terms; each block writes its
+// two FP64 totals to a partials array, and a one-block kernel adds the
+// partials in a fixed order, so the result is the same on every run.
+#include "qai_device.cuh"
+#include "qai_launch.h"
+
+namespace qai {
+namespace {
+
+struct Kahan {
+    float s = 0.f, c = 0.f;
+    __device__ void add(float v)
+    {
+        const float y = v - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(256) k_backward(BackArgs a)
+{
+    Kahan ke, kp;
+    double de = 0.0, dp = 0.0;
+    int since = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += stride) {
+        const float g = __ldg(a.grad_out + i);
+        if (a.grad_dprime) a.grad_dprime[i] = g;
+        const int s = __ldg(a.s + i);
+        if (s != 0) {
+            const int d1 = __ldg(a.dist1 + i), d2 = __ldg(a.dist2 + i);
+            float w = 1.0f, dw = 0.0f;
+            if (d1 != 0 && d2 == 0) {
+                w = 0.0f;
+            } else if (d1 != 0 && d2 != kDistInf) {
+                const float l1 = logf((float)d1), l2 = logf((float)d2);
+                const float t = expf(0.5f * a.p * (l1 - l2));
+                w = 1.0f / (1.0f + t);
+                dw = w * (1.0f - w) * 0.5f * (l2 - l1);
+            }
+            const float gs = (float)s * g;
+            ke.add(gs * w);
+            kp.add(gs * dw);
+        }
+        if (++since == 64) {
+            de += (double)ke.s;
+            dp += (double)kp.s;
+            ke = Kahan();
+            kp = Kahan();
+            since = 0;
+        }
+    }
+    de += (double)ke.s;
+    dp += (double)kp.s;
+    __shared__ double red[2][8];
+    de = warp_sum(de);
+    dp = warp_sum(dp);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][warp] = de;
+        red[1][warp] = dp;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double te = 0.0, tp = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            te += red[0][k];
+            tp += red[1][k];
+        }
+        a.partials[2 * blockIdx.x] = te;
+        a.partials[2 * blockIdx.x + 1] = tp;
+    }
+}
+
+__global__ void __launch_bounds__(32) k_backward_final(BackArgs a, int nblocks)
+{
+    if (threadIdx.x != 0) return;
+    double te = 0.0, tp = 0.0;
+    for (int k = 0; k < nblocks; ++k) {
+        te += a.partials[2 * k];
+        tp += a.partials[2 * k + 1];
+    }
+    a.grad_params[0] = te * a.eb;
+    a.grad_params[1] = tp * a.eta * a.eb;
+}
+
+}  // namespace
+
+cudaError_t launch_backward(const BackArgs& a, cudaStream_t st)
+{
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t blocks = (a.N + 255) / 256;
+    if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
+    if (blocks > kBackwardMaxBlocks) blocks = kBackwardMaxBlocks;
+    if (blocks < 1) blocks = 1;
+    k_backward<<<(int)blocks, 256, 0, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_backward_final<<<1, 32, 0, st>>>(a, (int)blocks);
+    return cudaGetLastError();
+}
+
+}  // namespace qai

@@ -38,6 +38,7 @@ struct MethodArgs {
     int grad_threshold;  // Algorithm 2 fast-varying test, integer form
     int sign_rule;       // 0 SUM, 1 FIRST
     int b2_rule;         // 0 SAME_Q, 1 LITERAL
+    int output_c;        // write the compensation C instead of D''
 };
 
 // Row pass: one warp per x-row; rows enumerated (z, y).
@@ -81,6 +82,21 @@ struct ColArgs {
     int32_t* dbg_idx_out;
     int32_t* dbg_dist2;      // phase 2 final
     MethodArgs m;
+};
+
+// Adjoint of step E: a reduction over the points (qai_backward.cu).
+constexpr int kBackwardMaxBlocks = 2048;
+struct BackArgs {
+    int64_t N;
+    const float* grad_out;   // dL/dD''
+    const int8_t* s;         // S
+    const int32_t* dist1;    // Dist1
+    const int32_t* dist2;    // Dist2
+    float* grad_dprime;      // dL/dD' (= dL/dD''), NULL to skip
+    double* grad_params;     // [2]: dL/deta, dL/dp
+    double* partials;        // [2 * kBackwardMaxBlocks] block totals (workspace)
+    float p;                 // IDW exponent
+    double eta, eb;
 };
 
 // PTX approximate square root, reciprocal, log2 and exp2 (a few ulp each;
@@ -132,7 +148,8 @@ __device__ __forceinline__ float compensate(int32_t q, int32_t d1, int32_t d2, i
     w = d2 == 0 ? 0.0f : w;
     w = d1 == 0 ? 1.0f : w;
     const float fs = s > 0 ? 1.0f : (s < 0 ? -1.0f : 0.0f);
-    return fmaf((float)q, m.two_eb, fs * w * m.eta_eb);
+    const float c = fs * w * m.eta_eb;
+    return m.output_c ? c : fmaf((float)q, m.two_eb, c);
 }
 
 }  // namespace qai

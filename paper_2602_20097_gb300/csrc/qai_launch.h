@@ -27,6 +27,9 @@ bool choose_colpass(int L, int in_bytes, ColConfig* cfg);
 cudaError_t launch_colpass(int phase, int in_bytes, bool final_pass, ColArgs& a,
                            const ColConfig& cfg, bool debug, int64_t max_g, cudaStream_t st);
 
+// Adjoint reduction of step E (qai_backward.cu).
+cudaError_t launch_backward(const BackArgs& a, cudaStream_t st);
+
 // Records `msg` as qai_last_error() of the calling host thread.
 void set_last_error(const char* msg);
 

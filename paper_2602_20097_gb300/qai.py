@@ -31,6 +31,7 @@ _lib = None
 SIGN_SUM, SIGN_FIRST = 0, 1
 B2_SAME_Q, B2_LITERAL = 0, 1
 WS_INDEX = 1
+FLAG_OUTPUT_C = 1
 INF32 = 2 ** 31 - 1
 
 
@@ -64,6 +65,13 @@ SIGNATURES = {
                                          P, ctypes.c_size_t, P]),
     "qai_mitigate_static": (ctypes.c_int, [P, P, ctypes.c_int, P, ctypes.c_double,
                                            ctypes.POINTER(Params), P]),
+    "qai_saved_size": (ctypes.c_int, [ctypes.c_int, P, ctypes.POINTER(ctypes.c_size_t)]),
+    "qai_mitigate_save": (ctypes.c_int, [P, P, ctypes.c_int, P, ctypes.c_double, ctypes.POINTER(Params),
+                                         P, P, ctypes.c_size_t, P]),
+    "qai_workspace_size_backward": (ctypes.c_int, [ctypes.c_int, P, ctypes.c_int,
+                                                   ctypes.POINTER(ctypes.c_size_t)]),
+    "qai_mitigate_backward": (ctypes.c_int, [P, P, P, P, ctypes.c_int, P, ctypes.c_double,
+                                             ctypes.POINTER(Params), P, P, ctypes.c_size_t, P]),
     "qai_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "qai_profile_read": (ctypes.c_int, [ctypes.POINTER(KernelStat), ctypes.c_int]),
     "qai_launch_count": (ctypes.c_int64, []),
@@ -142,19 +150,21 @@ def alloc_workspace(nbytes: int, device=None) -> torch.Tensor:
     return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device or "cuda")
 
 
-def _params(eta, idw_power, grad_threshold, sign_rule, b2_rule):
+def _params(eta, idw_power, grad_threshold, sign_rule, b2_rule, output_c=False):
     return default_params(eta=eta, idw_power=idw_power, grad_threshold=grad_threshold,
-                          sign_rule=sign_rule, b2_rule=b2_rule)
+                          sign_rule=sign_rule, b2_rule=b2_rule,
+                          flags=FLAG_OUTPUT_C if output_c else 0)
 
 
 def mitigate(q: torch.Tensor, eb: float, eta: float = 0.9, idw_power: float = 1.0,
              grad_threshold: int = 2, sign_rule: int = SIGN_SUM, b2_rule: int = B2_SAME_Q,
              out: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
-             debug: bool = False, stream=None):
+             debug: bool = False, stream=None, output_c: bool = False):
     """Algorithm 4 on a contiguous CUDA int32 tensor ``q`` (rank 1-3).
 
-    Returns D'' as a float32 tensor of ``q``'s shape, or ``(D'', maps)`` when
-    ``debug`` with ``maps`` = dict of the per-step outputs (device tensors).
+    Returns D'' as a float32 tensor of ``q``'s shape (the compensation C alone
+    with ``output_c``), or ``(D'', maps)`` when ``debug`` with ``maps`` = dict
+    of the per-step outputs (device tensors).
     """
     lib = load()
     if not (q.is_cuda and q.dtype == torch.int32 and q.is_contiguous()):
@@ -172,7 +182,7 @@ def mitigate(q: torch.Tensor, eb: float, eta: float = 0.9, idw_power: float = 1.
         dbg = DebugOut(**{k: v.data_ptr() for k, v in maps.items()})
     if workspace is None:
         workspace = alloc_workspace(workspace_size(shape, with_index=debug), q.device)
-    p = _params(eta, idw_power, grad_threshold, sign_rule, b2_rule)
+    p = _params(eta, idw_power, grad_threshold, sign_rule, b2_rule, output_c)
     rc = lib.qai_mitigate(q.data_ptr(), out.data_ptr(), len(shape), _dims(shape), float(eb),
                           ctypes.byref(p), workspace.data_ptr(), workspace.numel(), _stream(stream),
                           ctypes.byref(dbg) if dbg is not None else None)
@@ -200,6 +210,115 @@ def mitigate_host(q_host: torch.Tensor, eb: float, out_host: torch.Tensor | None
                                _stream(stream))
     _check(rc)
     return out_host
+
+
+def saved_size(shape) -> int:
+    n = ctypes.c_size_t()
+    _check(load().qai_saved_size(len(shape), _dims(shape), ctypes.byref(n)))
+    return int(n.value)
+
+
+def workspace_size_backward(shape, recompute: bool) -> int:
+    n = ctypes.c_size_t()
+    _check(load().qai_workspace_size_backward(len(shape), _dims(shape), 1 if recompute else 0,
+                                              ctypes.byref(n)))
+    return int(n.value)
+
+
+def mitigate_save(q: torch.Tensor, eb: float, eta: float = 0.9, idw_power: float = 1.0,
+                  grad_threshold: int = 2, sign_rule: int = SIGN_SUM, b2_rule: int = B2_SAME_Q,
+                  output_c: bool = False, saved: torch.Tensor | None = None,
+                  workspace: torch.Tensor | None = None, stream=None):
+    """Forward that also keeps Dist1, Dist2 and S for the stored-mode adjoint.
+    Returns ``(out, saved)``."""
+    lib = load()
+    shape = tuple(q.shape)
+    out = torch.empty(shape, dtype=torch.float32, device=q.device)
+    if saved is None:
+        saved = alloc_workspace(saved_size(shape), q.device)
+    if workspace is None:
+        workspace = alloc_workspace(workspace_size(shape), q.device)
+    p = _params(eta, idw_power, grad_threshold, sign_rule, b2_rule, output_c)
+    _check(lib.qai_mitigate_save(q.data_ptr(), out.data_ptr(), len(shape), _dims(shape), float(eb),
+                                 ctypes.byref(p), saved.data_ptr(), workspace.data_ptr(),
+                                 workspace.numel(), _stream(stream)))
+    return out, saved
+
+
+def mitigate_backward(q: torch.Tensor, eb: float, grad_out: torch.Tensor, saved=None,
+                      eta: float = 0.9, idw_power: float = 1.0, grad_threshold: int = 2,
+                      sign_rule: int = SIGN_SUM, b2_rule: int = B2_SAME_Q,
+                      want_grad_dprime: bool = True, workspace: torch.Tensor | None = None,
+                      stream=None):
+    """Adjoint of step E: returns ``(dL/dD' or None, tensor([dL/deta, dL/dp]))``
+    (float64, on the device). ``saved`` from :func:`mitigate_save` selects the
+    stored mode; ``None`` recomputes Dist1, Dist2 and S from ``q``."""
+    lib = load()
+    shape = tuple(q.shape)
+    g = grad_out.contiguous().to(torch.float32)
+    gd = torch.empty(shape, dtype=torch.float32, device=q.device) if want_grad_dprime else None
+    gp = torch.empty(2, dtype=torch.float64, device=q.device)
+    if workspace is None:
+        workspace = alloc_workspace(workspace_size_backward(shape, saved is None), q.device)
+    p = _params(eta, idw_power, grad_threshold, sign_rule, b2_rule)
+    _check(lib.qai_mitigate_backward(
+        q.data_ptr(), g.data_ptr(), gd.data_ptr() if gd is not None else None, gp.data_ptr(),
+        len(shape), _dims(shape), float(eb), ctypes.byref(p),
+        saved.data_ptr() if saved is not None else None,
+        workspace.data_ptr(), workspace.numel(), _stream(stream)))
+    return gd, gp
+
+
+class QAIFunction(torch.autograd.Function):
+    """D'' = D' + C(q; eta, p), differentiable in D', eta and p with the EDT
+    assignment held fixed (the adjoint of step E, run by the CUDA library).
+
+    ``QAIFunction.apply(dprime, eta, p, q, eb, stored)``: ``dprime`` float32
+    field on the device, ``eta`` and ``p`` 0-dim float64 tensors, ``q`` the
+    int32 indices, ``stored`` True keeps Dist1/Dist2/S from the forward,
+    False recomputes them in the backward (no memory held between the two).
+    """
+
+    @staticmethod
+    def forward(ctx, dprime, eta, p, q, eb, stored=True):
+        e, pw = float(eta), float(p)
+        if stored:
+            comp, saved = mitigate_save(q, eb, eta=e, idw_power=pw, output_c=True)
+        else:
+            comp, saved = mitigate(q, eb, eta=e, idw_power=pw, output_c=True), None
+        ctx.save_for_backward(q)
+        ctx.saved_state, ctx.eb, ctx.e, ctx.pw = saved, eb, e, pw
+        return dprime + comp
+
+    @staticmethod
+    def backward(ctx, grad):
+        (q,) = ctx.saved_tensors
+        _, gp = mitigate_backward(q, ctx.eb, grad, saved=ctx.saved_state, eta=ctx.e,
+                                  idw_power=ctx.pw, want_grad_dprime=False)
+        return grad, gp[0], gp[1], None, None, None
+
+
+def tune(q: torch.Tensor, eb: float, x: torch.Tensor, eta: float = 0.9, p: float = 1.0,
+         steps: int = 20, lr: float = 0.05, stored: bool = True):
+    """Gradient descent on (eta, p) minimising mean((D'' - x)^2) against the
+    original field ``x``; returns the list of (eta, p, loss) per step."""
+    dprime = (q.to(torch.float64) * (2.0 * eb)).to(torch.float32)
+    e = torch.tensor(eta, dtype=torch.float64, device=q.device, requires_grad=True)
+    pw = torch.tensor(p, dtype=torch.float64, device=q.device, requires_grad=True)
+    xs = x.to(torch.float32)
+    hist = []
+    for _ in range(steps):
+        out = QAIFunction.apply(dprime, e, pw, q, eb, stored)
+        loss = torch.mean((out.double() - xs.double()) ** 2)
+        e.grad = pw.grad = None
+        loss.backward()
+        hist.append((float(e.detach()), float(pw.detach()), float(loss.detach())))
+        with torch.no_grad():
+            # normalised steps: the loss scale is eps^2, so divide by it
+            e -= lr * e.grad / (eb * eb)
+            pw -= lr * pw.grad / (eb * eb)
+            pw.clamp_(min=0.05)
+    return hist
 
 
 STATIC_MAX_POINTS = 2097152

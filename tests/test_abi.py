@@ -81,7 +81,7 @@ def test_argument_errors_return_status():
     for bad in (0.0, -1.0, float("nan"), float("inf")):
         assert _call(eb=bad) == 1
     for field, val in (("eta", float("nan")), ("eta", -1.0), ("idw_power", 0.0),
-                       ("grad_threshold", 0), ("sign_rule", 2), ("b2_rule", -1), ("flags", 1)):
+                       ("grad_threshold", 0), ("sign_rule", 2), ("b2_rule", -1), ("flags", 2)):
         p = qai.default_params()
         setattr(p, field, val)
         assert _call(params=p) == 1, field
@@ -96,3 +96,20 @@ def test_argument_errors_return_status():
 def test_profile_counters_start_empty():
     assert qai.profile_read() == {}
     assert qai.launch_count() >= 0
+
+
+def test_adjoint_sizes_and_argument_errors():
+    lib = qai.load()
+    assert qai.saved_size((64, 64, 64)) >= 64 ** 3 * 9
+    assert 0 < qai.workspace_size_backward((64, 64, 64), False) <= 64 * 1024
+    assert qai.workspace_size_backward((64, 64, 64), True) >= qai.workspace_size((64, 64, 64)) + 2 * 4 * 64 ** 3
+    shape = (8, 8, 8)
+    rc = lib.qai_mitigate_backward(ctypes.c_void_p(16), None, None, ctypes.c_void_p(16), 3, qai._dims(shape),
+                                   0.1, None, None, None, 0, None)
+    assert rc == 1                                     # NULL grad_out
+    rc = lib.qai_mitigate_backward(ctypes.c_void_p(16), ctypes.c_void_p(16), None, ctypes.c_void_p(16), 3,
+                                   qai._dims(shape), 0.1, None, None, None, 0, None)
+    assert rc == 1 and b"workspace" in lib.qai_last_error()   # no workspace
+    rc = lib.qai_mitigate_save(ctypes.c_void_p(16), ctypes.c_void_p(16), 3, qai._dims(shape), 0.1, None,
+                               ctypes.c_void_p(257), None, 0, None)
+    assert rc == 1                                     # misaligned saved state

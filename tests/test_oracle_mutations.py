@@ -34,6 +34,9 @@ MUTATIONS = {
                           "if (c[a] < 1 || c[a] > s->n[a] - 1) return 0;"),
     "dequantize_missing_2": ("double dprime = 2.0 * (double)Q[i] * eb;",
                              "double dprime = (double)Q[i] * eb;"),
+    "adjoint_dw_missing_factor": ("double dw = w * (1.0 - w) * (0.5 * log((double)b) - 0.5 * log((double)a));",
+                                  "double dw = w * (0.5 * log((double)b) - 0.5 * log((double)a));"),
+    "adjoint_eta_missing_eb": ("ge += G[i] * S[i] * w * eb;", "ge += G[i] * S[i] * w;"),
     "k2_zero_precedence": ("    if (d1 == 0) return 1.0;                /* on a quantization boundary     */\n"
                            "    if (d2 == 0) return 0.0;",
                            "    if (d2 == 0) return 0.0;\n    if (d1 == 0) return 1.0;"),
@@ -52,6 +55,7 @@ def test_mutation_is_caught(name, tmp_path):
                     str(lib), str(mutated), "-lm"], check=True)
     env = dict(os.environ, QAI_ORACLE_LIB=str(lib), OMP_NUM_THREADS="1")
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_adjoint.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutation {name} survived the pins:\n{r.stdout[-2000:]}"
