@@ -164,6 +164,46 @@ qai_status qai_mitigate_backward(const int32_t* d_q, const float* d_grad_out, fl
                                  const qai_params* params, const void* d_saved, void* d_ws,
                                  size_t ws_bytes, cudaStream_t stream);
 
+/* ---- Batched form (no counterpart in the paper) ---------------------------
+ * n independent fields in one call: field i is d_q[i] -> d_out[i] (device
+ * buffers), rank ranks[i], extents dims[3*i .. 3*i + ranks[i]) (slowest first),
+ * bound eb[i]; params are shared. Each pipeline stage runs as one grouped
+ * kernel over all fields of the same rank, and the whole launch sequence is
+ * captured into a CUDA graph the first time a batch is seen (keyed by every
+ * pointer, extent and parameter) and replayed afterwards: a repeated batch is
+ * one graph launch on `stream`. When `stream` is already capturing, the
+ * launches are recorded into the caller's graph instead. Results equal those
+ * of n qai_mitigate calls. Column-pass tile shapes and the field order come
+ * from qai_autotune_batched when it has seen a batch of the same shapes. */
+
+/* Device workspace of a batch: the sum of the fields' workspaces. */
+qai_status qai_workspace_size_batched(int n, const int32_t* ranks, const int64_t* dims, size_t* bytes);
+
+qai_status qai_mitigate_batched(int n, const int32_t* const* d_q, float* const* d_out,
+                                const int32_t* ranks, const int64_t* dims, const double* eb,
+                                const qai_params* params, void* d_ws, size_t ws_bytes,
+                                cudaStream_t stream);
+
+/* Autotuner result for the fields of one rank. */
+typedef struct {
+    int32_t rank;           /* 1, 2 or 3 (0: no field of this rank)           */
+    int32_t fields;
+    int32_t rows_per_band;  /* rows per band of the column passes             */
+    int32_t max_w;          /* columns per CTA, at most                       */
+    int32_t order;          /* 0: fields as given, 1: largest field first     */
+    float ms;               /* time of the group's stages with this choice    */
+} qai_batch_choice;
+
+/* Times every candidate tile shape and field order on this batch (running
+ * its stages several times; the outputs hold a correct result afterwards),
+ * keeps the fastest per rank group for later qai_mitigate_batched calls with
+ * the same shapes, and reports it in choices[0..2] (ranks 1..3) when non-NULL.
+ * Synchronises `stream`. */
+qai_status qai_autotune_batched(int n, const int32_t* const* d_q, float* const* d_out,
+                                const int32_t* ranks, const int64_t* dims, const double* eb,
+                                const qai_params* params, void* d_ws, size_t ws_bytes,
+                                cudaStream_t stream, qai_batch_choice* choices);
+
 /* Largest field (points, after squeezing) that qai_mitigate_static accepts. */
 #define QAI_STATIC_MAX_POINTS 2097152
 

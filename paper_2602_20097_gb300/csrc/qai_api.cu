@@ -11,13 +11,16 @@
 
 #include "qai.h"
 #include "qai_device.cuh"
+#include "qai_host.h"
 #include "qai_launch.h"
 
 namespace {
-
 thread_local std::string g_last_error;
+}  // namespace
 
-qai_status fail(qai_status s, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+namespace qai {
+namespace host {
+
 qai_status fail(qai_status s, const char* fmt, ...)
 {
     char buf[512];
@@ -30,6 +33,13 @@ qai_status fail(qai_status s, const char* fmt, ...)
 }
 
 std::atomic<int64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1); }
+
+}  // namespace host
+}  // namespace qai
+
+namespace {
+using namespace qai::host;
 
 // ---- per-kernel timing ------------------------------------------------------
 struct Pending {
@@ -85,13 +95,12 @@ cudaError_t timed(const char* name, double algo_bytes, cudaStream_t st, F&& fn)
     return e;
 }
 
-// ---- shapes -----------------------------------------------------------------
-struct Shape {
-    int rank;       // after squeezing extent-1 axes
-    int nz, ny, nx;
-    int64_t N;
-};
+}  // namespace
 
+namespace qai {
+namespace host {
+
+// ---- shapes -----------------------------------------------------------------
 constexpr int kMaxX = 16383, kMaxYZ = 4096, kMax1D = 32768;
 
 qai_status make_shape(int rank, const int64_t* dims, Shape* s)
@@ -124,10 +133,6 @@ qai_status make_shape(int rank, const int64_t* dims, Shape* s)
 }
 
 // ---- workspace layout -----------------------------------------------------------
-struct Layout {
-    size_t eqm, xw, yw, dist1, s, idx, total;
-};
-
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 Layout layout_for(const Shape& s, uint32_t flags)
@@ -176,6 +181,12 @@ qai_status cuda_fail(cudaError_t e, const char* what)
 {
     return fail(QAI_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
+
+}  // namespace host
+}  // namespace qai
+
+namespace {
+using namespace qai::host;
 
 // The launch sequence of Algorithm 4 on a validated shape.
 qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const qai::MethodArgs& m,

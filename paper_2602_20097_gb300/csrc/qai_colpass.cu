@@ -95,8 +95,9 @@ __device__ __forceinline__ void emit_point(const ColArgs& a, int idx, int src, i
     }
 }
 
+// One CTA of the column pass: tile `blk` of the lines described by `a`.
 template <int PHASE, int IN, bool FINAL, bool DEBUG, bool NARROW>
-__global__ void __launch_bounds__(512, IN == 2 ? 3 : 2) k_colpass(ColArgs a)
+__device__ __forceinline__ void colpass_tile(const ColArgs& a, const int blk)
 {
     using Word = std::conditional_t<IN == 2, uint16_t, uint32_t>;
     constexpr Word kWInf = IN == 2 ? (Word)kInf16 : (Word)kInf32;
@@ -114,8 +115,8 @@ __global__ void __launch_bounds__(512, IN == 2 ? 3 : 2) k_colpass(ColArgs a)
     uint16_t* nlst = lmap + B * W;                                      // [W] number of such bands
 
     const int tiles_per_plane = (a.C + W - 1) / W;
-    const int p = blockIdx.x / tiles_per_plane;
-    const int c0 = (blockIdx.x - p * tiles_per_plane) * W;
+    const int p = blk / tiles_per_plane;
+    const int c0 = (blk - p * tiles_per_plane) * W;
     const int pbase = p * a.plane_stride;
     const int RS = a.row_stride;
     const Word* in = static_cast<const Word*>(a.in);
@@ -426,6 +427,30 @@ __global__ void __launch_bounds__(512, IN == 2 ? 3 : 2) k_colpass(ColArgs a)
     }
 }
 
+template <int PHASE, int IN, bool FINAL, bool DEBUG, bool NARROW>
+__global__ void __launch_bounds__(512, IN == 2 ? 3 : 2) k_colpass(ColArgs a)
+{
+    colpass_tile<PHASE, IN, FINAL, DEBUG, NARROW>(a, blockIdx.x);
+}
+
+// Several fields in one launch: CTA b works on field f with
+// first_block[f] <= b < first_block[f + 1]. The table travels by value in the
+// kernel parameters.
+template <int PHASE, int IN, bool FINAL>
+__global__ void __launch_bounds__(512, IN == 2 ? 3 : 2) k_colpass_grouped(const __grid_constant__ ColTable t)
+{
+    const int b = blockIdx.x;
+    int lo = 0, hi = t.n - 1;
+    while (lo < hi) {  // last f with first_block[f] <= b
+        const int mid = (lo + hi + 1) >> 1;
+        if (t.first_block[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const ColArgs& a = t.args[lo];
+    if (a.narrow) colpass_tile<PHASE, IN, FINAL, false, true>(a, b - t.first_block[lo]);
+    else colpass_tile<PHASE, IN, FINAL, false, false>(a, b - t.first_block[lo]);
+}
+
 template <int PHASE, int IN, bool FINAL>
 cudaError_t go(ColArgs& a, bool debug, bool narrow, dim3 grid, dim3 block, size_t smem, cudaStream_t st)
 {
@@ -455,11 +480,17 @@ bool choose_colpass(int L, int in_bytes, ColConfig* cfg)
 {
     static const int rows_per_band = env_int("QAI_COL_ROWS_PER_BAND", 32);
     static const int max_w = env_int("QAI_COL_MAX_W", 16);
+    return choose_colpass_with(L, in_bytes, rows_per_band, max_w, cfg);
+}
+
+bool choose_colpass_with(int L, int in_bytes, int rows_per_band, int max_w, ColConfig* cfg)
+{
     int B = (L + rows_per_band - 1) / rows_per_band;
     B = B < 2 ? 2 : (B > kMaxBands ? kMaxBands : B);
     if (B > L) B = L < 1 ? 1 : L;
     const size_t budget = 200 * 1024;
     for (int W = max_w; W >= 4; W >>= 1) {
+        if (W * B > 512) continue;  // the kernels' launch bound
         const size_t smem = (size_t)L * W * (in_bytes + 2) + (size_t)4 * B * W * 2 + (size_t)W * 2;
         if (smem <= budget) {
             cfg->W = W;
@@ -471,11 +502,9 @@ bool choose_colpass(int L, int in_bytes, ColConfig* cfg)
     return false;
 }
 
-cudaError_t launch_colpass(int phase, int in_bytes, bool final_pass, ColArgs& a, const ColConfig& cfg,
-                           bool debug, int64_t max_g, cudaStream_t st)
+void prepare_colpass(ColArgs& a, int in_bytes, const ColConfig& cfg, int64_t max_g)
 {
     a.bands = cfg.B;
-    // cp.async granularity: every tile row segment must start 'vb'-aligned
     a.load_bytes = 0;
     for (int vb = 16; vb >= 4; vb >>= 1) {
         const bool ok = ((int64_t)a.row_stride * in_bytes) % vb == 0 &&
@@ -485,9 +514,35 @@ cudaError_t launch_colpass(int phase, int in_bytes, bool final_pass, ColArgs& a,
         if (ok) { a.load_bytes = vb; break; }
     }
     const int64_t L = a.L;
-    const bool narrow = 2 * L * max_g + L * L * L < (int64_t)0x7FFFFFFF;
-    const int tiles = ((a.C + cfg.W - 1) / cfg.W) * a.P;
-    const dim3 grid(tiles), block(cfg.W, cfg.B);
+    a.narrow = 2 * L * max_g + L * L * L < (int64_t)0x7FFFFFFF;
+}
+
+int colpass_blocks(const ColArgs& a, int W) { return ((a.C + W - 1) / W) * a.P; }
+
+cudaError_t launch_colpass_grouped(int phase, int in_bytes, bool final_pass, const ColTable& t,
+                                   const ColConfig& cfg, cudaStream_t st)
+{
+    const dim3 grid(t.first_block[t.n]), block(cfg.W, cfg.B);
+    auto run = [&](auto kern) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
+        if (e != cudaSuccess) return e;
+        kern<<<grid, block, cfg.smem, st>>>(t);
+        return cudaGetLastError();
+    };
+    if (phase == 1) {
+        if (in_bytes == 2) return final_pass ? run(k_colpass_grouped<1, 2, true>) : run(k_colpass_grouped<1, 2, false>);
+        return run(k_colpass_grouped<1, 4, true>);
+    }
+    if (in_bytes == 2) return final_pass ? run(k_colpass_grouped<2, 2, true>) : run(k_colpass_grouped<2, 2, false>);
+    return run(k_colpass_grouped<2, 4, true>);
+}
+
+cudaError_t launch_colpass(int phase, int in_bytes, bool final_pass, ColArgs& a, const ColConfig& cfg,
+                           bool debug, int64_t max_g, cudaStream_t st)
+{
+    prepare_colpass(a, in_bytes, cfg, max_g);
+    const bool narrow = a.narrow != 0;
+    const dim3 grid(colpass_blocks(a, cfg.W)), block(cfg.W, cfg.B);
     if (phase == 1) {
         if (in_bytes == 2) return final_pass ? go<1, 2, true>(a, debug, narrow, grid, block, cfg.smem, st)
                                              : go<1, 2, false>(a, debug, narrow, grid, block, cfg.smem, st);

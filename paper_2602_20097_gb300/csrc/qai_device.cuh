@@ -44,6 +44,7 @@ struct MethodArgs {
 // Row pass: one warp per x-row; rows enumerated (z, y).
 struct RowArgs {
     int rank, nz, ny, nx;
+    int vec;                 // 128-bit access path usable (set by the launcher)
     const int32_t* q;        // phase 1 input; phase 2 final: D' source
     uint8_t* eqm;            // phase 1 writes, phase 2 reads: equal-q neighbour mask
     const int8_t* s_in;      // phase 2: propagated sign map S
@@ -71,6 +72,7 @@ struct ColArgs {
     int64_t row_stride, plane_stride;
     int bands;               // B, rows are split in B bands of ceil(L / B)
     int load_bytes;          // cp.async width of the tile staging (16, 8, 4; 0 = plain loads)
+    int narrow;              // RemoveEDT fits 32-bit arithmetic (set by the launcher)
     void* out_w;             // non-final output words (yword)
     int32_t* dist1;          // phase 1 final
     int8_t* s_out;           // phase 1 final
@@ -82,6 +84,22 @@ struct ColArgs {
     int32_t* dbg_idx_out;
     int32_t* dbg_dist2;      // phase 2 final
     MethodArgs m;
+};
+
+// Grouped launches: several fields in one kernel, the per-field arguments
+// passed by value in the kernel parameters (at most kMaxGroup per launch).
+constexpr int kMaxGroup = 96;
+struct ColTable {
+    int n;                            // fields
+    int first_block[kMaxGroup + 1];   // CTA offsets; first_block[n] = grid size
+    ColArgs args[kMaxGroup];
+};
+struct RowTable {
+    int n;
+    int warps;                        // warps per CTA
+    int smem_nx;                      // x extent the per-warp shared memory is sized for
+    int first_row[kMaxGroup + 1];     // row offsets; first_row[n] = rows in total
+    RowArgs args[kMaxGroup];
 };
 
 // Adjoint of step E: a reduction over the points (qai_backward.cu).

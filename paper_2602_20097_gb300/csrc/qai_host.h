@@ -1,0 +1,36 @@
+// qai_host.h -- host-side helpers shared by the C-ABI translation units
+// (internal): shapes, workspace layout, parameter checks, error reporting.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "qai.h"
+#include "qai_device.cuh"
+
+namespace qai {
+namespace host {
+
+// A field after squeezing extent-1 axes: rank 1..3, extents nz, ny, nx.
+struct Shape {
+    int rank;
+    int nz, ny, nx;
+    int64_t N;
+};
+
+// Byte offsets of the workspace slices of one field.
+struct Layout {
+    size_t eqm, xw, yw, dist1, s, idx, total;
+};
+
+qai_status fail(qai_status s, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+qai_status cuda_fail(cudaError_t e, const char* what);
+qai_status make_shape(int rank, const int64_t* dims, Shape* s);
+size_t align256(size_t v);
+Layout layout_for(const Shape& s, uint32_t flags);
+qai_status check_params(const qai_params* p);
+MethodArgs method_args(const qai_params* p, double eb);
+void count_launch();
+
+}  // namespace host
+}  // namespace qai

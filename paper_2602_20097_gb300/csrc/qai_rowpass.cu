@@ -174,25 +174,19 @@ __device__ __forceinline__ void detect_sum32(int q0, int zl, int zr, int yl, int
     mask = mk;
 }
 
+// One warp's work: x-row `row` of the field `a`, with `wsm` this warp's
+// shared memory (smem_per_warp of an extent >= a.nx).
 template <int PHASE, int RANK, bool FINAL, bool DEBUG, bool VEC>
-__global__ void __launch_bounds__(256) k_rowpass(RowArgs a)
+__device__ __forceinline__ void rowpass_row(const RowArgs& a, const int row, unsigned char* wsm)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
     const int nx = a.nx;
     const int nseg = (nx + kSeg - 1) / kSeg;
     RowSmem sm;
-    {
-        unsigned char* base = smem + (size_t)warp * smem_per_warp(nx);
-        sm.sfirst = reinterpret_cast<int*>(base);
-        sm.slast = sm.sfirst + nseg;
-        sm.nextr = sm.slast + nseg;
-        sm.info = reinterpret_cast<uint16_t*>(sm.nextr + nseg);
-    }
-    const int row = blockIdx.x * nwarps + warp;
-    if (row >= a.nz * a.ny) return;  // whole warp leaves; only warp-level sync below
+    sm.sfirst = reinterpret_cast<int*>(wsm);
+    sm.slast = sm.sfirst + nseg;
+    sm.nextr = sm.slast + nseg;
+    sm.info = reinterpret_cast<uint16_t*>(sm.nextr + nseg);
     const int z = row / a.ny;
     const int y = row - z * a.ny;
     const int rbase = row * nx;
@@ -424,6 +418,37 @@ __global__ void __launch_bounds__(256) k_rowpass(RowArgs a)
     }
 }
 
+template <int PHASE, int RANK, bool FINAL, bool DEBUG, bool VEC>
+__global__ void __launch_bounds__(256) k_rowpass(RowArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5;
+    const int row = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (row >= a.nz * a.ny) return;  // whole warp leaves; only warp-level sync inside
+    rowpass_row<PHASE, RANK, FINAL, DEBUG, VEC>(a, row, smem + (size_t)warp * smem_per_warp(a.nx));
+}
+
+// Several fields in one launch: global row g belongs to field f with
+// first_row[f] <= g < first_row[f + 1]; the table travels by value.
+template <int PHASE, int RANK, bool FINAL>
+__global__ void __launch_bounds__(256) k_rowpass_grouped(const __grid_constant__ RowTable t)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5;
+    const int g = blockIdx.x * t.warps + warp;
+    if (g >= t.first_row[t.n]) return;
+    int lo = 0, hi = t.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (t.first_row[mid] <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    const RowArgs& a = t.args[lo];
+    unsigned char* wsm = smem + (size_t)warp * smem_per_warp(t.smem_nx);
+    if (a.vec) rowpass_row<PHASE, RANK, FINAL, false, true>(a, g - t.first_row[lo], wsm);
+    else rowpass_row<PHASE, RANK, FINAL, false, false>(a, g - t.first_row[lo], wsm);
+}
+
 template <int PHASE, int RANK, bool FINAL>
 cudaError_t go(const RowArgs& a, bool debug, bool vec, dim3 grid, dim3 block, size_t smem,
                cudaStream_t st)
@@ -451,15 +476,42 @@ int rowpass_warps(int nx)
 
 size_t rowpass_smem(int nx, int warps) { return (size_t)warps * smem_per_warp(nx); }
 
-cudaError_t launch_rowpass(int phase, bool final_pass, const RowArgs& a, bool debug, cudaStream_t st)
+void prepare_rowpass(RowArgs& a)
 {
+    // 128-bit / 32-bit accesses need 4 | nx and 16-byte aligned base pointers
+    auto al = [](const void* p, int b) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) % b) == 0; };
+    a.vec = (a.nx % 4 == 0) && al(a.q, 16) && al(a.eqm, 4) && al(a.s_in, 4) && al(a.xw, 8);
+}
+
+cudaError_t launch_rowpass_grouped(int phase, bool final_pass, const RowTable& t, cudaStream_t st)
+{
+    const size_t smem = rowpass_smem(t.smem_nx, t.warps);
+    const int rows = t.first_row[t.n];
+    const dim3 grid((rows + t.warps - 1) / t.warps), block(32 * t.warps);
+    auto run = [&](auto kern) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<grid, block, smem, st>>>(t);
+        return cudaGetLastError();
+    };
+    const int rank = t.args[0].rank;
+    if (phase == 1) {
+        if (final_pass) return run(k_rowpass_grouped<1, 1, true>);
+        return rank == 2 ? run(k_rowpass_grouped<1, 2, false>) : run(k_rowpass_grouped<1, 3, false>);
+    }
+    if (final_pass) return run(k_rowpass_grouped<2, 1, true>);
+    return rank == 2 ? run(k_rowpass_grouped<2, 2, false>) : run(k_rowpass_grouped<2, 3, false>);
+}
+
+cudaError_t launch_rowpass(int phase, bool final_pass, const RowArgs& a_in, bool debug, cudaStream_t st)
+{
+    RowArgs a = a_in;
+    prepare_rowpass(a);
     const int warps = rowpass_warps(a.nx);
     const size_t smem = rowpass_smem(a.nx, warps);
     const int rows = a.nz * a.ny;
     const dim3 grid((rows + warps - 1) / warps), block(32 * warps);
-    // 128-bit / 32-bit accesses need 4 | nx and 16-byte aligned base pointers
-    auto al = [](const void* p, int b) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) % b) == 0; };
-    const bool vec = (a.nx % 4 == 0) && al(a.q, 16) && al(a.eqm, 4) && al(a.s_in, 4) && al(a.xw, 8);
+    const bool vec = a.vec != 0;
     if (phase == 1) {
         if (final_pass) return go<1, 1, true>(a, debug, vec, grid, block, smem, st);
         if (a.rank == 2) return go<1, 2, false>(a, debug, vec, grid, block, smem, st);

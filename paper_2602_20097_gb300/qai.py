@@ -49,6 +49,11 @@ class DebugOut(ctypes.Structure):
     _fields_ = [("b1", P), ("sb", P), ("dist1", P), ("idx1", P), ("s", P), ("b2", P), ("dist2", P)]
 
 
+class BatchChoice(ctypes.Structure):
+    _fields_ = [("rank", ctypes.c_int32), ("fields", ctypes.c_int32), ("rows_per_band", ctypes.c_int32),
+                ("max_w", ctypes.c_int32), ("order", ctypes.c_int32), ("ms", ctypes.c_float)]
+
+
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64),
                 ("total_ms", ctypes.c_double), ("algo_bytes", ctypes.c_double)]
@@ -72,6 +77,11 @@ SIGNATURES = {
                                                    ctypes.POINTER(ctypes.c_size_t)]),
     "qai_mitigate_backward": (ctypes.c_int, [P, P, P, P, ctypes.c_int, P, ctypes.c_double,
                                              ctypes.POINTER(Params), P, P, ctypes.c_size_t, P]),
+    "qai_workspace_size_batched": (ctypes.c_int, [ctypes.c_int, P, P, ctypes.POINTER(ctypes.c_size_t)]),
+    "qai_mitigate_batched": (ctypes.c_int, [ctypes.c_int, P, P, P, P, P, ctypes.POINTER(Params), P,
+                                            ctypes.c_size_t, P]),
+    "qai_autotune_batched": (ctypes.c_int, [ctypes.c_int, P, P, P, P, P, ctypes.POINTER(Params), P,
+                                            ctypes.c_size_t, P, ctypes.POINTER(BatchChoice)]),
     "qai_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "qai_profile_read": (ctypes.c_int, [ctypes.POINTER(KernelStat), ctypes.c_int]),
     "qai_launch_count": (ctypes.c_int64, []),
@@ -319,6 +329,60 @@ def tune(q: torch.Tensor, eb: float, x: torch.Tensor, eta: float = 0.9, p: float
             pw -= lr * pw.grad / (eb * eb)
             pw.clamp_(min=0.05)
     return hist
+
+
+class Batch:
+    """A batch of fields for :func:`mitigate_batched`: the marshalled pointer,
+    rank, extent and bound arrays, the outputs and the workspace, built once
+    and reused across calls (so the library's cached CUDA graph is replayed)."""
+
+    def __init__(self, qs, ebs, outs=None, workspace=None):
+        self.qs = list(qs)
+        n = len(self.qs)
+        if n < 1 or len(ebs) != n:
+            raise QAIError("need one eb per field")
+        for q in self.qs:
+            if not (q.is_cuda and q.dtype == torch.int32 and q.is_contiguous() and 1 <= q.dim() <= 3):
+                raise QAIError("every field must be a contiguous CUDA int32 tensor of rank 1-3")
+        self.outs = list(outs) if outs is not None else [
+            torch.empty(q.shape, dtype=torch.float32, device=q.device) for q in self.qs]
+        self.n = n
+        self.q_ptrs = (ctypes.c_void_p * n)(*[q.data_ptr() for q in self.qs])
+        self.out_ptrs = (ctypes.c_void_p * n)(*[o.data_ptr() for o in self.outs])
+        self.ranks = (ctypes.c_int32 * n)(*[q.dim() for q in self.qs])
+        dims = []
+        for q in self.qs:
+            d = list(q.shape) + [1] * (3 - q.dim())
+            dims += d
+        self.dims = (ctypes.c_int64 * (3 * n))(*dims)
+        self.ebs = (ctypes.c_double * n)(*[float(e) for e in ebs])
+        nb = ctypes.c_size_t()
+        _check(load().qai_workspace_size_batched(n, self.ranks, self.dims, ctypes.byref(nb)))
+        self.workspace = workspace if workspace is not None else alloc_workspace(nb.value, self.qs[0].device)
+
+    def _args(self):
+        return (self.n, self.q_ptrs, self.out_ptrs, self.ranks, self.dims, self.ebs)
+
+
+def mitigate_batched(batch: Batch, stream=None, **kw):
+    """Algorithm 4 on every field of ``batch`` in one call (grouped kernels,
+    replayed from a cached CUDA graph). Returns ``batch.outs``."""
+    p = _params(kw.get("eta", 0.9), kw.get("idw_power", 1.0), kw.get("grad_threshold", 2),
+                kw.get("sign_rule", SIGN_SUM), kw.get("b2_rule", B2_SAME_Q))
+    _check(load().qai_mitigate_batched(*batch._args(), ctypes.byref(p), batch.workspace.data_ptr(),
+                                       batch.workspace.numel(), _stream(stream)))
+    return batch.outs
+
+
+def autotune_batched(batch: Batch, stream=None, **kw):
+    """Time the tile-shape and field-order candidates on ``batch`` and keep the
+    fastest per rank group; returns {rank: (rows_per_band, max_w, order, ms)}."""
+    p = _params(kw.get("eta", 0.9), kw.get("idw_power", 1.0), kw.get("grad_threshold", 2),
+                kw.get("sign_rule", SIGN_SUM), kw.get("b2_rule", B2_SAME_Q))
+    ch = (BatchChoice * 3)()
+    _check(load().qai_autotune_batched(*batch._args(), ctypes.byref(p), batch.workspace.data_ptr(),
+                                       batch.workspace.numel(), _stream(stream), ch))
+    return {c.rank: (c.rows_per_band, c.max_w, c.order, c.ms) for c in ch if c.rank}
 
 
 STATIC_MAX_POINTS = 2097152
