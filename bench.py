@@ -138,6 +138,11 @@ def dist_env():
     return world, rank, local
 
 
+def synth_quantize(x, eb):
+    from paper_2602_20097_gb300 import synth
+    return synth.quantize(x, eb)
+
+
 def make_field(device, seed, shape=SHAPE):
     from paper_2602_20097_gb300 import synth
     x = synth.grf(shape, slope=11.0 / 3.0, seed=seed, device=device)
@@ -146,11 +151,17 @@ def make_field(device, seed, shape=SHAPE):
     return x, q, eb
 
 
-def psnr(x, y):
-    import torch
-    rng = float(x.max() - x.min())
-    mse = float(torch.mean((x.double() - y.double()) ** 2))
-    return 20.0 * __import__("math").log10(rng / mse ** 0.5)
+def quality_gain(x, q, eb, out):
+    """PSNR (Eq. 4) and SSIM (Eq. 3, window 7, stride 2) of D' = 2 q eb and of
+    D'' against x, from the library's GPU quality kernels (untimed)."""
+    from paper_2602_20097_gb300 import qai
+    xf = x.float().contiguous()
+    dp = (q.double() * (2 * eb)).float()
+    a = qai.quality(xf, dp)
+    b = qai.quality(xf, out.contiguous())
+    return {"psnr_dprime_db": a["psnr"], "psnr_mitigated_db": b["psnr"], "psnr_gain_db": b["psnr"] - a["psnr"],
+            "ssim_dprime": a["ssim"], "ssim_mitigated": b["ssim"], "ssim_gain": b["ssim"] - a["ssim"],
+            "max_err_over_eps": float((x.double() - out.double()).abs().max()) / eb}
 
 
 def time_oracle(q_sample, eb, min_s=10.0, max_s=30.0):
@@ -288,10 +299,18 @@ def run_qai(args):
         e2e_value = run_e2e(q, eb, dev, stream, args.steps, barrier, world, ws)
         ws = None
 
-    # quality (untimed): PSNR gain and max error / eps of this field
-    psnr_q = psnr(x, q.double() * (2 * eb))
-    psnr_m = psnr(x, out)
-    max_err = float((x.double() - out.double()).abs().max()) / eb
+    # quality (untimed): PSNR and SSIM gain and max error / eps of this field
+    qual = quality_gain(x, q, eb, out)
+
+    # the same field at the configuration's second bound, eb = 1e-2 x range
+    eb2 = 1e-2 * (float(x.max()) - float(x.min()))
+    q2 = synth_quantize(x, eb2)
+    ws2 = qai.alloc_workspace(qai.workspace_size(tuple(q2.shape)), dev)
+    out2 = torch.empty_like(q2, dtype=torch.float32)
+    ms2 = _time_steps(lambda: qai.mitigate(q2, eb2, out=out2, workspace=ws2), args.steps)
+    second = {"rel_eb": 1e-2, "ms_per_step": ms2, "value": N * 4 / (ms2 * 1e-3) / 1e9,
+              **quality_gain(x, q2, eb2, out2)}
+    del q2, ws2, out2
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -335,14 +354,173 @@ def run_qai(args):
         "gpu_launches": launches,
         "clocks": clk.summary(tc0, tc1),
         "cpu_baseline": cpu,
-        "quality": {"psnr_dprime_db": psnr_q, "psnr_mitigated_db": psnr_m,
-                    "psnr_gain_db": psnr_m - psnr_q, "max_err_over_eps": max_err},
+        "quality": qual,
+        "second_bound": second,
         "kernels": kernels,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def _time_steps(fn, steps, warmup=3):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_aniso(args):
+    """The anisotropic shapes with a tanh front (one JSON line per shape)."""
+    import torch
+    from paper_2602_20097_gb300 import qai, synth
+    for shape, seed in (((100, 500, 500), 3), ((256, 384, 384), 4), ((98, 1200, 1200), 5), ((1800, 3600), 6)):
+        x = synth.grf_front(shape, seed=seed, device="cuda")
+        eb = 1e-3 * synth.value_range(x)
+        q = synth.quantize(x, eb)
+        ws = qai.alloc_workspace(qai.workspace_size(tuple(q.shape)))
+        out = torch.empty_like(q, dtype=torch.float32)
+        ms = _time_steps(lambda: qai.mitigate(q, eb, out=out, workspace=ws), args.steps)
+        print(json.dumps({"workload": "front_" + "x".join(map(str, shape)) + "_eb1e-3",
+                          "value": q.numel() * 4 / (ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ms,
+                          **quality_gain(x, q, eb, out)}), flush=True)
+
+
+def run_batch96(args):
+    """96 uneven 2-D/3-D fields: one batched call (cached CUDA graph, autotuned
+    tile shapes) vs 96 sequential plain calls on one stream."""
+    import torch
+    from paper_2602_20097_gb300 import qai, synth
+    specs = synth.batch_specs()
+    qs, ebs = [], []
+    for sp in specs:
+        x = synth.grf(sp["shape"], slope=sp["slope"], seed=sp["seed"], device="cuda")
+        eb = sp["rel_eb"] * synth.value_range(x)
+        qs.append(synth.quantize(x, eb))
+        ebs.append(eb)
+    npts = sum(q.numel() for q in qs)
+    batch = qai.Batch(qs, ebs)
+    choice = qai.autotune_batched(batch)
+    n0 = qai.launch_count()
+    ms_b = _time_steps(lambda: qai.mitigate_batched(batch), args.steps)
+    launches = (qai.launch_count() - n0) // (args.steps + 3)
+    wss = [qai.alloc_workspace(qai.workspace_size(tuple(q.shape))) for q in qs]
+    outs = [torch.empty_like(q, dtype=torch.float32) for q in qs]
+
+    def seq():
+        for q, eb, o, w in zip(qs, ebs, outs, wss):
+            qai.mitigate(q, eb, out=o, workspace=w)
+    ms_s = _time_steps(seq, args.steps)
+    same = all(torch.equal(a, b) for a, b in zip(batch.outs, outs))
+    print(json.dumps({"workload": "batch96_mixed", "fields": len(qs), "points": npts,
+                      "value": npts * 4 / (ms_b * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ms_b,
+                      "sequential": {"value": npts * 4 / (ms_s * 1e-3) / 1e9, "ms_per_step": ms_s,
+                                     "launches": 6 * len(qs)},
+                      "batched_kernels_per_graph": launches, "identical_to_sequential": same,
+                      "autotuned": {str(k): {"rows_per_band": v[0], "max_w": v[1],
+                                             "order": "largest first" if v[2] else "as given"}
+                                    for k, v in choice.items()}}), flush=True)
+
+
+def run_adjoint1024(args):
+    """Forward + adjoint on a 1024^3 k^-11/3 GRF (eb 1e-4): stored vs recompute.
+    One workspace serves the forward and, in recompute mode, the backward."""
+    import torch
+    from paper_2602_20097_gb300 import qai, synth
+    shape = (1024, 1024, 1024)
+    x = synth.grf(shape, slope=11.0 / 3.0, seed=7, device="cuda")
+    eb = 1e-4 * synth.value_range(x)
+    q = synth.quantize(x, eb)
+    N = q.numel()
+    ws = qai.alloc_workspace(max(qai.workspace_size(shape), qai.workspace_size_backward(shape, True)))
+    out = torch.empty(shape, dtype=torch.float32, device="cuda")
+    ms_fwd = _time_steps(lambda: qai.mitigate(q, eb, out=out, workspace=ws), args.steps)
+    g = (out.double() - x.double()).float()  # dL/dD'' of 0.5 * sum (D'' - x)^2
+    del x
+    res = {}
+    for mode in ("stored", "recompute"):
+        torch.cuda.synchronize()
+        torch.cuda.reset_peak_memory_stats()
+        base = torch.cuda.memory_allocated()
+        saved = qai.alloc_workspace(qai.saved_size(shape)) if mode == "stored" else None
+        bws = ws if mode == "recompute" else qai.alloc_workspace(qai.workspace_size_backward(shape, False))
+
+        def fwd():
+            if mode == "stored":
+                qai.mitigate_save(q, eb, saved=saved, workspace=ws)
+            else:
+                qai.mitigate(q, eb, out=out, workspace=ws)
+
+        def bwd():
+            return qai.mitigate_backward(q, eb, g, saved=saved, workspace=bws, want_grad_dprime=False)
+
+        def step():
+            fwd()
+            return bwd()
+        ms = _time_steps(step, args.steps)
+        fwd()
+        ms_b = _time_steps(bwd, args.steps)
+        qai.profile_read()
+        qai.profile_enable(True)
+        bwd()
+        torch.cuda.synchronize()
+        kst = qai.profile_read()
+        qai.profile_enable(False)
+        _, gp = step()
+        torch.cuda.synchronize()
+        res[mode] = {"ms_fwd_bwd": ms, "ms_bwd": ms_b, "extra_bytes": torch.cuda.max_memory_allocated() - base,
+                     "grad_eta": float(gp[0]), "grad_p": float(gp[1]),
+                     "bwd_kernels_ms": {k: v[1] / v[0] for k, v in kst.items()}}
+        del saved, bws
+    print(json.dumps({"workload": "adjoint_grf1024_eb1e-4", "points": N, "ms_forward": ms_fwd,
+                      "value": N * 4 / (ms_fwd * 1e-3) / 1e9, "unit": "GB/s",
+                      "workspace_bytes": ws.numel(), **res}), flush=True)
+
+
+def run_quality512(args):
+    """SSIM + PSNR kernels on the 512^3 GRF against its mitigated field (eb 1e-3):
+    two kernels, each reading both fields once (16 bytes per point)."""
+    import torch
+    from paper_2602_20097_gb300 import qai, synth
+    shape = tuple(int(v) for v in args.shape.split(",")) if args.shape else (512, 512, 512)
+    x = synth.grf(shape, slope=11.0 / 3.0, seed=2, device="cuda").float().contiguous()
+    eb = REL_EB * synth.value_range(x)
+    q = synth.quantize(x, eb)
+    y = qai.mitigate(q, eb)
+    N = x.numel()
+    ws = qai.alloc_workspace(qai.workspace_size_quality(shape))
+    res = torch.zeros(6, dtype=torch.float64, device="cuda")
+    lib = qai.load()
+    dims = qai._dims(shape)
+
+    def step():
+        qai._check(lib.qai_quality(x.data_ptr(), y.data_ptr(), len(shape), dims, 7, 2, res.data_ptr(), None,
+                                   ws.data_ptr(), ws.numel(), qai._stream()))
+    ms = _time_steps(step, args.steps)
+    qai.profile_read()
+    qai.profile_enable(True)
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    kstats = qai.profile_read()
+    qai.profile_enable(False)
+    peak, peak_src = hbm_peak()
+    kern = {k: {"launches": v[0], "ms": v[1] / v[0], "gbs": v[2] / (v[1] * 1e-3) / 1e9,
+                "frac": v[2] / (v[1] * 1e-3) / 1e9 / peak} for k, v in kstats.items()}
+    r = qai.quality(x, y)
+    print(json.dumps({"workload": "quality_grf" + "x".join(map(str, shape)), "points": N, "ms_per_call": ms,
+                      "value": N * 16 / (ms * 1e-3) / 1e9, "unit": "GB/s (16 B/pt read)",
+                      "frac_of_hbm": N * 16 / (ms * 1e-3) / 1e9 / peak, "peak_gbs": peak, "peak_src": peak_src,
+                      "kernels": kern, "ssim": r["ssim"], "psnr_db": r["psnr"], "windows": r["windows"]}),
+          flush=True)
 
 
 def main():
@@ -354,9 +532,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--shape", default="", help="Z,Y,X override (profiling of smaller cases)")
+    ap.add_argument("--workload", default="grf512", choices=["grf512", "aniso", "batch96", "adjoint1024", "quality512"],
+                    help="grf512: the headline line; the others print their own lines")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "grf512":
+        sys.path.insert(0, ROOT)
+        return {"aniso": run_aniso, "batch96": run_batch96, "adjoint1024": run_adjoint1024,
+                "quality512": run_quality512}[args.workload](args)
     return run_qai(args)
 
 

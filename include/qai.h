@@ -131,7 +131,9 @@ qai_status qai_mitigate_host(const int32_t* h_q, float* h_out, int rank, const i
  *   dL/dp  = sum G S eta eps w (1 - w) (ln k2 - ln k1),  w = 1/(1 + (k1/k2)^p)
  * (dw/dp = 0 where k1 = 0, k2 = 0 or no B2 exists). Stored mode keeps Dist1,
  * Dist2 and S from the forward (9 bytes per point); recompute mode re-runs the
- * forward pipeline in the backward call and keeps nothing in between. */
+ * forward pipeline in the backward call and keeps nothing in between: for 2-D
+ * and 3-D fields its last column pass sums the terms against G in place of
+ * writing D'', so it needs no more device memory than the forward. */
 
 /* Bytes of the saved state of the stored mode (256-byte aligned buffer). */
 qai_status qai_saved_size(int rank, const int64_t* dims, size_t* bytes);
@@ -143,8 +145,9 @@ qai_status qai_mitigate_save(const int32_t* d_q, float* d_out, int rank, const i
                              size_t ws_bytes, cudaStream_t stream);
 
 /* Device workspace of qai_mitigate_backward: 32 KiB of block partial sums
- * (stored mode), plus, with recompute != 0, the forward workspace and two
- * field-sized arrays. */
+ * (stored mode); with recompute != 0, 16 bytes per CTA of the last column
+ * pass (at least 32 KiB) plus the forward workspace, and for 1-D fields two
+ * more field-sized arrays. */
 qai_status qai_workspace_size_backward(int rank, const int64_t* dims, int recompute, size_t* bytes);
 
 /* Adjoint of step E.
@@ -158,7 +161,9 @@ qai_status qai_workspace_size_backward(int rank, const int64_t* dims, int recomp
  *  d_ws, ws_bytes qai_workspace_size_backward(rank, dims, d_saved == NULL)
  *                 bytes, device, 256-byte aligned
  * Sums run in fp32 with compensation, folded into FP64 in a fixed order (the
- * same result on every run). Asynchronous on `stream` like every other call. */
+ * same result on every run of a mode; the two modes group the terms
+ * differently, so they agree to rounding, not bit for bit). Asynchronous on
+ * `stream` like every other call. */
 qai_status qai_mitigate_backward(const int32_t* d_q, const float* d_grad_out, float* d_grad_dprime,
                                  double* d_grad_params, int rank, const int64_t* dims, double eb,
                                  const qai_params* params, const void* d_saved, void* d_ws,
@@ -203,6 +208,45 @@ qai_status qai_autotune_batched(int n, const int32_t* const* d_q, float* const* 
                                 const int32_t* ranks, const int64_t* dims, const double* eb,
                                 const qai_params* params, void* d_ws, size_t ws_bytes,
                                 cudaStream_t stream, qai_batch_choice* choices);
+
+/* ---- Quality metrics (Sec. III-B, Eq. 3 and Eq. 4) -------------------------
+ * How close a field y (D' or D'') is to the original x. Readings: both fields
+ * are normalised by the range of x before SSIM (v' = (v - min x) / range x;
+ * a constant x is only shifted), since Eq. 3's c1 = 1e-4 and c2 = 9e-4 assume
+ * data in [0, 1]; "sample" variances and covariance divide the centred sums
+ * by n - 1 (n = points of a window); on every axis (extent-1 axes dropped) a
+ * window spans m = min(window, extent) points and starts at 0, stride,
+ * 2 stride, ... while it fits; the field's SSIM is the mean over all windows.
+ * The paper's setting is window 7, stride 2. */
+typedef struct {
+    double x_min, x_max; /* range of the original field */
+    double mse;          /* mean of (x - y)^2 over all points */
+    double psnr;         /* Eq. 4 in dB: 20 log10((x_max - x_min) / sqrt(mse));
+                            +inf when mse = 0, -inf when x is constant */
+    double ssim;         /* Eq. 3 averaged over the windows */
+    int64_t windows;     /* number of windows */
+} qai_quality_out;
+
+/* Device workspace of qai_quality for this shape, window and stride. */
+qai_status qai_workspace_size_quality(int rank, const int64_t* dims, int window, int stride,
+                                      size_t* bytes);
+
+/* PSNR and SSIM of y against x.
+ *  d_x, d_y     float[N] original and reconstructed field, device, C order
+ *  rank, dims   as qai_mitigate (the same shapes are accepted)
+ *  window       1..11 points per axis (7 in the paper)
+ *  stride       1..4 (2 in the paper)
+ *  d_result     one qai_quality_out, device; written on `stream`
+ *  d_ssim_map   float[windows] per-window SSIM (z, y, x order of the window
+ *               starts), device, or NULL
+ *  d_ws         qai_workspace_size_quality bytes, device, 256-byte aligned
+ * Sums are fp32 per window and over points with compensation, FP64 across
+ * windows and blocks, added in a fixed order (the same result on every run).
+ * Returns QAI_ERR_INVALID_ARG for NULL inputs, a window or stride out of
+ * range, or a short or misaligned workspace; QAI_ERR_SHAPE as qai_mitigate. */
+qai_status qai_quality(const float* d_x, const float* d_y, int rank, const int64_t* dims, int window,
+                       int stride, qai_quality_out* d_result, float* d_ssim_map, void* d_ws,
+                       size_t ws_bytes, cudaStream_t stream);
 
 /* Largest field (points, after squeezing) that qai_mitigate_static accepts. */
 #define QAI_STATIC_MAX_POINTS 2097152

@@ -1,5 +1,6 @@
 // qai_api.cu -- the C ABI of libqai (see include/qai.h): argument checks,
 // workspace layout and the stream-ordered launch sequence of Algorithm 4.
+#include <algorithm>
 #include <atomic>
 #include <cstdarg>
 #include <cmath>
@@ -188,9 +189,31 @@ qai_status cuda_fail(cudaError_t e, const char* what)
 namespace {
 using namespace qai::host;
 
+// Adjoint mode of the pipeline (rank 2 and 3): the last column pass sums the
+// terms of dL/deta and dL/dp against grad_out instead of writing D''.
+struct GradSink {
+    const float* grad_out;
+    double* partials;  // 2 doubles per CTA of the last pass
+    int nblocks;       // set by run_pipeline
+};
+
+// CTAs of the last EDT2 pass (the sums it leaves in the partials array).
+int final_pass_blocks(const Shape& sh)
+{
+    if (sh.rank == 1) return 0;
+    const int L = sh.rank == 2 ? sh.ny : sh.nz, in_bytes = sh.rank == 2 ? 2 : 4;
+    qai::ColConfig cfg;
+    if (!qai::choose_colpass(L, in_bytes, &cfg)) return -1;
+    qai::ColArgs c{};
+    c.C = sh.rank == 2 ? sh.nx : sh.ny * sh.nx;
+    c.P = sh.rank == 2 ? sh.nz : 1;
+    return qai::colpass_blocks(c, cfg.W);
+}
+
 // The launch sequence of Algorithm 4 on a validated shape.
 qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const qai::MethodArgs& m,
-                        char* ws, const Layout& lay, cudaStream_t st, const qai_debug_out* dbg)
+                        char* ws, const Layout& lay, cudaStream_t st, const qai_debug_out* dbg,
+                        GradSink* grad = nullptr)
 {
     const double N = (double)sh.N;
     uint8_t* eqm = reinterpret_cast<uint8_t*>(ws + lay.eqm);
@@ -278,8 +301,21 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
     auto fuse_e = [&](qai::ColArgs& c) {
         c.out = d_out; c.q = d_q; c.dist1_in = dist1; c.s_in = s; c.dbg_dist2 = d.dist2;
     };
+    // Adjoint mode: the last pass reads G, Dist1, S and the input words.
+    auto last_grad = [&](qai::ColArgs& c, int in_bytes, const char* name) -> qai_status {
+        c.dist1_in = dist1; c.s_in = s; c.grad_out = grad->grad_out; c.partials = grad->partials;
+        qai::ColConfig cfg;
+        if (!qai::choose_colpass(c.L, in_bytes, &cfg))
+            return fail(QAI_ERR_SHAPE, "line length %d does not fit shared memory", c.L);
+        grad->nblocks = qai::colpass_blocks(c, cfg.W);
+        cudaError_t err = timed(name, N * (in_bytes + 4 + 1 + 4), st, [&] {
+            return qai::launch_colpass_grad(in_bytes, c, cfg, in_bytes == 2 ? gx : gxy, st);
+        });
+        return err == cudaSuccess ? QAI_OK : cuda_fail(err, name);
+    };
     if (sh.rank == 2) {
         qai::ColArgs c = y_args(xw);
+        if (grad) return last_grad(c, 2, "colpass2_y_grad");
         fuse_e(c);
         if ((st_ = colpass(2, 2, true, c, "colpass2_y_final", 2 + 4 + 1 + 4 + 4)) != QAI_OK) return st_;
     } else if (sh.rank == 3) {
@@ -287,6 +323,7 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
         c.out_w = yw;
         if ((st_ = colpass(2, 2, false, c, "colpass2_y", 2 + 4)) != QAI_OK) return st_;
         qai::ColArgs cz = z_args(yw);
+        if (grad) return last_grad(cz, 4, "colpass2_z_grad");
         fuse_e(cz);
         if ((st_ = colpass(2, 4, true, cz, "colpass2_z_final", 4 + 4 + 1 + 4 + 4)) != QAI_OK) return st_;
     }
@@ -423,14 +460,34 @@ qai_status qai_mitigate_save(const int32_t* d_q, float* d_out, int rank, const i
     return qai_mitigate(d_q, d_out, rank, dims, eb, params, d_ws, ws_bytes, stream, &d);
 }
 
+}  // extern "C"
+
+namespace {
+// Partials of the adjoint: one pair per block of k_backward, or per CTA of
+// the last column pass when that pass computes the sums.
+size_t backward_partials_bytes(const Shape& sh, bool recompute)
+{
+    int64_t n = qai::kBackwardMaxBlocks;
+    if (recompute) n = std::max<int64_t>(n, final_pass_blocks(sh));
+    return align256(2 * sizeof(double) * (size_t)n);
+}
+
+// Recompute mode: the forward workspace; rank 1 also holds Dist2 and D''.
+size_t recompute_bytes(const Shape& sh)
+{
+    return layout_for(sh, 0).total + (sh.rank == 1 ? 2 * align256((size_t)sh.N * 4) : 0);
+}
+}  // namespace
+
+extern "C" {
+
 qai_status qai_workspace_size_backward(int rank, const int64_t* dims, int recompute, size_t* bytes)
 {
     if (!bytes) return fail(QAI_ERR_INVALID_ARG, "bytes is NULL");
     Shape sh;
     qai_status s = make_shape(rank, dims, &sh);
     if (s != QAI_OK) return s;
-    const size_t partials = align256(2 * sizeof(double) * qai::kBackwardMaxBlocks);
-    *bytes = partials + (recompute ? layout_for(sh, 0).total + 2 * align256((size_t)sh.N * 4) : 0);
+    *bytes = backward_partials_bytes(sh, recompute != 0) + (recompute ? recompute_bytes(sh) : 0);
     return QAI_OK;
 }
 
@@ -458,37 +515,132 @@ qai_status qai_mitigate_backward(const int32_t* d_q, const float* d_grad_out, fl
     b.p = (float)p->idw_power;
     b.eta = p->eta;
     b.eb = eb;
-    size_t need = 0;
-    qai_workspace_size_backward(rank, dims, d_saved ? 0 : 1, &need);
+    if (final_pass_blocks(sh) < 0) return fail(QAI_ERR_SHAPE, "line length does not fit shared memory");
+    const size_t partials = backward_partials_bytes(sh, !d_saved);
+    const size_t need = partials + (d_saved ? 0 : recompute_bytes(sh));
     if (!d_ws || ws_bytes < need)
         return fail(QAI_ERR_INVALID_ARG, "the adjoint needs a workspace of %zu bytes", need);
     if (reinterpret_cast<uintptr_t>(d_ws) & 255) return fail(QAI_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
-    const size_t partials = align256(2 * sizeof(double) * qai::kBackwardMaxBlocks);
     b.partials = static_cast<double*>(d_ws);
+    cudaError_t e;
     if (d_saved) {
         const qai_debug_out v = saved_views(const_cast<void*>(d_saved), sh.N);
         b.dist1 = v.dist1;
         b.dist2 = v.dist2;
         b.s = v.s;
+    } else if (sh.rank >= 2) {
+        // recompute Dist1, S and the EDT2 words with the forward pipeline; its
+        // last column pass sums the adjoint terms in place of writing D''
+        const Layout lay = layout_for(sh, 0);
+        GradSink g{d_grad_out, b.partials, 0};
+        s = run_pipeline(d_q, nullptr, sh, method_args(p, eb), static_cast<char*>(d_ws) + partials, lay,
+                         stream, nullptr, &g);
+        if (s != QAI_OK) return s;
+        if (d_grad_dprime &&
+            (e = cudaMemcpyAsync(d_grad_dprime, d_grad_out, (size_t)sh.N * 4, cudaMemcpyDeviceToDevice, stream)))
+            return cuda_fail(e, "copy dL/dD'");
+        e = timed("backward_sum", (double)g.nblocks * 16, stream, [&] {
+            return qai::launch_partials_sum(b.partials, g.nblocks, eb, p->eta, d_grad_params, stream);
+        });
+        return e == cudaSuccess ? QAI_OK : cuda_fail(e, "backward sum");
     } else {
-        // recompute Dist1, S and Dist2 from q with the forward pipeline
+        // rank 1: recompute Dist1, S and Dist2 with the forward pipeline
         const Layout lay = layout_for(sh, 0);
         char* ws = static_cast<char*>(d_ws) + partials;
         int32_t* dist2 = reinterpret_cast<int32_t*>(ws + lay.total);
         float* scratch_out = reinterpret_cast<float*>(ws + lay.total + align256((size_t)sh.N * 4));
         qai_debug_out d{};
         d.dist2 = dist2;
-        qai_params pc = *p;
-        pc.flags |= QAI_FLAG_OUTPUT_C;
-        s = run_pipeline(d_q, scratch_out, sh, method_args(&pc, eb), ws, lay, stream, &d);
+        s = run_pipeline(d_q, scratch_out, sh, method_args(p, eb), ws, lay, stream, &d);
         if (s != QAI_OK) return s;
         b.dist1 = reinterpret_cast<int32_t*>(ws + lay.dist1);
         b.s = reinterpret_cast<int8_t*>(ws + lay.s);
         b.dist2 = dist2;
     }
-    cudaError_t e = timed("backward", (double)sh.N * (4 + 1 + 4 + 4 + (d_grad_dprime ? 4 : 0)), stream,
+    e = timed("backward", (double)sh.N * (4 + 1 + 4 + 4 + (d_grad_dprime ? 4 : 0)), stream,
               [&] { return qai::launch_backward(b, stream); });
+    count_launch();  // the one-block combine
     if (e != cudaSuccess) return cuda_fail(e, "backward");
+    return QAI_OK;
+}
+
+}  // extern "C"
+
+namespace {
+constexpr int kQualStatBlocks = 1024;
+
+// The window grid of qai_quality on a validated shape (readings in qai.h).
+qai::QualArgs quality_args(const Shape& sh, int window, int stride)
+{
+    qai::QualArgs a{};
+    a.nz = sh.nz; a.ny = sh.ny; a.nx = sh.nx;
+    auto axis = [&](int n, int* m, int* s, int* nw) {
+        *m = n > 1 ? std::min(window, n) : 1;
+        *s = n > 1 ? stride : 1;
+        *nw = (n - *m) / *s + 1;
+    };
+    axis(sh.nz, &a.mz, &a.sz, &a.nwz);
+    axis(sh.ny, &a.my, &a.sy, &a.nwy);
+    axis(sh.nx, &a.mx, &a.sx, &a.nwx);
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    qai::plan_quality(a, sms);
+    return a;
+}
+
+size_t quality_stat_bytes() { return align256(3 * sizeof(double) * kQualStatBlocks); }
+
+qai_status check_window(int window, int stride)
+{
+    if (window < 1 || window > 11) return fail(QAI_ERR_INVALID_ARG, "window %d outside 1..11", window);
+    if (stride < 1 || stride > 4) return fail(QAI_ERR_INVALID_ARG, "stride %d outside 1..4", stride);
+    return QAI_OK;
+}
+}  // namespace
+
+extern "C" {
+
+qai_status qai_workspace_size_quality(int rank, const int64_t* dims, int window, int stride, size_t* bytes)
+{
+    if (!bytes) return fail(QAI_ERR_INVALID_ARG, "bytes is NULL");
+    qai_status s = check_window(window, stride);
+    if (s != QAI_OK) return s;
+    Shape sh;
+    if ((s = make_shape(rank, dims, &sh)) != QAI_OK) return s;
+    const qai::QualArgs a = quality_args(sh, window, stride);
+    *bytes = quality_stat_bytes() + align256(sizeof(double) * (size_t)qai::quality_ssim_blocks(a));
+    return QAI_OK;
+}
+
+qai_status qai_quality(const float* d_x, const float* d_y, int rank, const int64_t* dims, int window,
+                       int stride, qai_quality_out* d_result, float* d_ssim_map, void* d_ws,
+                       size_t ws_bytes, cudaStream_t stream)
+{
+    g_last_error.clear();
+    if (!d_x || !d_y || !d_result) return fail(QAI_ERR_INVALID_ARG, "d_x, d_y and d_result must be non-NULL");
+    size_t need = 0;
+    qai_status s = qai_workspace_size_quality(rank, dims, window, stride, &need);
+    if (s != QAI_OK) return s;
+    if (!d_ws || ws_bytes < need)
+        return fail(QAI_ERR_INVALID_ARG, "qai_quality needs a workspace of %zu bytes", need);
+    if (reinterpret_cast<uintptr_t>(d_ws) & 255) return fail(QAI_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    Shape sh;
+    make_shape(rank, dims, &sh);
+    qai::QualArgs a = quality_args(sh, window, stride);
+    a.x = d_x;
+    a.y = d_y;
+    a.result = d_result;
+    a.map = d_ssim_map;
+    const int blocks = (int)std::min<int64_t>(kQualStatBlocks, (sh.N + 255) / 256);
+    a.partials = static_cast<double*>(d_ws);
+    cudaError_t e = timed("quality_stats", (double)sh.N * 8, stream,
+                          [&] { return qai::launch_quality_stats(a, sh.N, blocks, stream); });
+    count_launch();  // the one-block combine
+    if (e != cudaSuccess) return cuda_fail(e, "quality stats");
+    a.partials = reinterpret_cast<double*>(static_cast<char*>(d_ws) + quality_stat_bytes());
+    e = timed("quality_ssim", (double)sh.N * 8, stream, [&] { return qai::launch_quality_ssim(a, stream); });
+    count_launch();
+    if (e != cudaSuccess) return cuda_fail(e, "quality ssim");
     return QAI_OK;
 }
 

@@ -16,17 +16,6 @@
 namespace qai {
 namespace {
 
-struct Kahan {
-    float s = 0.f, c = 0.f;
-    __device__ void add(float v)
-    {
-        const float y = v - c;
-        const float t = s + y;
-        c = (t - s) - y;
-        s = t;
-    }
-};
-
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll
@@ -36,39 +25,17 @@ __device__ __forceinline__ double warp_sum(double v)
 
 __global__ void __launch_bounds__(256) k_backward(BackArgs a)
 {
-    Kahan ke, kp;
-    double de = 0.0, dp = 0.0;
-    int since = 0;
+    GradAcc acc;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += stride) {
         const float g = __ldg(a.grad_out + i);
         if (a.grad_dprime) a.grad_dprime[i] = g;
-        const int s = __ldg(a.s + i);
-        if (s != 0) {
-            const int d1 = __ldg(a.dist1 + i), d2 = __ldg(a.dist2 + i);
-            float w = 1.0f, dw = 0.0f;
-            if (d1 != 0 && d2 == 0) {
-                w = 0.0f;
-            } else if (d1 != 0 && d2 != kDistInf) {
-                const float l1 = logf((float)d1), l2 = logf((float)d2);
-                const float t = expf(0.5f * a.p * (l1 - l2));
-                w = 1.0f / (1.0f + t);
-                dw = w * (1.0f - w) * 0.5f * (l2 - l1);
-            }
-            const float gs = (float)s * g;
-            ke.add(gs * w);
-            kp.add(gs * dw);
-        }
-        if (++since == 64) {
-            de += (double)ke.s;
-            dp += (double)kp.s;
-            ke = Kahan();
-            kp = Kahan();
-            since = 0;
-        }
+        float te, tp;
+        grad_terms(g, __ldg(a.s + i), __ldg(a.dist1 + i), __ldg(a.dist2 + i), a.p, te, tp);
+        acc.add(te, tp);
     }
-    de += (double)ke.s;
-    dp += (double)kp.s;
+    acc.fold();
+    double de = acc.de, dp = acc.dp;
     __shared__ double red[2][8];
     de = warp_sum(de);
     dp = warp_sum(dp);
@@ -89,19 +56,42 @@ __global__ void __launch_bounds__(256) k_backward(BackArgs a)
     }
 }
 
-__global__ void __launch_bounds__(32) k_backward_final(BackArgs a, int nblocks)
+// Thread t adds partials t, t + 256, ... in order; thread 0 then adds the
+// 256 subtotals in order. The order depends only on nblocks.
+__global__ void __launch_bounds__(256) k_backward_final(BackArgs a, int nblocks)
 {
-    if (threadIdx.x != 0) return;
+    __shared__ double red[2][256];
     double te = 0.0, tp = 0.0;
-    for (int k = 0; k < nblocks; ++k) {
+    for (int k = threadIdx.x; k < nblocks; k += 256) {
         te += a.partials[2 * k];
         tp += a.partials[2 * k + 1];
+    }
+    red[0][threadIdx.x] = te;
+    red[1][threadIdx.x] = tp;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    te = tp = 0.0;
+    for (int k = 0; k < 256; ++k) {
+        te += red[0][k];
+        tp += red[1][k];
     }
     a.grad_params[0] = te * a.eb;
     a.grad_params[1] = tp * a.eta * a.eb;
 }
 
 }  // namespace
+
+cudaError_t launch_partials_sum(const double* partials, int nblocks, double eb, double eta,
+                                double* grad_params, cudaStream_t st)
+{
+    BackArgs a{};
+    a.partials = const_cast<double*>(partials);
+    a.grad_params = grad_params;
+    a.eb = eb;
+    a.eta = eta;
+    k_backward_final<<<1, 256, 0, st>>>(a, nblocks);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_backward(const BackArgs& a, cudaStream_t st)
 {
@@ -114,7 +104,7 @@ cudaError_t launch_backward(const BackArgs& a, cudaStream_t st)
     k_backward<<<(int)blocks, 256, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_backward_final<<<1, 32, 0, st>>>(a, (int)blocks);
+    k_backward_final<<<1, 256, 0, st>>>(a, (int)blocks);
     return cudaGetLastError();
 }
 

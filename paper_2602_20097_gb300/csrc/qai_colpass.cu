@@ -72,8 +72,9 @@ __device__ __forceinline__ void cp_async(void* dst, const void* src, int bytes)
 // Writes the result of one point: `val` is its squared distance, `w` the
 // input word of the winning row (phase 1: carries the sign code), `src` the
 // element index of that row in the same column (phase 1 index carry).
-template <int PHASE, int IN, bool FINAL, bool DEBUG, class Word>
-__device__ __forceinline__ void emit_point(const ColArgs& a, int idx, int src, int val, Word w, bool valid)
+template <int PHASE, int IN, bool FINAL, bool DEBUG, bool GRAD, class Word>
+__device__ __forceinline__ void emit_point(const ColArgs& a, int idx, int src, int val, Word w, bool valid,
+                                           GradAcc& acc)
 {
     if (PHASE == 1) {
         const int code = valid ? (int)(w & 3u) : 0;
@@ -88,6 +89,11 @@ __device__ __forceinline__ void emit_point(const ColArgs& a, int idx, int src, i
         const int32_t d = valid ? val : kDistInf;
         if (!FINAL) {
             static_cast<uint32_t*>(a.out_w)[idx] = valid ? (uint32_t)val : kInf32;
+        } else if (GRAD) {
+            float te, tp;
+            grad_terms(__ldg(a.grad_out + idx), __ldg(a.s_in + idx), __ldg(a.dist1_in + idx), d,
+                       a.m.idw_power, te, tp);
+            acc.add(te, tp);
         } else {
             a.out[idx] = compensate(__ldg(a.q + idx), __ldg(a.dist1_in + idx), d, __ldg(a.s_in + idx), a.m);
             if (DEBUG && a.dbg_dist2) a.dbg_dist2[idx] = d;
@@ -96,9 +102,12 @@ __device__ __forceinline__ void emit_point(const ColArgs& a, int idx, int src, i
 }
 
 // One CTA of the column pass: tile `blk` of the lines described by `a`.
-template <int PHASE, int IN, bool FINAL, bool DEBUG, bool NARROW>
+// GRAD (last phase-2 pass only): accumulate the adjoint terms of step E
+// instead of writing D'', and store the CTA's two sums in a.partials.
+template <int PHASE, int IN, bool FINAL, bool DEBUG, bool NARROW, bool GRAD = false>
 __device__ __forceinline__ void colpass_tile(const ColArgs& a, const int blk)
 {
+    GradAcc acc;
     using Word = std::conditional_t<IN == 2, uint16_t, uint32_t>;
     constexpr Word kWInf = IN == 2 ? (Word)kInf16 : (Word)kInf32;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -190,13 +199,15 @@ __device__ __forceinline__ void colpass_tile(const ColArgs& a, const int blk)
                     *vfail = 1;
                     break;
                 }
-                emit_point<PHASE, IN, FINAL, DEBUG>(a, pbase + r * RS + c, pbase + bh * RS + c, best, bw, true);
+                emit_point<PHASE, IN, FINAL, DEBUG, GRAD>(a, pbase + r * RS + c, pbase + bh * RS + c, best, bw, true, acc);
             }
         }
         __syncthreads();
-        if (!s_fail) return;
     }
+    const bool use_envelope = s_fail != 0;  // CTA-uniform
+    if (GRAD && use_envelope) acc = GradAcc();  // the envelope path redoes every row
 
+    auto envelope_path = [&]() {
     // ---- build: Algorithm 1's envelope over this band ------------------------
     uint16_t* scol = stk + col;  // stack entry i of this column at scol[i * W]
     {
@@ -324,7 +335,7 @@ __device__ __forceinline__ void colpass_tile(const ColArgs& a, const int blk)
     const int nl = nlst[col];
     if (nl == 0) {  // empty column: no site reaches it
         for (int r = r0; r < r1; ++r)
-            emit_point<PHASE, IN, FINAL, DEBUG>(a, pbase + r * RS + c, 0, 0, (Word)0, false);
+            emit_point<PHASE, IN, FINAL, DEBUG, GRAD>(a, pbase + r * RS + c, 0, 0, (Word)0, false, acc);
         return;
     }
     // envelope entry of row r0: the first entry that the next one does not
@@ -384,15 +395,19 @@ __device__ __forceinline__ void colpass_tile(const ColArgs& a, const int blk)
     constexpr bool kFuseE = PHASE == 2 && FINAL;
     int idx = pbase + r0 * RS + c;
     int pq = 0, pd1 = 0, ps = 0;
+    float pg = 0.f;
     if (kFuseE) {
-        pq = __ldg(a.q + idx);
+        if (GRAD) pg = __ldg(a.grad_out + idx);
+        else pq = __ldg(a.q + idx);
         pd1 = __ldg(a.dist1_in + idx);
         ps = __ldg(a.s_in + idx);
     }
     for (int r = r0; r < r1; ++r) {
         int nq = 0, nd1 = 0, nsg = 0;
+        float ng = 0.f;
         if (kFuseE && r + 1 < r1) {
-            nq = __ldg(a.q + idx + RS);
+            if (GRAD) ng = __ldg(a.grad_out + idx + RS);
+            else nq = __ldg(a.q + idx + RS);
             nd1 = __ldg(a.dist1_in + idx + RS);
             nsg = __ldg(a.s_in + idx + RS);
         }
@@ -415,15 +430,41 @@ __device__ __forceinline__ void colpass_tile(const ColArgs& a, const int blk)
         }
         const int val = g + (h - r) * (h - r);
         if (kFuseE) {
-            a.out[idx] = compensate(pq, pd1, val, ps, a.m);
-            if (DEBUG && a.dbg_dist2) a.dbg_dist2[idx] = val;
+            if (GRAD) {
+                float te, tp;
+                grad_terms(pg, ps, pd1, val, a.m.idw_power, te, tp);
+                acc.add(te, tp);
+            } else {
+                a.out[idx] = compensate(pq, pd1, val, ps, a.m);
+                if (DEBUG && a.dbg_dist2) a.dbg_dist2[idx] = val;
+            }
             pq = nq;
+            pg = ng;
             pd1 = nd1;
             ps = nsg;
         } else {
-            emit_point<PHASE, IN, FINAL, DEBUG>(a, idx, pbase + h * RS + c, val, w, true);
+            emit_point<PHASE, IN, FINAL, DEBUG, GRAD>(a, idx, pbase + h * RS + c, val, w, true, acc);
         }
         idx += RS;
+    }
+    };  // envelope_path
+    if (use_envelope) envelope_path();
+
+    if constexpr (GRAD) {  // the CTA's two sums, added in thread order
+        __shared__ double red[2][512];
+        acc.fold();
+        red[0][tid] = acc.de;
+        red[1][tid] = acc.dp;
+        __syncthreads();
+        if (tid == 0) {
+            double de = 0.0, dp = 0.0;
+            for (int k = 0; k < nthr; ++k) {
+                de += red[0][k];
+                dp += red[1][k];
+            }
+            a.partials[2 * blk] = de;
+            a.partials[2 * blk + 1] = dp;
+        }
     }
 }
 
@@ -449,6 +490,13 @@ __global__ void __launch_bounds__(512, IN == 2 ? 3 : 2) k_colpass_grouped(const 
     const ColArgs& a = t.args[lo];
     if (a.narrow) colpass_tile<PHASE, IN, FINAL, false, true>(a, b - t.first_block[lo]);
     else colpass_tile<PHASE, IN, FINAL, false, false>(a, b - t.first_block[lo]);
+}
+
+// The last phase-2 pass in adjoint mode (IN = 2: 2-D fields, 4: 3-D).
+template <int IN, bool NARROW>
+__global__ void __launch_bounds__(512, 2) k_colpass_grad(ColArgs a)
+{
+    colpass_tile<2, IN, true, false, NARROW, true>(a, blockIdx.x);
 }
 
 template <int PHASE, int IN, bool FINAL>
@@ -551,6 +599,24 @@ cudaError_t launch_colpass(int phase, int in_bytes, bool final_pass, ColArgs& a,
     if (in_bytes == 2) return final_pass ? go<2, 2, true>(a, debug, narrow, grid, block, cfg.smem, st)
                                          : go<2, 2, false>(a, debug, narrow, grid, block, cfg.smem, st);
     return go<2, 4, true>(a, debug, narrow, grid, block, cfg.smem, st);
+}
+
+}  // namespace qai
+
+namespace qai {
+
+cudaError_t launch_colpass_grad(int in_bytes, ColArgs& a, const ColConfig& cfg, int64_t max_g, cudaStream_t st)
+{
+    prepare_colpass(a, in_bytes, cfg, max_g);
+    const dim3 grid(colpass_blocks(a, cfg.W)), block(cfg.W, cfg.B);
+    auto run = [&](auto kern) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
+        if (e != cudaSuccess) return e;
+        kern<<<grid, block, cfg.smem, st>>>(a);
+        return cudaGetLastError();
+    };
+    if (in_bytes == 2) return a.narrow ? run(k_colpass_grad<2, true>) : run(k_colpass_grad<2, false>);
+    return a.narrow ? run(k_colpass_grad<4, true>) : run(k_colpass_grad<4, false>);
 }
 
 }  // namespace qai

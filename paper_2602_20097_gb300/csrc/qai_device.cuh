@@ -83,6 +83,8 @@ struct ColArgs {
     const int32_t* dbg_idx_in;   // phase 1: carried nearest-site index
     int32_t* dbg_idx_out;
     int32_t* dbg_dist2;      // phase 2 final
+    const float* grad_out;   // phase 2 final, adjoint mode: dL/dD'' (no D'' written)
+    double* partials;        // adjoint mode: two FP64 sums per CTA
     MethodArgs m;
 };
 
@@ -100,6 +102,53 @@ struct RowTable {
     int smem_nx;                      // x extent the per-warp shared memory is sized for
     int first_row[kMaxGroup + 1];     // row offsets; first_row[n] = rows in total
     RowArgs args[kMaxGroup];
+};
+
+// Adjoint of step E for one point (with the EDT assignment fixed): the terms
+// of dL/deta / eps and dL/dp / (eta eps) for G = dL/dD'', S, Dist1, Dist2:
+//   G S w  and  G S w (1 - w) (ln k2 - ln k1),  w = 1 / (1 + (k1/k2)^p),
+// with dw/dp = 0 where w is fixed (k1 = 0 -> 1, k2 = 0 -> 0, no B2 -> 1).
+__device__ __forceinline__ void grad_terms(float g, int s, int32_t d1, int32_t d2, float p,
+                                           float& te, float& tp)
+{
+    float w = 1.0f, dw = 0.0f;
+    if (d1 != 0 && d2 == 0) {
+        w = 0.0f;
+    } else if (d1 != 0 && d2 != kDistInf) {
+        const float l1 = logf((float)d1), l2 = logf((float)d2);
+        const float t = expf(0.5f * p * (l1 - l2));
+        w = 1.0f / (1.0f + t);
+        dw = w * (1.0f - w) * 0.5f * (l2 - l1);
+    }
+    const float gs = s == 0 ? 0.0f : (s > 0 ? g : -g);
+    te = gs * w;
+    tp = gs * dw;
+}
+
+// Per-thread sums of the adjoint terms: fp32 with Kahan compensation, folded
+// into FP64 every 64 terms.
+struct GradAcc {
+    float se = 0.f, ce = 0.f, sp = 0.f, cp = 0.f;
+    double de = 0.0, dp = 0.0;
+    int since = 0;
+    __device__ __forceinline__ void add(float te, float tp)
+    {
+        float y = te - ce, t = se + y;
+        ce = (t - se) - y;
+        se = t;
+        y = tp - cp;
+        t = sp + y;
+        cp = (t - sp) - y;
+        sp = t;
+        if (++since == 64) fold();
+    }
+    __device__ __forceinline__ void fold()
+    {
+        de += (double)se;
+        dp += (double)sp;
+        se = ce = sp = cp = 0.f;
+        since = 0;
+    }
 };
 
 // Adjoint of step E: a reduction over the points (qai_backward.cu).

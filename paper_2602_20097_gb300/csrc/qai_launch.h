@@ -3,6 +3,7 @@
 #include <cstddef>
 #include <cuda_runtime.h>
 
+#include "qai.h"
 #include "qai_device.cuh"
 
 namespace qai {
@@ -29,6 +30,9 @@ bool choose_colpass_with(int L, int in_bytes, int rows_per_band, int max_w, ColC
 // Sets a.bands, a.load_bytes and a.narrow for a launch with `cfg`.
 void prepare_colpass(ColArgs& a, int in_bytes, const ColConfig& cfg, int64_t max_g);
 int colpass_blocks(const ColArgs& a, int W);
+// The last phase-2 column pass in adjoint mode: a.grad_out, a.partials set,
+// one pair of FP64 sums per CTA (colpass_blocks(a, cfg.W) CTAs).
+cudaError_t launch_colpass_grad(int in_bytes, ColArgs& a, const ColConfig& cfg, int64_t max_g, cudaStream_t st);
 cudaError_t launch_colpass_grouped(int phase, int in_bytes, bool final_pass, const ColTable& t,
                                    const ColConfig& cfg, cudaStream_t st);
 // max_g bounds the squared distances carried by the input words; it decides
@@ -38,8 +42,33 @@ cudaError_t launch_colpass(int phase, int in_bytes, bool final_pass, ColArgs& a,
 
 // Adjoint reduction of step E (qai_backward.cu).
 cudaError_t launch_backward(const BackArgs& a, cudaStream_t st);
+// Adds the per-CTA partial sums of the fused adjoint pass in a fixed order.
+cudaError_t launch_partials_sum(const double* partials, int nblocks, double eb, double eta,
+                                double* grad_params, cudaStream_t st);
 
 // Records `msg` as qai_last_error() of the calling host thread.
 void set_last_error(const char* msg);
+
+// Quality metrics (qai_quality.cu). The field is viewed as nz x ny x nx with
+// window extents m* and strides s* per axis (1 on the axes a field lacks).
+struct QualArgs {
+    const float* x;
+    const float* y;
+    int nz, ny, nx;
+    int mz, my, mx;
+    int sz, sy, sx;
+    int nwz, nwy, nwx;  // window counts
+    int tz, gx, gy;     // windows per CTA along z, CTA grid along x and y
+    qai_quality_out* result;
+    double* partials;
+    float* map;         // per-window SSIM or nullptr
+};
+void plan_quality(QualArgs& a, int sms);
+int quality_ssim_blocks(const QualArgs& a);
+size_t quality_smem(const QualArgs& a);
+// min / max / MSE / PSNR: `blocks` block partials (3 doubles each) then one block.
+cudaError_t launch_quality_stats(QualArgs& a, int64_t N, int blocks, cudaStream_t st);
+// SSIM: quality_ssim_blocks(a) partials (1 double each) then one block.
+cudaError_t launch_quality_ssim(QualArgs& a, cudaStream_t st);
 
 }  // namespace qai

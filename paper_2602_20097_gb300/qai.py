@@ -84,6 +84,10 @@ SIGNATURES = {
                                             ctypes.c_size_t, P, ctypes.POINTER(BatchChoice)]),
     "qai_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "qai_profile_read": (ctypes.c_int, [ctypes.POINTER(KernelStat), ctypes.c_int]),
+    "qai_workspace_size_quality": (ctypes.c_int, [ctypes.c_int, P, ctypes.c_int, ctypes.c_int,
+                                                  ctypes.POINTER(ctypes.c_size_t)]),
+    "qai_quality": (ctypes.c_int, [P, P, ctypes.c_int, P, ctypes.c_int, ctypes.c_int, P, P, P,
+                                   ctypes.c_size_t, P]),
     "qai_launch_count": (ctypes.c_int64, []),
     "qai_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "qai_last_error": (ctypes.c_char_p, []),
@@ -386,6 +390,48 @@ def autotune_batched(batch: Batch, stream=None, **kw):
 
 
 STATIC_MAX_POINTS = 2097152
+
+
+def workspace_size_quality(shape, window: int = 7, stride: int = 2) -> int:
+    n = ctypes.c_size_t()
+    _check(load().qai_workspace_size_quality(len(shape), _dims(shape), int(window), int(stride),
+                                             ctypes.byref(n)))
+    return int(n.value)
+
+
+def quality(x: torch.Tensor, y: torch.Tensor, window: int = 7, stride: int = 2, ssim_map: bool = False,
+            workspace: torch.Tensor | None = None, stream=None):
+    """PSNR (Eq. 4) and SSIM (Eq. 3 over sliding windows) of ``y`` against the
+    original ``x`` on the GPU. Returns a dict (x_min, x_max, mse, psnr, ssim,
+    windows), plus the per-window SSIM tensor under "map" when ``ssim_map``.
+    Synchronises the stream to read the six numbers back."""
+    lib = load()
+    for t in (x, y):
+        if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+            raise QAIError("x and y must be contiguous float32 CUDA tensors")
+    if x.shape != y.shape:
+        raise QAIError("x and y must have the same shape")
+    shape = tuple(d for d in x.shape if d != 1) or (1,)   # the C ABI squeezes the same way
+    if workspace is None:
+        workspace = alloc_workspace(workspace_size_quality(shape, window, stride), x.device)
+    res = torch.zeros(6, dtype=torch.float64, device=x.device)
+    mp = None
+    if ssim_map:
+        counts = []
+        for d in shape:
+            m = min(window, d)
+            counts.append((d - m) // stride + 1)
+        mp = torch.empty(counts, dtype=torch.float32, device=x.device)
+    st = _stream(stream)
+    _check(lib.qai_quality(x.data_ptr(), y.data_ptr(), len(shape), _dims(shape), int(window), int(stride),
+                           res.data_ptr(), mp.data_ptr() if mp is not None else None, workspace.data_ptr(),
+                           workspace.numel(), st))
+    vals = res.cpu()
+    out = {"x_min": float(vals[0]), "x_max": float(vals[1]), "mse": float(vals[2]), "psnr": float(vals[3]),
+           "ssim": float(vals[4]), "windows": int(vals[5:6].view(torch.int64)[0])}
+    if mp is not None:
+        out["map"] = mp
+    return out
 
 
 def mitigate_static(q: torch.Tensor, eb: float, out: torch.Tensor | None = None, stream=None, **kw):

@@ -102,7 +102,10 @@ def test_adjoint_sizes_and_argument_errors():
     lib = qai.load()
     assert qai.saved_size((64, 64, 64)) >= 64 ** 3 * 9
     assert 0 < qai.workspace_size_backward((64, 64, 64), False) <= 64 * 1024
-    assert qai.workspace_size_backward((64, 64, 64), True) >= qai.workspace_size((64, 64, 64)) + 2 * 4 * 64 ** 3
+    # recompute mode for a 3-D field: the forward workspace and the partials only
+    fwd = qai.workspace_size((64, 64, 64))
+    assert fwd < qai.workspace_size_backward((64, 64, 64), True) < fwd + 4 * 64 ** 3
+    assert qai.workspace_size_backward((5000,), True) >= qai.workspace_size((5000,)) + 2 * 4 * 5000
     shape = (8, 8, 8)
     rc = lib.qai_mitigate_backward(ctypes.c_void_p(16), None, None, ctypes.c_void_p(16), 3, qai._dims(shape),
                                    0.1, None, None, None, 0, None)
@@ -113,3 +116,19 @@ def test_adjoint_sizes_and_argument_errors():
     rc = lib.qai_mitigate_save(ctypes.c_void_p(16), ctypes.c_void_p(16), 3, qai._dims(shape), 0.1, None,
                                ctypes.c_void_p(257), None, 0, None)
     assert rc == 1                                     # misaligned saved state
+
+
+def test_quality_sizes_and_argument_errors():
+    lib = qai.load()
+    assert 0 < qai.workspace_size_quality((512, 512, 512)) < 1 << 20
+    assert qai.workspace_size_quality((1800, 3600), 7, 2) > 0
+    n = ctypes.c_size_t()
+    for w, s in ((0, 2), (12, 2), (7, 0), (7, 5)):
+        assert lib.qai_workspace_size_quality(3, qai._dims((8, 8, 8)), w, s, ctypes.byref(n)) == 1
+    shape = (8, 8, 8)
+    rc = lib.qai_quality(None, ctypes.c_void_p(256), 3, qai._dims(shape), 7, 2, ctypes.c_void_p(256), None,
+                         ctypes.c_void_p(256), 1 << 20, None)
+    assert rc == 1                                        # NULL x
+    rc = lib.qai_quality(ctypes.c_void_p(256), ctypes.c_void_p(256), 3, qai._dims(shape), 7, 2,
+                         ctypes.c_void_p(256), None, ctypes.c_void_p(256), 8, None)
+    assert rc == 1 and b"workspace" in lib.qai_last_error()

@@ -48,14 +48,18 @@ def test_gradient_matches_fp64_oracle(name, shape, seed, rel, eta, p, stored):
         assert abs(got[k] - ref[k]) <= 1e-5 * abs(ref[k]) + 1e-7 * scale, (k, got[k], ref[k])
 
 
-def test_stored_and_recompute_modes_agree_bitwise():
-    x, q, eb = _case("grf", (64, 80, 96), 6, 1e-2)
+@pytest.mark.parametrize("shape", [(64, 80, 96), (200, 300), (3000,)], ids=str)
+def test_modes_agree_and_each_is_deterministic(shape):
+    x, q, eb = _case("grf" if len(shape) > 1 else "sinusoids", shape, 6, 1e-2)
     g = _grad_out(x, q, eb, 0.9, 1.0)
     saved = qai.mitigate_save(q, eb)[1]
-    _, a = qai.mitigate_backward(q, eb, g, saved=saved, want_grad_dprime=False)
-    _, b = qai.mitigate_backward(q, eb, g, saved=None, want_grad_dprime=False)
+    a = [qai.mitigate_backward(q, eb, g, saved=saved, want_grad_dprime=False)[1] for _ in range(2)]
+    b = [qai.mitigate_backward(q, eb, g, saved=None)[1] for _ in range(2)]
     torch.cuda.synchronize()
-    assert torch.equal(a, b)
+    assert torch.equal(a[0], a[1]) and torch.equal(b[0], b[1])
+    scale = float(torch.sum(torch.abs(g.double()))) * eb
+    # the modes group the fp32 partial sums differently: agreement to rounding
+    assert torch.allclose(a[0], b[0], rtol=1e-6, atol=1e-8 * scale)
 
 
 def test_crops_of_a_larger_field():

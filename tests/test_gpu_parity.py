@@ -89,7 +89,7 @@ def test_parity_maximum_extents(shape):
 
 def test_golden_vectors_on_gpu():
     import glob, json, os
-    for path in sorted(glob.glob(os.path.join(os.path.dirname(__file__), "golden", "*.json"))):
+    for path in sorted(glob.glob(os.path.join(os.path.dirname(__file__), "golden", "V*.json"))):
         fx = json.load(open(path))
         p = fx["params"]
         out, maps = gpu_run(np.array(fx["q"], np.int32), fx["eb"], eta=fx["eta"],

@@ -19,7 +19,7 @@ import oracle
 from paper_2602_20097_gb300 import synth
 from tests import oracle_checks as oc
 
-GOLDEN = sorted(glob.glob(os.path.join(os.path.dirname(__file__), "golden", "*.json")))
+GOLDEN = sorted(glob.glob(os.path.join(os.path.dirname(__file__), "golden", "V*.json")))
 
 
 @pytest.mark.parametrize("path", GOLDEN, ids=[os.path.basename(p)[:-5] for p in GOLDEN])
