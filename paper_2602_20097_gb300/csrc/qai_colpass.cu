@@ -450,23 +450,27 @@ __device__ __forceinline__ void colpass_tile(const ColArgs& a, const int blk)
     };  // envelope_path
     if (use_envelope) envelope_path();
 
-    if constexpr (GRAD) {  // the CTA's two sums, added in thread order
-        __shared__ double red[2][512];
-        acc.fold();
-        red[0][tid] = acc.de;
-        red[1][tid] = acc.dp;
+    if constexpr (GRAD) {  // the CTA's two sums: a fixed float-float tree over the threads
+        __shared__ float red[4][512];
+        red[0][tid] = acc.se;
+        red[1][tid] = -acc.ce;
+        red[2][tid] = acc.sp;
+        red[3][tid] = -acc.cp;
         __syncthreads();
-        if (tid == 0) {
-            double de = 0.0, dp = 0.0;
-            for (int k = 0; k < nthr; ++k) {
-                de += red[0][k];
-                dp += red[1][k];
+        for (int n = nthr; n > 1;) {
+            const int h = (n + 1) >> 1;
+            if (tid < n - h) {
+                ff_add(red[0][tid], red[1][tid], red[0][tid + h], red[1][tid + h]);
+                ff_add(red[2][tid], red[3][tid], red[2][tid + h], red[3][tid + h]);
             }
-            a.partials[2 * blk] = de;
-            a.partials[2 * blk + 1] = dp;
+            __syncthreads();
+            n = h;
         }
-    }
-}
+        if (tid == 0) {
+            a.partials[2 * blk] = (double)red[0][0] + (double)red[1][0];
+            a.partials[2 * blk + 1] = (double)red[2][0] + (double)red[3][0];
+        }
+    }}
 
 template <int PHASE, int IN, bool FINAL, bool DEBUG, bool NARROW>
 __global__ void __launch_bounds__(512, IN == 2 ? 3 : 2) k_colpass(ColArgs a)

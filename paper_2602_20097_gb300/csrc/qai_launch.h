@@ -59,6 +59,7 @@ struct QualArgs {
     int sz, sy, sx;
     int nwz, nwy, nwx;  // window counts
     int tz, gx, gy;     // windows per CTA along z, CTA grid along x and y
+    int vec;            // 16-byte staging copies (set by launch_quality_ssim)
     qai_quality_out* result;
     double* partials;
     float* map;         // per-window SSIM or nullptr
