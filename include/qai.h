@@ -259,8 +259,8 @@ qai_status qai_quality(const float* d_x, const float* d_y, int rank, const int64
  * no counterpart; it is a deployment convenience of this library.
  *
  * Instead of a workspace it uses one scratch array compiled into the library
- * (a 256-byte aligned __device__ array of 12 * QAI_STATIC_MAX_POINTS + 1280
- * bytes, about 24 MiB). Every GPU that loads the library holds that array
+ * (a 256-byte aligned __device__ array of 13 * QAI_STATIC_MAX_POINTS + 1536
+ * bytes, about 26 MiB). Every GPU that loads the library holds that array
  * until the process exits. The call itself allocates nothing: no cudaMalloc,
  * no cudaFree, no library routine that allocates.
  *  d_q, d_out, rank, dims, eb, params, stream: as for qai_mitigate (the

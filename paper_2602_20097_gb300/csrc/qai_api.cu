@@ -148,6 +148,8 @@ Layout layout_for(const Shape& s, uint32_t flags)
     l.xw = s.rank >= 2 ? take(N * 2) : 0;
     l.yw = s.rank >= 3 ? take(N * 4) : 0;
     l.idx = (flags & QAI_WS_INDEX) && s.rank >= 2 ? take(N * 4) : 0;
+    // a uint16 count per column of the last column pass (z: ny * nx, y: nx)
+    l.cflag = s.rank == 3 ? take((size_t)s.ny * s.nx * 2) : s.rank == 2 ? take((size_t)s.nx * 2) : 0;
     l.total = off;
     return l;
 }
@@ -266,9 +268,10 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
         return c;
     };
     qai_status st_;
+    uint16_t* cflag = sh.rank >= 2 ? reinterpret_cast<uint16_t*>(ws + lay.cflag) : nullptr;
     if (sh.rank == 2) {
         qai::ColArgs c = y_args(xw);
-        c.dist1 = dist1; c.s_out = s;
+        c.dist1 = dist1; c.s_out = s; c.col_count_out = cflag;
         if (d.idx1) { c.dbg_idx_in = idx_tmp; c.dbg_idx_out = d.idx1; }
         if ((st_ = colpass(1, 2, true, c, "colpass1_y_final", 2 + 4 + 1)) != QAI_OK) return st_;
     } else if (sh.rank == 3) {
@@ -277,7 +280,7 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
         if (d.idx1) { c.dbg_idx_in = d.idx1; c.dbg_idx_out = idx_tmp; }
         if ((st_ = colpass(1, 2, false, c, "colpass1_y", 2 + 4)) != QAI_OK) return st_;
         qai::ColArgs cz = z_args(yw);
-        cz.dist1 = dist1; cz.s_out = s;
+        cz.dist1 = dist1; cz.s_out = s; cz.col_count_out = cflag;
         if (d.idx1) { cz.dbg_idx_in = idx_tmp; cz.dbg_idx_out = d.idx1; }
         if ((st_ = colpass(1, 4, true, cz, "colpass1_z_final", 4 + 4 + 1)) != QAI_OK) return st_;
     }
@@ -300,10 +303,12 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
     // EDT2 along y (and z), the last pass fused with step E.
     auto fuse_e = [&](qai::ColArgs& c) {
         c.out = d_out; c.q = d_q; c.dist1_in = dist1; c.s_in = s; c.dbg_dist2 = d.dist2;
+        c.col_count_in = cflag;
     };
     // Adjoint mode: the last pass reads G, Dist1, S and the input words.
     auto last_grad = [&](qai::ColArgs& c, int in_bytes, const char* name) -> qai_status {
         c.dist1_in = dist1; c.s_in = s; c.grad_out = grad->grad_out; c.partials = grad->partials;
+        c.col_count_in = cflag;
         qai::ColConfig cfg;
         if (!qai::choose_colpass(c.L, in_bytes, &cfg))
             return fail(QAI_ERR_SHAPE, "line length %d does not fit shared memory", c.L);

@@ -197,10 +197,15 @@ qai_status launch_group(const Batch& bt, int rank, const GroupCfg& cfg, char* ws
                     a.in = yw; a.L = f.sh.nz; a.C = f.sh.ny * f.sh.nx; a.P = 1;
                     a.row_stride = (int64_t)f.sh.ny * f.sh.nx; a.plane_stride = 0;
                 }
+                uint16_t* cflag = reinterpret_cast<uint16_t*>(ws + f.ws_off + f.lay.cflag);
                 if (phase == 1) {
-                    if (fin) { a.dist1 = dist1; a.s_out = s; } else a.out_w = yw;
+                    if (fin) { a.dist1 = dist1; a.s_out = s; a.col_count_out = cflag; } else a.out_w = yw;
                 } else {
-                    if (fin) { a.out = f.out; a.q = f.q; a.dist1_in = dist1; a.s_in = s; } else a.out_w = yw;
+                    if (fin) {
+                        a.out = f.out; a.q = f.q; a.dist1_in = dist1; a.s_in = s; a.col_count_in = cflag;
+                    } else {
+                        a.out_w = yw;
+                    }
                 }
                 const int64_t gx = (int64_t)(f.sh.nx - 1) * (f.sh.nx - 1);
                 const int64_t gxy = gx + (int64_t)(f.sh.ny - 1) * (f.sh.ny - 1);

@@ -74,7 +74,7 @@ __device__ __forceinline__ void cp_async(void* dst, const void* src, int bytes)
 // element index of that row in the same column (phase 1 index carry).
 template <int PHASE, int IN, bool FINAL, bool DEBUG, bool GRAD, class Word>
 __device__ __forceinline__ void emit_point(const ColArgs& a, int idx, int src, int val, Word w, bool valid,
-                                           GradAcc& acc)
+                                           GradAcc& acc, int& any_sign)
 {
     if (PHASE == 1) {
         const int code = valid ? (int)(w & 3u) : 0;
@@ -83,6 +83,7 @@ __device__ __forceinline__ void emit_point(const ColArgs& a, int idx, int src, i
         } else {
             a.dist1[idx] = valid ? val : kDistInf;
             a.s_out[idx] = (int8_t)sign_of_code(code);
+            any_sign += sign_of_code(code) != 0;
         }
         if (DEBUG && a.dbg_idx_out) a.dbg_idx_out[idx] = valid ? a.dbg_idx_in[src] : -1;
     } else {
@@ -130,11 +131,44 @@ __device__ __forceinline__ void colpass_tile(const ColArgs& a, const int blk)
     const int RS = a.row_stride;
     const Word* in = static_cast<const Word*>(a.in);
 
-    __shared__ int s_fail;  // the fast path below could not settle a row
-    if (tid == 0) s_fail = 0;
+    __shared__ int s_fail;      // the fast path below could not settle a row
+    __shared__ int s_sign[32];  // phase 1 final: points with S != 0 per column (W <= 32)
+    __shared__ int s_total;     // phase 2 final: points with S != 0 in the tile
+    if (tid == 0) s_fail = s_total = 0;
+    if (PHASE == 1 && FINAL && tid < W) s_sign[tid] = 0;
+    int any_sign = 0;  // phase 1 final: this thread's points with S != 0
+
+    // Phase 2 final: where S = 0, C = S w eta eps = 0 and D'' = D' whatever
+    // Dist2 is; a tile whose columns all lack S != 0 only streams D'.
+    if (PHASE == 2 && FINAL && !DEBUG && a.col_count_in != nullptr) {
+        const int cc = c0 + col;
+        const int cnt = band == 0 && cc < a.C ? (int)a.col_count_in[(int64_t)p * a.C + cc] : 0;
+        if (__syncthreads_count(cnt > 0) == 0) {
+            if (GRAD) {
+                if (tid == 0) a.partials[2 * blk] = a.partials[2 * blk + 1] = 0.0;
+                return;
+            }
+            const int Lb = (a.L + B - 1) / B;
+            const int r0 = min(a.L, band * Lb), r1 = min(a.L, r0 + Lb);
+            if (cc < a.C) {
+                for (int r = r0; r < r1; ++r) {
+                    const int idx = pbase + r * RS + cc;
+                    a.out[idx] = a.m.output_c ? 0.0f : fmaf((float)__ldg(a.q + idx), a.m.two_eb, 0.0f);
+                }
+            }
+            return;
+        }
+        if (cnt) atomicAdd(&s_total, cnt);
+        __syncthreads();
+    }
+    // few points with S != 0 in the tile (at most one per two threads): the
+    // last pass scans for Dist2 at them alone, reading the input words from
+    // global memory, and stages the tile only if it falls back to the
+    // envelope; otherwise every row takes the fast path below
+    const bool sign_scan = PHASE == 2 && FINAL && !DEBUG && a.col_count_in != nullptr && 2 * s_total <= nthr;
 
     // ---- stage the tile ----------------------------------------------------
-    {
+    auto stage = [&]() {
         const int cols = min(W, a.C - c0);
         const int vb = a.load_bytes;
         if (vb) {
@@ -158,8 +192,9 @@ __device__ __forceinline__ void colpass_tile(const ColArgs& a, const int blk)
                 tile[e] = c < cols ? in[pbase + r * RS + c0 + c] : kWInf;
             }
         }
-    }
-    __syncthreads();
+        __syncthreads();
+    };
+    if (!sign_scan) stage();
 
     const int Lb = (L + B - 1) / B;
     const int r0 = min(L, band * Lb), r1 = min(L, r0 + Lb);
@@ -176,9 +211,70 @@ __device__ __forceinline__ void colpass_tile(const ColArgs& a, const int blk)
     // best is below (kScanMax + 1)^2, since no farther row can reach that. If
     // any row of the tile is not settled, the whole tile takes the envelope
     // path below, which rewrites every output of the tile (same rows per thread).
+    //
+    // The last pass of the second EDT needs Dist2 only where S != 0: elsewhere
+    // C = S w eta eps = 0 and D'' = D'. Those rows are written directly; the
+    // others (sparse where signs are) get their exact Dist2 from an outward
+    // scan without the kScanMax limit (Dist2 carries no index, so ties do not
+    // matter). A thread that would scan more than 4 rows per row of its band
+    // (about what the envelope path costs it) sends the tile to the envelope
+    // path instead.
     {
         volatile int* vfail = &s_fail;  // any thread of the tile failed: all stop
-        if (c < a.C) {
+        if (sign_scan) {
+          if constexpr (PHASE == 2 && FINAL && !DEBUG) {
+            if (c < a.C) {
+                int steps = 0;
+                // rows in groups of four: their sign and index loads are issued
+                // together, ahead of the branches that use them
+                for (int rb = r0; rb < r1 && !*vfail; rb += 4) {
+                    int sv[4], qv[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int idx = pbase + (rb + u) * RS + c;
+                        sv[u] = rb + u < r1 ? (int)__ldg(a.s_in + idx) : 0;
+                        qv[u] = rb + u < r1 && !GRAD ? __ldg(a.q + idx) : 0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int r = rb + u;
+                        if (r >= r1) break;
+                        const int idx = pbase + r * RS + c;
+                        if (sv[u] == 0) {
+                            if (!GRAD) a.out[idx] = a.m.output_c ? 0.0f : fmaf((float)qv[u], a.m.two_eb, 0.0f);
+                            continue;
+                        }
+                        const Word* gcol = in + pbase + c;  // row r' at gcol[r' * RS]
+                        const Word w0 = __ldg(gcol + (int64_t)r * RS);
+                        int best = w0 != kWInf ? gval<PHASE, IN>(w0) : 0x7FFFFFFF;
+                        bool over = false;
+                        for (int k = 1; k * k <= best && (r - k >= 0 || r + k < L); ++k) {
+                            if (++steps > 4 * Lb) {
+                                over = true;
+                                break;
+                            }
+                            if (r - k >= 0) {
+                                const Word w = __ldg(gcol + (int64_t)(r - k) * RS);
+                                const int v = gval<PHASE, IN>(w) + k * k;
+                                if (w != kWInf && v < best) best = v;
+                            }
+                            if (r + k < L) {
+                                const Word w = __ldg(gcol + (int64_t)(r + k) * RS);
+                                const int v = gval<PHASE, IN>(w) + k * k;
+                                if (w != kWInf && v < best) best = v;
+                            }
+                        }
+                        if (over) {
+                            *vfail = 1;
+                            break;
+                        }
+                        emit_point<PHASE, IN, FINAL, DEBUG, GRAD>(a, idx, 0, best, (Word)0, best != 0x7FFFFFFF,
+                                                                  acc, any_sign);
+                    }
+                }
+            }
+          }
+        } else if (c < a.C) {
             for (int r = r0; r < r1 && !*vfail; ++r) {
                 Word bw = tcol[r * W];
                 int bh = bw != kWInf ? r : -1;
@@ -199,7 +295,7 @@ __device__ __forceinline__ void colpass_tile(const ColArgs& a, const int blk)
                     *vfail = 1;
                     break;
                 }
-                emit_point<PHASE, IN, FINAL, DEBUG, GRAD>(a, pbase + r * RS + c, pbase + bh * RS + c, best, bw, true, acc);
+                emit_point<PHASE, IN, FINAL, DEBUG, GRAD>(a, pbase + r * RS + c, pbase + bh * RS + c, best, bw, true, acc, any_sign);
             }
         }
         __syncthreads();
@@ -335,7 +431,7 @@ __device__ __forceinline__ void colpass_tile(const ColArgs& a, const int blk)
     const int nl = nlst[col];
     if (nl == 0) {  // empty column: no site reaches it
         for (int r = r0; r < r1; ++r)
-            emit_point<PHASE, IN, FINAL, DEBUG, GRAD>(a, pbase + r * RS + c, 0, 0, (Word)0, false, acc);
+            emit_point<PHASE, IN, FINAL, DEBUG, GRAD>(a, pbase + r * RS + c, 0, 0, (Word)0, false, acc, any_sign);
         return;
     }
     // envelope entry of row r0: the first entry that the next one does not
@@ -443,12 +539,22 @@ __device__ __forceinline__ void colpass_tile(const ColArgs& a, const int blk)
             pd1 = nd1;
             ps = nsg;
         } else {
-            emit_point<PHASE, IN, FINAL, DEBUG, GRAD>(a, idx, pbase + h * RS + c, val, w, true, acc);
+            emit_point<PHASE, IN, FINAL, DEBUG, GRAD>(a, idx, pbase + h * RS + c, val, w, true, acc, any_sign);
         }
         idx += RS;
     }
     };  // envelope_path
-    if (use_envelope) envelope_path();
+    if (use_envelope) {
+        if (sign_scan) stage();
+        envelope_path();
+    }
+
+    if constexpr (PHASE == 1 && FINAL) {  // the columns' counts of S != 0
+        if (any_sign) atomicAdd(&s_sign[col], any_sign);
+        __syncthreads();
+        if (band == 0 && c < a.C && a.col_count_out)
+            a.col_count_out[(int64_t)p * a.C + c] = (uint16_t)min(s_sign[col], 65535);
+    }
 
     if constexpr (GRAD) {  // the CTA's two sums: a fixed float-float tree over the threads
         __shared__ float red[4][512];

@@ -85,6 +85,12 @@ struct ColArgs {
     int32_t* dbg_dist2;      // phase 2 final
     const float* grad_out;   // phase 2 final, adjoint mode: dL/dD'' (no D'' written)
     double* partials;        // adjoint mode: two FP64 sums per CTA
+    // Per column (index p * C + c), the number of points with S != 0
+    // (saturated at 65535): written by the last pass of the first EDT, read by
+    // the last pass of the second, which streams D'' = D' through tiles
+    // without such points and scans for Dist2 only at them where they are few.
+    uint16_t* col_count_out;
+    const uint16_t* col_count_in;
     MethodArgs m;
 };
 

@@ -20,7 +20,7 @@ struct Shape {
 
 // Byte offsets of the workspace slices of one field.
 struct Layout {
-    size_t eqm, xw, yw, dist1, s, idx, total;
+    size_t eqm, xw, yw, dist1, s, idx, cflag, total;
 };
 
 qai_status fail(qai_status s, const char* fmt, ...) __attribute__((format(printf, 2, 3)));

@@ -12,10 +12,12 @@
 namespace {
 
 // Workspace of the largest accepted field: at most 12 bytes per point (the
-// rank-3 layout: equal-q mask 1, Dist1 4, S 1, xwords 2, ywords 4) plus the
-// 256-byte alignment of its five slices.
+// rank-3 layout: equal-q mask 1, Dist1 4, S 1, xwords 2, ywords 4), a uint16
+// count per column of the last column pass (at most one byte per point, since
+// that pass has at least two rows) and the 256-byte alignment of its six
+// slices.
 constexpr int64_t kMaxPoints = QAI_STATIC_MAX_POINTS;
-constexpr size_t kScratchBytes = (size_t)12 * (size_t)kMaxPoints + 5 * 256;
+constexpr size_t kScratchBytes = (size_t)13 * (size_t)kMaxPoints + 6 * 256;
 
 __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 

@@ -172,3 +172,23 @@ def test_profile_and_launch_count():
     assert set(stats) == {"rowpass1", "colpass1_y", "colpass1_z_final", "rowpass2",
                           "colpass2_y", "colpass2_z_final"}
     assert all(v[0] == 1 and v[1] > 0 for v in stats.values())
+
+
+@pytest.mark.parametrize("name,shape,rel_eb", [("grf", (96, 128, 160), 1e-3), ("front", (64, 200, 72), 1e-3),
+                                               ("front", (300, 500), 1e-3), ("sinusoids", (40, 64, 64), 3e-3)],
+                         ids=str)
+def test_flat_tiles_equal_full_evaluation(name, shape, rel_eb):
+    """Tiles whose columns hold no S != 0 stream D'' = D' in the last pass; the
+    debug path evaluates every point. Both must give the same bits, and the
+    field must have columns of both kinds."""
+    x = _field(name, shape, 11)
+    eb = rel_eb * synth.value_range(x)
+    q = synth.quantize(x, eb)
+    fast = qai.mitigate(q, eb)
+    fast_c = qai.mitigate(q, eb, output_c=True)
+    full, maps = qai.mitigate(q, eb, debug=True)
+    full_c, _ = qai.mitigate(q, eb, debug=True, output_c=True)
+    torch.cuda.synchronize()
+    assert torch.equal(fast, full) and torch.equal(fast_c, full_c)
+    col_has = (maps["s"] != 0).any(dim=0)             # columns of the last pass
+    assert bool(col_has.any()) and not bool(col_has.all())
