@@ -333,14 +333,31 @@ __device__ __forceinline__ void rowpass_row(const RowArgs& a, const int row, uns
         }
     }
     __syncwarp();
+    int row_first = kNoRef;  // first site of the row
     if (lane == 0) {
         int nxt = kNoRef;
         for (int seg = nseg - 1; seg >= 0; --seg) {
             sm.nextr[seg] = nxt;
             if (sm.sfirst[seg] != kNoRef) nxt = sm.sfirst[seg];
         }
+        row_first = nxt;
     }
     __syncwarp();
+    // a row without sites (common for the sparse sign flips of the second
+    // EDT) is INF everywhere: no sweep B
+    if (!FINAL && !DEBUG && __shfl_sync(kFull, row_first, 0) == kNoRef) {
+        for (int seg = 0; seg < nseg; ++seg) {
+            const int x0 = seg * kSeg + 4 * lane;
+            if (VEC) {
+                if (x0 < nx) *reinterpret_cast<uint2*>(a.xw + rbase + x0) = make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (x0 + j < nx) a.xw[rbase + x0 + j] = (uint16_t)kInf16;
+            }
+        }
+        return;
+    }
 
     // ---- sweep B: nearest site on both sides; emit -------------------------
     const unsigned lt = (1u << lane) - 1u;
