@@ -461,7 +461,7 @@ def run_adjoint1024(args):
 
         def fwd():
             if mode == "stored":
-                qai.mitigate_save(q, eb, saved=saved, workspace=ws)
+                qai.mitigate_save(q, eb, saved=saved, workspace=ws, out=out)
             else:
                 qai.mitigate(q, eb, out=out, workspace=ws)
 

@@ -242,12 +242,13 @@ def workspace_size_backward(shape, recompute: bool) -> int:
 def mitigate_save(q: torch.Tensor, eb: float, eta: float = 0.9, idw_power: float = 1.0,
                   grad_threshold: int = 2, sign_rule: int = SIGN_SUM, b2_rule: int = B2_SAME_Q,
                   output_c: bool = False, saved: torch.Tensor | None = None,
-                  workspace: torch.Tensor | None = None, stream=None):
+                  workspace: torch.Tensor | None = None, stream=None, out: torch.Tensor | None = None):
     """Forward that also keeps Dist1, Dist2 and S for the stored-mode adjoint.
     Returns ``(out, saved)``."""
     lib = load()
     shape = tuple(q.shape)
-    out = torch.empty(shape, dtype=torch.float32, device=q.device)
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float32, device=q.device)
     if saved is None:
         saved = alloc_workspace(saved_size(shape), q.device)
     if workspace is None:

@@ -43,3 +43,26 @@ def test_eta_gradient_is_linear_in_grad_out():
     b = np.array(oracle.grad_params(q, eb, g2))
     c = np.array(oracle.grad_params(q, eb, 2.0 * g1 - 3.0 * g2))
     np.testing.assert_allclose(c, 2.0 * a - 3.0 * b, rtol=1e-10, atol=1e-12)
+
+
+def test_fields_without_signs_have_zero_parameter_gradients():
+    # constant field: no boundary at all; a steep ramp (3 indices per cell):
+    # every interior point is a boundary whose sign the fast-varying rule
+    # zeroes (|q[+1] - q[-1]| = 6); S = 0 everywhere
+    g = np.random.default_rng(2).normal(size=(9, 10, 11))
+    for q in (np.full((9, 10, 11), 7, np.int32), (3 * np.indices((9, 10, 11))[2]).astype(np.int32)):
+        ge, gp = oracle.grad_params(q, 0.1, g)
+        assert ge == 0.0 and gp == 0.0
+
+
+def test_eta_gradient_of_the_hand_worked_ramp():
+    # D'' - D' = S w eta eps, so with G = 1 everywhere dL/deta = sum (D'' - D') / eta,
+    # taken from the hand-derived V1 values (tests/golden/V1_ramp.json)
+    import json
+    import os
+    fx = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "V1_ramp.json")))
+    q = np.array(fx["q"], np.int32)
+    dprime = 2 * fx["eb"] * q
+    want = float(np.sum(np.array(fx["expect"]["out"]) - dprime)) / fx["eta"]
+    ge, gp = oracle.grad_params(q, fx["eb"], np.ones(q.shape), eta=fx["eta"])
+    assert ge == pytest.approx(want, rel=1e-12, abs=1e-12)
