@@ -248,7 +248,7 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
                        double bytes_per_pt) -> qai_status {
         const int64_t max_g = in_bytes == 2 ? gx : gxy;
         qai::ColConfig cfg;
-        if (!qai::choose_colpass(c.L, in_bytes, &cfg))
+        if (!qai::choose_colpass(c.L, in_bytes, &cfg, phase == 1 && fin))
             return fail(QAI_ERR_SHAPE, "line length %d does not fit shared memory", c.L);
         cudaError_t err = timed(name, N * bytes_per_pt, st,
                                 [&] { return qai::launch_colpass(phase, in_bytes, fin, c, cfg, debug, max_g, st); });

@@ -25,7 +25,8 @@ struct ColConfig {
     int B;        // bands per column
     size_t smem;  // dynamic shared memory bytes
 };
-bool choose_colpass(int L, int in_bytes, ColConfig* cfg);
+// first_edt_last_pass: the tile of the last pass of the first EDT.
+bool choose_colpass(int L, int in_bytes, ColConfig* cfg, bool first_edt_last_pass = false);
 bool choose_colpass_with(int L, int in_bytes, int rows_per_band, int max_w, ColConfig* cfg);
 // Sets a.bands, a.load_bytes and a.narrow for a launch with `cfg`.
 void prepare_colpass(ColArgs& a, int in_bytes, const ColConfig& cfg, int64_t max_g);
