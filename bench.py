@@ -292,6 +292,8 @@ def run_qai(args):
     ms_max = float(t.item())
     value = N * 4 * world / (ms_max * 1e-3) / 1e9
 
+    route = qai.route_counts(ws, tuple(q.shape))  # how the second EDT went (signed-point route)
+
     # end to end from pinned host memory through the C ABI (copies timed)
     if args.no_e2e:
         e2e_value = None
@@ -309,6 +311,7 @@ def run_qai(args):
     out2 = torch.empty_like(q2, dtype=torch.float32)
     ms2 = _time_steps(lambda: qai.mitigate(q2, eb2, out=out2, workspace=ws2), args.steps)
     second = {"rel_eb": 1e-2, "ms_per_step": ms2, "value": N * 4 / (ms2 * 1e-3) / 1e9,
+              "signed_route": qai.route_counts(ws2, tuple(q2.shape)),
               **quality_gain(x, q2, eb2, out2)}
     del q2, ws2, out2
     if rank != 0:
@@ -355,6 +358,7 @@ def run_qai(args):
         "clocks": clk.summary(tc0, tc1),
         "cpu_baseline": cpu,
         "quality": qual,
+        "signed_route": route,
         "second_bound": second,
         "kernels": kernels,
     }
@@ -418,12 +422,14 @@ def run_batch96(args):
     def seq():
         for q, eb, o, w in zip(qs, ebs, outs, wss):
             qai.mitigate(q, eb, out=o, workspace=w)
+    n1 = qai.launch_count()
     ms_s = _time_steps(seq, args.steps)
+    seq_launches = (qai.launch_count() - n1) // (args.steps + 3)
     same = all(torch.equal(a, b) for a, b in zip(batch.outs, outs))
     print(json.dumps({"workload": "batch96_mixed", "fields": len(qs), "points": npts,
                       "value": npts * 4 / (ms_b * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ms_b,
                       "sequential": {"value": npts * 4 / (ms_s * 1e-3) / 1e9, "ms_per_step": ms_s,
-                                     "launches": 6 * len(qs)},
+                                     "launches": seq_launches},
                       "batched_kernels_per_graph": launches, "identical_to_sequential": same,
                       "autotuned": {str(k): {"rows_per_band": v[0], "max_w": v[1],
                                              "order": "largest first" if v[2] else "as given"}

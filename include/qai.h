@@ -110,6 +110,23 @@ qai_status qai_mitigate(const int32_t* d_q, float* d_out, int rank, const int64_
                         double eb, const qai_params* params, void* d_ws, size_t ws_bytes,
                         cudaStream_t stream, const qai_debug_out* dbg);
 
+/* How the last plain qai_mitigate call on this workspace computed the second
+ * EDT (step D) of a rank-2 or rank-3 field. Step E needs Dist2 only at the
+ * points with S != 0 off B1 (elsewhere C = 0, or the weight is 1: Sec. VI-E),
+ * so a plain call finds their nearest B2 site by an exact shell search, lists
+ * the B2 sites and searches them all for the points the shell search leaves,
+ * and runs the dense second EDT over the whole field only when one of those
+ * lists overflows. Outputs are the same bits on every route.
+ *  d_ws     the workspace of that call (device), after the call completed
+ *  counts   host int32[5]: points with S != 0 off B1; of them, those left to
+ *           the list search; B2 sites listed (0 if the list was not needed);
+ *           1 if the dense second EDT ran, else 0; B1 points with S != 0
+ *           (-1 if there were too many to list)
+ * Synchronises `stream`. Returns QAI_ERR_SHAPE for rank-1 fields (no such
+ * route) or an unsupported shape, QAI_ERR_INVALID_ARG for NULL pointers. */
+qai_status qai_route_counts(const void* d_ws, int rank, const int64_t* dims, int32_t* counts,
+                            cudaStream_t stream);
+
 /* Bytes of device workspace qai_mitigate_host needs: the device copies of q
  * and D'' plus qai_workspace_size(rank, dims, 0). */
 qai_status qai_workspace_size_host(int rank, const int64_t* dims, size_t* bytes);
@@ -259,8 +276,8 @@ qai_status qai_quality(const float* d_x, const float* d_y, int rank, const int64
  * no counterpart; it is a deployment convenience of this library.
  *
  * Instead of a workspace it uses one scratch array compiled into the library
- * (a 256-byte aligned __device__ array of 13 * QAI_STATIC_MAX_POINTS + 1536
- * bytes, about 26 MiB). Every GPU that loads the library holds that array
+ * (a 256-byte aligned __device__ array of 13.125 * QAI_STATIC_MAX_POINTS +
+ * 1 MiB bytes, about 27.3 MiB). Every GPU that loads the library holds that array
  * until the process exits. The call itself allocates nothing: no cudaMalloc,
  * no cudaFree, no library routine that allocates.
  *  d_q, d_out, rank, dims, eb, params, stream: as for qai_mitigate (the
@@ -269,9 +286,9 @@ qai_status qai_quality(const float* d_x, const float* d_y, int rank, const int64
  * any CUDA call. The first call on each device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current; make that first
  * call before any stream capture. Every call shares the array, which keeps
- * the last call's contents; no part of it needs to start at zero, because
- * each kernel writes its slice of the array in full before any kernel reads
- * it. Calls whose work overlaps on the GPU (two streams, or two host threads)
+ * the last call's contents; the call's first kernel clears the few counters
+ * that must start at zero, and every other slice is written before it is
+ * read. Calls whose work overlaps on the GPU (two streams, or two host threads)
  * race on the array and corrupt each other's results: serialise them, for
  * example on one stream. No per-step (debug) outputs. */
 qai_status qai_mitigate_static(const int32_t* d_q, float* d_out, int rank, const int64_t* dims,

@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -150,6 +151,18 @@ Layout layout_for(const Shape& s, uint32_t flags)
     l.idx = (flags & QAI_WS_INDEX) && s.rank >= 2 ? take(N * 4) : 0;
     // a uint16 count per column of the last column pass (z: ny * nx, y: nx)
     l.cflag = s.rank == 3 ? take((size_t)s.ny * s.nx * 2) : s.rank == 2 ? take((size_t)s.nx * 2) : 0;
+    if (s.rank >= 2) {
+        l.qcap = (int)(N / 128 + 1024);
+        l.scap = (int)(N / 256 + 1024);
+        l.fcap = std::min(l.qcap, 1 << 16);
+        l.b2cap = (int)(N / 256 + 1024);
+        l.ctr = take(qai::kCtrWords * 4);
+        l.qlist = take((size_t)l.qcap * sizeof(qai::Query));
+        l.slist = take((size_t)l.scap * 4);
+        l.flist = take((size_t)l.fcap * sizeof(qai::Query));
+        l.fmin = take((size_t)l.fcap * 4);
+        l.b2list = take((size_t)l.b2cap * 8);
+    }
     l.total = off;
     return l;
 }
@@ -199,6 +212,22 @@ struct GradSink {
     int nblocks;       // set by run_pipeline
 };
 
+// Route of the second EDT for plain calls: QAI_SIGNED_ROUTE = "off" (the
+// dense second EDT alone, no signed-point route), "dense" (the route's
+// kernels run but hand every field to the dense second EDT), "brute" (no
+// shell search: every query goes to the brute-force search); anything else
+// is the default. Read on every call; all routes give the same bits.
+enum class Route { Auto, Off, Dense, Brute };
+Route signed_route()
+{
+    const char* v = getenv("QAI_SIGNED_ROUTE");
+    if (!v) return Route::Auto;
+    if (!strcmp(v, "off")) return Route::Off;
+    if (!strcmp(v, "dense")) return Route::Dense;
+    if (!strcmp(v, "brute")) return Route::Brute;
+    return Route::Auto;
+}
+
 // CTAs of the last EDT2 pass (the sums it leaves in the partials array).
 int final_pass_blocks(const Shape& sh)
 {
@@ -230,12 +259,18 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
     const int64_t gx = (int64_t)(sh.nx - 1) * (sh.nx - 1);           // max g after the x pass
     const int64_t gxy = gx + (int64_t)(sh.ny - 1) * (sh.ny - 1);     // after the y pass
     cudaError_t e;
+    // The signed-point route: plain calls on rank 2 and 3 fields (the debug
+    // maps and the adjoint need the dense second EDT everywhere).
+    const Route route = signed_route();
+    const bool signed_route_on = !debug && !grad && sh.rank >= 2 && route != Route::Off;
+    int* ctr = signed_route_on ? reinterpret_cast<int*>(ws + lay.ctr) : nullptr;
 
     // Step A + EDT-x of B1 (rank 1: the whole first EDT).
     qai::RowArgs r1{};
     r1.rank = sh.rank; r1.nz = sh.nz; r1.ny = sh.ny; r1.nx = sh.nx;
     r1.q = d_q; r1.eqm = eqm; r1.m = m;
     r1.dbg_b1 = d.b1; r1.dbg_sb = d.sb;
+    if (ctr) { r1.out_pre = d_out; r1.route_ctr = ctr; }
     const bool final1 = sh.rank == 1;
     if (final1) { r1.dist1 = dist1; r1.s_out = s; r1.dbg_idx = d.idx1; }
     else { r1.xw = xw; r1.dbg_idx = d.idx1 ? (sh.rank == 3 ? d.idx1 : idx_tmp) : nullptr; }
@@ -269,9 +304,16 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
     };
     qai_status st_;
     uint16_t* cflag = sh.rank >= 2 ? reinterpret_cast<uint16_t*>(ws + lay.cflag) : nullptr;
+    qai::Query* qlist = ctr ? reinterpret_cast<qai::Query*>(ws + lay.qlist) : nullptr;
+    auto route_args = [&](qai::ColArgs& c) {
+        if (!ctr) return;
+        c.route_ctr = ctr; c.qlist = qlist; c.qcap = lay.qcap;
+        c.slist = reinterpret_cast<int32_t*>(ws + lay.slist); c.scap = lay.scap;
+    };
     if (sh.rank == 2) {
         qai::ColArgs c = y_args(xw);
         c.dist1 = dist1; c.s_out = s; c.col_count_out = cflag;
+        route_args(c);
         if (d.idx1) { c.dbg_idx_in = idx_tmp; c.dbg_idx_out = d.idx1; }
         if ((st_ = colpass(1, 2, true, c, "colpass1_y_final", 2 + 4 + 1)) != QAI_OK) return st_;
     } else if (sh.rank == 3) {
@@ -281,6 +323,7 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
         if ((st_ = colpass(1, 2, false, c, "colpass1_y", 2 + 4)) != QAI_OK) return st_;
         qai::ColArgs cz = z_args(yw);
         cz.dist1 = dist1; cz.s_out = s; cz.col_count_out = cflag;
+        route_args(cz);
         if (d.idx1) { cz.dbg_idx_in = idx_tmp; cz.dbg_idx_out = d.idx1; }
         if ((st_ = colpass(1, 4, true, cz, "colpass1_z_final", 4 + 4 + 1)) != QAI_OK) return st_;
     }
@@ -289,6 +332,33 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
     if (d.s && (e = cudaMemcpyAsync(d.s, s, (size_t)sh.N, cudaMemcpyDeviceToDevice, st)))
         return cuda_fail(e, "copy s");
 
+    // Signed-point route: exact Dist2 and step E at the queries; the dense
+    // second EDT below runs only if this route hands the field over.
+    if (ctr) {
+        qai::RouteArgs ra{};
+        ra.rank = sh.rank; ra.nz = sh.nz; ra.ny = sh.ny; ra.nx = sh.nx;
+        ra.q = d_q; ra.eqm = eqm; ra.s = s; ra.out = d_out; ra.ctr = ctr;
+        ra.qlist = qlist; ra.qcap = lay.qcap;
+        ra.slist = reinterpret_cast<const int32_t*>(ws + lay.slist); ra.scap = lay.scap;
+        ra.flist = reinterpret_cast<qai::Query*>(ws + lay.flist); ra.fcap = lay.fcap;
+        ra.fmin = reinterpret_cast<int32_t*>(ws + lay.fmin);
+        ra.b2list = reinterpret_cast<int32_t*>(ws + lay.b2list); ra.b2cap = lay.b2cap;
+        ra.max_r2 = route == Route::Brute ? -1 : qai::route_table_r2();
+        ra.brute_budget = 1LL << 28;
+        ra.m = m;
+        if (route == Route::Dense) ra.qcap = -1;  // every count is over it: hand over at once
+        int dev = 0, sms = 152;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        e = timed("signed_query", 0.0, st, [&] { return qai::launch_route_query(ra, 4 * sms, st); });
+        if (e != cudaSuccess) return cuda_fail(e, "signed-point shell search");
+        e = timed("signed_b2dilate", 0.0, st, [&] { return qai::launch_route_b2dilate(ra, 4 * sms, st); });
+        if (e != cudaSuccess) return cuda_fail(e, "B2 sites from the signed points");
+        e = timed("signed_b2list", N * 2.0, st, [&] { return qai::launch_route_b2list(ra, 8 * sms, st); });
+        if (e != cudaSuccess) return cuda_fail(e, "B2 site list");
+        e = timed("signed_brute", 0.0, st, [&] { return qai::launch_route_brute(ra, 2 * sms, st); });
+        if (e != cudaSuccess) return cuda_fail(e, "brute-force search");
+    }
+
     // B2 = GetBoundary(S) + EDT-x of B2 (rank 1: also step E).
     qai::RowArgs r2{};
     r2.rank = sh.rank; r2.nz = sh.nz; r2.ny = sh.ny; r2.nx = sh.nx;
@@ -296,6 +366,7 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
     r2.dbg_b2 = d.b2;
     if (final1) { r2.dist1_in = dist1; r2.out = d_out; r2.dbg_dist2 = d.dist2; }
     else r2.xw = xw;
+    r2.route_ctr = ctr;
     e = timed(final1 ? "rowpass2_final" : "rowpass2", N * (final1 ? 14.0 : 4.0), st,
               [&] { return qai::launch_rowpass(2, final1, r2, debug, st); });
     if (e != cudaSuccess) return cuda_fail(e, "row pass 2");
@@ -303,7 +374,7 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
     // EDT2 along y (and z), the last pass fused with step E.
     auto fuse_e = [&](qai::ColArgs& c) {
         c.out = d_out; c.q = d_q; c.dist1_in = dist1; c.s_in = s; c.dbg_dist2 = d.dist2;
-        c.col_count_in = cflag;
+        c.col_count_in = cflag; c.route_ctr = ctr;
     };
     // Adjoint mode: the last pass reads G, Dist1, S and the input words.
     auto last_grad = [&](qai::ColArgs& c, int in_bytes, const char* name) -> qai_status {
@@ -326,6 +397,7 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
     } else if (sh.rank == 3) {
         qai::ColArgs c = y_args(xw);
         c.out_w = yw;
+        c.route_ctr = ctr;
         if ((st_ = colpass(2, 2, false, c, "colpass2_y", 2 + 4)) != QAI_OK) return st_;
         qai::ColArgs cz = z_args(yw);
         if (grad) return last_grad(cz, 4, "colpass2_z_grad");
@@ -392,6 +464,29 @@ qai_status qai_mitigate(const int32_t* d_q, float* d_out, int rank, const int64_
     s = run_pipeline(d_q, d_out, sh, method_args(p, eb), static_cast<char*>(d_ws), lay, stream, dbg);
     if (owned) cudaFreeAsync(d_ws, stream);
     return s;
+}
+
+qai_status qai_route_counts(const void* d_ws, int rank, const int64_t* dims, int32_t* counts,
+                            cudaStream_t stream)
+{
+    g_last_error.clear();
+    if (!d_ws || !counts) return fail(QAI_ERR_INVALID_ARG, "d_ws and counts must be non-NULL");
+    Shape sh;
+    qai_status s = make_shape(rank, dims, &sh);
+    if (s != QAI_OK) return s;
+    if (sh.rank < 2) return fail(QAI_ERR_SHAPE, "rank-1 fields have no signed-point route");
+    const Layout lay = layout_for(sh, 0);
+    int32_t c[qai::kCtrWords];
+    cudaError_t e = cudaMemcpyAsync(c, static_cast<const char*>(d_ws) + lay.ctr, sizeof c,
+                                    cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e, "read route counters");
+    counts[0] = c[qai::kCtrQueries];
+    counts[1] = c[qai::kCtrFailed];
+    counts[2] = c[qai::kCtrB2];
+    counts[3] = c[qai::kCtrDense] != 0;
+    counts[4] = c[qai::kCtrSignedOver] ? -1 : c[qai::kCtrSigned];
+    return QAI_OK;
 }
 
 qai_status qai_workspace_size_host(int rank, const int64_t* dims, size_t* bytes)

@@ -23,6 +23,7 @@
 // Phase 1 carries the sign code of the nearest boundary; its last pass writes
 // Dist1 and S = S_B[I1] (Algorithm 3's propagation). Phase 2's last pass fuses
 // step E: Dist2 goes straight into the compensation and never to memory.
+#include <algorithm>
 #include <cstdlib>
 #include <type_traits>
 
@@ -33,6 +34,18 @@ namespace qai {
 namespace {
 
 constexpr int kMaxBands = 32;
+
+// CTAs of `kern` that fit on the device at once (at least one per SM).
+template <class K>
+unsigned resident_grid(K kern, dim3 block, size_t smem)
+{
+    int dev = 0, sms = 152, per = 1;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, (int)(block.x * block.y * block.z), smem) !=
+            cudaSuccess || per < 1)
+        per = 1;
+    return (unsigned)(sms * per);
+}
 constexpr int kScanMax = 5;    // outward-scan fast path: rows settled within 5 rows
 
 template <int PHASE, int IN>
@@ -72,16 +85,49 @@ __device__ __forceinline__ void cp_async(void* dst, const void* src, int bytes)
 // Writes the result of one point: `val` is its squared distance, `w` the
 // input word of the winning row (phase 1: carries the sign code), `src` the
 // element index of that row in the same column (phase 1 index carry).
+// Points of the signed-point route collected by one CTA of the last pass of
+// the first EDT before they go to the global lists: the queries (S != 0 off
+// B1) and the B1 points with S != 0.
+constexpr int kQueryBuf = 768;
+constexpr int kSignedBuf = 512;
+struct QueryBuf {
+    Query* e;   // [kQueryBuf] in shared memory
+    int* n;     // shared count (may pass kQueryBuf: the route then gives up)
+    int32_t* se;// [kSignedBuf]
+    int* sn;    // shared count (may pass kSignedBuf: that list is then incomplete)
+};
+
 template <int PHASE, int IN, bool FINAL, bool DEBUG, bool GRAD, class Word>
 __device__ __forceinline__ void emit_point(const ColArgs& a, int idx, int src, int val, Word w, bool valid,
-                                           GradAcc& acc, int& any_sign)
+                                           GradAcc& acc, int& any_sign, const QueryBuf& qb)
 {
     if (PHASE == 1) {
         const int code = valid ? (int)(w & 3u) : 0;
         if (!FINAL) {
             static_cast<uint32_t*>(a.out_w)[idx] = valid ? ((uint32_t)val << 2) | (uint32_t)code : kInf32;
         } else {
-            a.dist1[idx] = valid ? val : kDistInf;
+            if (!a.qlist) {
+                a.dist1[idx] = valid ? val : kDistInf;
+            } else if (code != 0) {
+                // signed-point route: Dist1 matters only where S != 0, and a
+                // point off B1 there is a query of the second EDT
+                a.dist1[idx] = val;
+                if (val > 0) {
+                    const int k = atomicAdd(qb.n, 1);
+                    if (k < kQueryBuf) {
+                        qb.e[k] = Query{idx, (val << 2) | code};
+                    } else {
+                        // a full buffer spills to the global list; should the
+                        // tile fall back to the envelope path, these entries
+                        // are listed twice (the same query, the same output)
+                        const int g = atomicAdd(a.route_ctr + kCtrQueries, 1);
+                        if (g < a.qcap) a.qlist[g] = Query{idx, (val << 2) | code};
+                    }
+                } else {
+                    const int k = atomicAdd(qb.sn, 1);
+                    if (k < kSignedBuf) qb.se[k] = idx;
+                }
+            }
             a.s_out[idx] = (int8_t)sign_of_code(code);
             any_sign += sign_of_code(code) != 0;
         }
@@ -96,7 +142,10 @@ __device__ __forceinline__ void emit_point(const ColArgs& a, int idx, int src, i
                        a.m.idw_power, te, tp);
             acc.add(te, tp);
         } else {
-            a.out[idx] = compensate(__ldg(a.q + idx), __ldg(a.dist1_in + idx), d, __ldg(a.s_in + idx), a.m);
+            const int sv = __ldg(a.s_in + idx);
+            // signed-point route: row pass 1 wrote every point with S = 0
+            if (!a.route_ctr || sv != 0)
+                a.out[idx] = compensate(__ldg(a.q + idx), __ldg(a.dist1_in + idx), d, sv, a.m);
             if (DEBUG && a.dbg_dist2) a.dbg_dist2[idx] = d;
         }
     }
@@ -108,6 +157,8 @@ __device__ __forceinline__ void emit_point(const ColArgs& a, int idx, int src, i
 template <int PHASE, int IN, bool FINAL, bool DEBUG, bool NARROW, bool GRAD = false>
 __device__ __forceinline__ void colpass_tile(const ColArgs& a, const int blk)
 {
+    if (PHASE == 2 && a.route_ctr && *static_cast<volatile int*>(a.route_ctr + kCtrDense) == 0)
+        return;  // the signed-point route handled the second EDT
     GradAcc acc;
     using Word = std::conditional_t<IN == 2, uint16_t, uint32_t>;
     constexpr Word kWInf = IN == 2 ? (Word)kInf16 : (Word)kInf32;
@@ -134,7 +185,12 @@ __device__ __forceinline__ void colpass_tile(const ColArgs& a, const int blk)
     __shared__ int s_fail;      // the fast path below could not settle a row
     __shared__ int s_sign[32];  // phase 1 final: points with S != 0 per column (W <= 32)
     __shared__ int s_total;     // phase 2 final: points with S != 0 in the tile
-    if (tid == 0) s_fail = s_total = 0;
+    constexpr bool kQueries = PHASE == 1 && FINAL;
+    __shared__ Query s_qbuf[kQueries ? kQueryBuf : 1];
+    __shared__ int32_t s_sbuf[kQueries ? kSignedBuf : 1];
+    __shared__ int s_qn, s_qbase, s_sn, s_sbase;
+    const QueryBuf qb{s_qbuf, &s_qn, s_sbuf, &s_sn};
+    if (tid == 0) s_fail = s_total = s_qn = s_sn = 0;
     if (PHASE == 1 && FINAL && tid < W) s_sign[tid] = 0;
     int any_sign = 0;  // phase 1 final: this thread's points with S != 0
 
@@ -148,6 +204,7 @@ __device__ __forceinline__ void colpass_tile(const ColArgs& a, const int blk)
                 if (tid == 0) a.partials[2 * blk] = a.partials[2 * blk + 1] = 0.0;
                 return;
             }
+            if (a.route_ctr) return;  // row pass 1 wrote D' here
             const int Lb = (a.L + B - 1) / B;
             const int r0 = min(a.L, band * Lb), r1 = min(a.L, r0 + Lb);
             if (cc < a.C) {
@@ -233,7 +290,7 @@ __device__ __forceinline__ void colpass_tile(const ColArgs& a, const int blk)
                     for (int u = 0; u < 4; ++u) {
                         const int idx = pbase + (rb + u) * RS + c;
                         sv[u] = rb + u < r1 ? (int)__ldg(a.s_in + idx) : 0;
-                        qv[u] = rb + u < r1 && !GRAD ? __ldg(a.q + idx) : 0;
+                        qv[u] = rb + u < r1 && !GRAD && !a.route_ctr ? __ldg(a.q + idx) : 0;
                     }
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
@@ -241,7 +298,8 @@ __device__ __forceinline__ void colpass_tile(const ColArgs& a, const int blk)
                         if (r >= r1) break;
                         const int idx = pbase + r * RS + c;
                         if (sv[u] == 0) {
-                            if (!GRAD) a.out[idx] = a.m.output_c ? 0.0f : fmaf((float)qv[u], a.m.two_eb, 0.0f);
+                            if (!GRAD && !a.route_ctr)
+                                a.out[idx] = a.m.output_c ? 0.0f : fmaf((float)qv[u], a.m.two_eb, 0.0f);
                             continue;
                         }
                         const Word* gcol = in + pbase + c;  // row r' at gcol[r' * RS]
@@ -269,7 +327,7 @@ __device__ __forceinline__ void colpass_tile(const ColArgs& a, const int blk)
                             break;
                         }
                         emit_point<PHASE, IN, FINAL, DEBUG, GRAD>(a, idx, 0, best, (Word)0, best != 0x7FFFFFFF,
-                                                                  acc, any_sign);
+                                                                  acc, any_sign, qb);
                     }
                 }
             }
@@ -295,7 +353,7 @@ __device__ __forceinline__ void colpass_tile(const ColArgs& a, const int blk)
                     *vfail = 1;
                     break;
                 }
-                emit_point<PHASE, IN, FINAL, DEBUG, GRAD>(a, pbase + r * RS + c, pbase + bh * RS + c, best, bw, true, acc, any_sign);
+                emit_point<PHASE, IN, FINAL, DEBUG, GRAD>(a, pbase + r * RS + c, pbase + bh * RS + c, best, bw, true, acc, any_sign, qb);
             }
         }
         __syncthreads();
@@ -304,6 +362,7 @@ __device__ __forceinline__ void colpass_tile(const ColArgs& a, const int blk)
     if (GRAD && use_envelope) acc = GradAcc();  // the envelope path redoes every row
 
     auto envelope_path = [&]() {
+    if (kQueries && tid == 0) s_qn = s_sn = 0;  // the envelope path emits every point again
     // ---- build: Algorithm 1's envelope over this band ------------------------
     uint16_t* scol = stk + col;  // stack entry i of this column at scol[i * W]
     {
@@ -431,7 +490,7 @@ __device__ __forceinline__ void colpass_tile(const ColArgs& a, const int blk)
     const int nl = nlst[col];
     if (nl == 0) {  // empty column: no site reaches it
         for (int r = r0; r < r1; ++r)
-            emit_point<PHASE, IN, FINAL, DEBUG, GRAD>(a, pbase + r * RS + c, 0, 0, (Word)0, false, acc, any_sign);
+            emit_point<PHASE, IN, FINAL, DEBUG, GRAD>(a, pbase + r * RS + c, 0, 0, (Word)0, false, acc, any_sign, qb);
         return;
     }
     // envelope entry of row r0: the first entry that the next one does not
@@ -531,7 +590,7 @@ __device__ __forceinline__ void colpass_tile(const ColArgs& a, const int blk)
                 grad_terms(pg, ps, pd1, val, a.m.idw_power, te, tp);
                 acc.add(te, tp);
             } else {
-                a.out[idx] = compensate(pq, pd1, val, ps, a.m);
+                if (!a.route_ctr || ps != 0) a.out[idx] = compensate(pq, pd1, val, ps, a.m);
                 if (DEBUG && a.dbg_dist2) a.dbg_dist2[idx] = val;
             }
             pq = nq;
@@ -539,7 +598,7 @@ __device__ __forceinline__ void colpass_tile(const ColArgs& a, const int blk)
             pd1 = nd1;
             ps = nsg;
         } else {
-            emit_point<PHASE, IN, FINAL, DEBUG, GRAD>(a, idx, pbase + h * RS + c, val, w, true, acc, any_sign);
+            emit_point<PHASE, IN, FINAL, DEBUG, GRAD>(a, idx, pbase + h * RS + c, val, w, true, acc, any_sign, qb);
         }
         idx += RS;
     }
@@ -554,6 +613,24 @@ __device__ __forceinline__ void colpass_tile(const ColArgs& a, const int blk)
         __syncthreads();
         if (band == 0 && c < a.C && a.col_count_out)
             a.col_count_out[(int64_t)p * a.C + c] = (uint16_t)min(s_sign[col], 65535);
+        // the tile's points go to the global lists with one atomic each
+        const int nq = min(s_qn, kQueryBuf), ns = s_sn;
+        if (a.qlist && (nq > 0 || ns > 0)) {
+            if (tid == 0) {
+                s_qbase = s_sbase = -1;
+                if (nq > 0) s_qbase = atomicAdd(a.route_ctr + kCtrQueries, nq);
+                if (ns > kSignedBuf)
+                    *static_cast<volatile int*>(a.route_ctr + kCtrSignedOver) = 1;
+                else if (ns > 0)
+                    s_sbase = atomicAdd(a.route_ctr + kCtrSigned, ns);
+            }
+            __syncthreads();
+            const int qbase = s_qbase, sbase = s_sbase;
+            if (qbase >= 0)
+                for (int i = tid; i < nq && qbase + i < a.qcap; i += nthr) a.qlist[qbase + i] = s_qbuf[i];
+            if (sbase >= 0)
+                for (int i = tid; i < ns && sbase + i < a.scap; i += nthr) a.slist[sbase + i] = s_sbuf[i];
+        }
     }
 
     if constexpr (GRAD) {  // the CTA's two sums: a fixed float-float tree over the threads
@@ -578,10 +655,22 @@ __device__ __forceinline__ void colpass_tile(const ColArgs& a, const int blk)
         }
     }}
 
+// One tile per CTA, or (a grid smaller than the tile count: the dense second
+// EDT behind the signed-point route, which mostly finds nothing to do) a loop
+// over the tiles.
 template <int PHASE, int IN, bool FINAL, bool DEBUG, bool NARROW>
 __global__ void __launch_bounds__(512, IN == 2 ? 3 : 2) k_colpass(ColArgs a)
 {
-    colpass_tile<PHASE, IN, FINAL, DEBUG, NARROW>(a, blockIdx.x);
+    if constexpr (PHASE == 1) {
+        colpass_tile<PHASE, IN, FINAL, DEBUG, NARROW>(a, blockIdx.x);
+    } else {
+        if (a.route_ctr && *static_cast<volatile int*>(a.route_ctr + kCtrDense) == 0) return;
+        const int tiles = ((a.C + (int)blockDim.x - 1) / (int)blockDim.x) * a.P;
+        for (int blk = blockIdx.x; blk < tiles; blk += gridDim.x) {
+            colpass_tile<PHASE, IN, FINAL, DEBUG, NARROW>(a, blk);
+            __syncthreads();
+        }
+    }
 }
 
 // Several fields in one launch: CTA b works on field f with
@@ -615,7 +704,9 @@ cudaError_t go(ColArgs& a, bool debug, bool narrow, dim3 grid, dim3 block, size_
     auto run = [&](auto kern) -> cudaError_t {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        kern<<<grid, block, smem, st>>>(a);
+        dim3 g = grid;
+        if (PHASE == 2 && a.route_ctr) g.x = std::min<unsigned>(g.x, resident_grid(kern, block, smem));
+        kern<<<g, block, smem, st>>>(a);
         return cudaGetLastError();
     };
     if (debug) return narrow ? run(k_colpass<PHASE, IN, FINAL, true, true>)

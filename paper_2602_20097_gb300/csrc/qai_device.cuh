@@ -41,6 +41,27 @@ struct MethodArgs {
     int output_c;        // write the compensation C instead of D''
 };
 
+// Signed-point route of the second EDT (qai_signed.cu). Step E adds
+// C = S w eta eps: where S = 0 the output is D' whatever Dist2 is, and on B1
+// (Dist1 = 0) the weight is 1 whatever Dist2 is. Dist2 is needed only at the
+// "queries": points with S != 0 off B1. The route counters live in the
+// workspace; row pass 1 zeroes them.
+enum RouteCtr : int {
+    kCtrQueries = 0,   // queries appended by the last pass of the first EDT
+    kCtrFailed = 1,    // queries whose local search found no B2 site
+    kCtrB2 = 2,        // B2 sites listed for the brute-force search
+    kCtrDense = 3,     // != 0: the dense second EDT must run
+    kCtrSigned = 4,    // B1 points with S != 0 appended (the rest of the signed set)
+    kCtrSignedOver = 5,// != 0: a tile had more of them than it could buffer
+    kCtrBruteDone = 6, // CTAs of the brute-force search that finished
+    kCtrWords = 16
+};
+// A query: linear index and (Dist1 << 2) | sign code of S.
+struct Query {
+    int32_t idx;
+    int32_t d1code;
+};
+
 // Row pass: one warp per x-row; rows enumerated (z, y).
 struct RowArgs {
     int rank, nz, ny, nx;
@@ -59,6 +80,11 @@ struct RowArgs {
     int32_t* dbg_idx;        // phase 1: nearest-site linear index along the row
     uint8_t* dbg_b2;
     int32_t* dbg_dist2;      // phase 2 final (rank 1)
+    // Signed-point route (rank 2 and 3, plain calls): phase 1 writes the
+    // output at every point (D' + S_B eta eps on B1, D' elsewhere) and zeroes
+    // the counters; phase 2 runs only when route_ctr[kCtrDense] != 0.
+    float* out_pre;
+    int* route_ctr;
     MethodArgs m;
 };
 
@@ -91,6 +117,38 @@ struct ColArgs {
     // without such points and scans for Dist2 only at them where they are few.
     uint16_t* col_count_out;
     const uint16_t* col_count_in;
+    // Signed-point route (plain calls). Phase 1 final: Dist1 is written only
+    // where S != 0 and each query is appended to qlist (at most qcap; the
+    // count goes on past it); phase 2: the pass runs only when
+    // route_ctr[kCtrDense] != 0, and the last pass writes only points with
+    // S != 0 (row pass 1 wrote every other output).
+    int* route_ctr;
+    Query* qlist;
+    int qcap;
+    int32_t* slist;          // B1 points with S != 0 (linear indices), at most scap
+    int scap;
+    MethodArgs m;
+};
+
+// The kernels of the signed-point route.
+struct RouteArgs {
+    int rank, nz, ny, nx;
+    const int32_t* q;
+    const uint8_t* eqm;      // equal-q neighbour mask of row pass 1
+    const int8_t* s;         // S
+    float* out;
+    int* ctr;                // RouteCtr words
+    const Query* qlist;
+    int qcap;
+    const int32_t* slist;    // B1 points with S != 0
+    int scap;
+    Query* flist;            // queries left to the brute-force search
+    int32_t* fmin;           // their Dist2, min-reduced by the brute-force CTAs
+    int fcap;
+    int32_t* b2list;         // B2 sites as (x | y << 16, z) pairs
+    int b2cap;
+    int max_r2;              // local search radius^2 (<= the offset table's)
+    long long brute_budget;  // largest failed x sites product searched by brute force
     MethodArgs m;
 };
 

@@ -20,7 +20,12 @@ struct Shape {
 
 // Byte offsets of the workspace slices of one field.
 struct Layout {
-    size_t eqm, xw, yw, dist1, s, idx, cflag, total;
+    size_t eqm, xw, yw, dist1, s, idx, cflag;
+    // signed-point route (rank 2 and 3): counters, queries, queries left to
+    // the brute-force search, B2 sites; capacities in entries
+    size_t ctr, qlist, slist, flist, fmin, b2list;
+    int qcap, scap, fcap, b2cap;
+    size_t total;
 };
 
 qai_status fail(qai_status s, const char* fmt, ...) __attribute__((format(printf, 2, 3)));

@@ -41,6 +41,15 @@ cudaError_t launch_colpass_grouped(int phase, int in_bytes, bool final_pass, con
 cudaError_t launch_colpass(int phase, int in_bytes, bool final_pass, ColArgs& a,
                            const ColConfig& cfg, bool debug, int64_t max_g, cudaStream_t st);
 
+// Signed-point route of the second EDT (qai_signed.cu): the shell search at
+// the queries, the list of B2 sites and the brute-force search; each kernel
+// reads the route counters and does nothing when it is not needed.
+int route_table_r2();
+cudaError_t launch_route_query(const RouteArgs& a, int blocks, cudaStream_t st);
+cudaError_t launch_route_b2dilate(const RouteArgs& a, int blocks, cudaStream_t st);
+cudaError_t launch_route_b2list(const RouteArgs& a, int blocks, cudaStream_t st);
+cudaError_t launch_route_brute(const RouteArgs& a, int blocks, cudaStream_t st);
+
 // Adjoint reduction of step E (qai_backward.cu).
 cudaError_t launch_backward(const BackArgs& a, cudaStream_t st);
 // Adds the per-CTA partial sums of the fused adjoint pass in a fixed order.

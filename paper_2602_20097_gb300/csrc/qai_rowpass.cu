@@ -23,6 +23,8 @@
 //      left one on a tie (the smaller index, as Algorithm 1's strict query).
 // Arithmetic on q is 32-bit; a warp whose loaded values reach |q| >= 2^27
 // (where a sum of six differences could overflow) takes a 64-bit path.
+#include <algorithm>
+
 #include "qai_device.cuh"
 #include "qai_launch.h"
 
@@ -270,6 +272,26 @@ __device__ __forceinline__ void rowpass_row(const RowArgs& a, const int row, uns
                         if (x0 + j < nx) a.eqm[rbase + x0 + j] = (uint8_t)(eq >> (8 * j));
                 }
             }
+            if (a.out_pre) {
+                // the output wherever Dist2 does not matter: on B1 the weight
+                // is 1 (C = S_B eta eps), elsewhere D' until a later kernel
+                // writes the points with S != 0; the same expressions as
+                // compensate(), so the same bits
+                float o[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const unsigned cd = (codes >> (2 * j)) & 3u;
+                    const float cc = (cd == 1u ? 1.0f : (cd == 2u ? -1.0f : 0.0f)) * a.m.eta_eb;
+                    o[j] = a.m.output_c ? cc : fmaf((float)c[j], a.m.two_eb, cc);
+                }
+                if (VEC) {
+                    if (x0 < nx) *reinterpret_cast<float4*>(a.out_pre + rbase + x0) = make_float4(o[0], o[1], o[2], o[3]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (x0 + j < nx) a.out_pre[rbase + x0 + j] = o[j];
+                }
+            }
             if (DEBUG) {
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
@@ -439,10 +461,22 @@ template <int PHASE, int RANK, bool FINAL, bool DEBUG, bool VEC>
 __global__ void __launch_bounds__(256) k_rowpass(RowArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int warp = threadIdx.x >> 5;
-    const int row = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (row >= a.nz * a.ny) return;  // whole warp leaves; only warp-level sync inside
-    rowpass_row<PHASE, RANK, FINAL, DEBUG, VEC>(a, row, smem + (size_t)warp * smem_per_warp(a.nx));
+    if (a.route_ctr) {
+        // signed-point route: row pass 1 starts the counters; row pass 2 (the
+        // dense second EDT) runs only when that route handed the field over
+        if (PHASE == 1) {
+            if (blockIdx.x == 0 && threadIdx.x < kCtrWords) a.route_ctr[threadIdx.x] = 0;
+        } else if (*static_cast<volatile int*>(a.route_ctr + kCtrDense) == 0) {
+            return;
+        }
+    }
+    const int warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
+    // one row per warp, or (a grid smaller than the rows: the dense second EDT
+    // behind the signed-point route) a loop over them; only warp-level sync
+    for (int row = blockIdx.x * warps + warp; row < a.nz * a.ny; row += gridDim.x * warps) {
+        rowpass_row<PHASE, RANK, FINAL, DEBUG, VEC>(a, row, smem + (size_t)warp * smem_per_warp(a.nx));
+        __syncwarp();
+    }
 }
 
 // Several fields in one launch: global row g belongs to field f with
@@ -473,7 +507,15 @@ cudaError_t go(const RowArgs& a, bool debug, bool vec, dim3 grid, dim3 block, si
     auto run = [&](auto kern) -> cudaError_t {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        kern<<<grid, block, smem, st>>>(a);
+        dim3 g = grid;
+        if (PHASE == 2 && a.route_ctr) {  // gated: a resident grid that loops over the rows
+            int dev = 0, sms = 152, per = 1;
+            if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, (int)block.x, smem) != cudaSuccess || per < 1)
+                per = 1;
+            g.x = std::min<unsigned>(g.x, (unsigned)(sms * per));
+        }
+        kern<<<g, block, smem, st>>>(a);
         return cudaGetLastError();
     };
     if (debug) return vec ? run(k_rowpass<PHASE, RANK, FINAL, true, true>)
@@ -497,7 +539,8 @@ void prepare_rowpass(RowArgs& a)
 {
     // 128-bit / 32-bit accesses need 4 | nx and 16-byte aligned base pointers
     auto al = [](const void* p, int b) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) % b) == 0; };
-    a.vec = (a.nx % 4 == 0) && al(a.q, 16) && al(a.eqm, 4) && al(a.s_in, 4) && al(a.xw, 8);
+    a.vec = (a.nx % 4 == 0) && al(a.q, 16) && al(a.eqm, 4) && al(a.s_in, 4) && al(a.xw, 8) &&
+            al(a.out_pre, 16);
 }
 
 cudaError_t launch_rowpass_grouped(int phase, bool final_pass, const RowTable& t, cudaStream_t st)

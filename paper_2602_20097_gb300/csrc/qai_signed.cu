@@ -1,0 +1,397 @@
+// qai_signed.cu -- the signed-point route of the second EDT (step D) and of
+// step E.
+//
+// Step E adds C = S w eta eps (Sec. VI-E). Where S = 0 the output is D'
+// whatever Dist2 is, and on B1 (Dist1 = 0) the weight is 1 whatever Dist2 is
+// (the boundary value eta eps); row pass 1 writes both of these outputs. Dist2
+// is needed only at the queries -- points with S != 0 off B1 -- which the last
+// pass of the first EDT lists, with the B1 points that have S != 0. These
+// kernels then give the exact Dist2 of every query, Eq. 2 over the
+// sign-flipping boundary B2 of Algorithm 3:
+//
+//   k_query    a shell search around the query (one warp each): lattice
+//              offsets in order of squared length, GetBoundary(S) evaluated at
+//              each candidate from S and the equal-q mask; the first hit is
+//              the minimum. A query with no B2 site within the search radius
+//              goes to a second list.
+//   k_b2dilate (only when such queries exist) lists the B2 sites from the
+//              signed points and their axis neighbours;
+//   k_b2list   (idem, when the list of signed points overflowed) lists them
+//              from a pass over the whole field;
+//   k_brute    (idem) min over the site list for each remaining query.
+//
+// A count over a capacity, or a brute-force product over its budget, sets the
+// dense flag; the dense second EDT (row pass 2, column passes 2) runs only
+// then, and rewrites every point with S != 0. Every route gives the same bits:
+// the same Dist2 goes into the same compensate().
+#include "qai_device.cuh"
+#include "qai_launch.h"
+
+namespace qai {
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// Lattice offsets with squared length <= kTableR2, in order of squared
+// length: (r2 << 24) | (dz & 0xFF) << 16 | (dy & 0xFF) << 8 | (dx & 0xFF).
+// off3 spans three axes, off2 two (dz = 0).
+constexpr int kTableR2 = 36;
+constexpr int kTableR = 6;
+constexpr int kN3 = 925, kN2 = 113;
+struct OffsetTable {
+    int off3[kN3];
+    int off2[kN2];
+};
+constexpr int pack_offset(int r2, int dz, int dy, int dx)
+{
+    return (int)(((unsigned)r2 << 24) | ((unsigned)(dz & 0xFF) << 16) | ((unsigned)(dy & 0xFF) << 8) |
+                 (unsigned)(dx & 0xFF));
+}
+constexpr OffsetTable make_offsets()
+{
+    OffsetTable t{};
+    int n3 = 0, n2 = 0;
+    for (int r2 = 0; r2 <= kTableR2; ++r2)
+        for (int dz = -kTableR; dz <= kTableR; ++dz)
+            for (int dy = -kTableR; dy <= kTableR; ++dy)
+                for (int dx = -kTableR; dx <= kTableR; ++dx)
+                    if (dz * dz + dy * dy + dx * dx == r2) {
+                        t.off3[n3++] = pack_offset(r2, dz, dy, dx);
+                        if (dz == 0) t.off2[n2++] = pack_offset(r2, 0, dy, dx);
+                    }
+    return t;
+}
+__constant__ OffsetTable c_off = make_offsets();
+
+// GetBoundary(S) of Algorithm 3 at an interior point b: an axis neighbour
+// (with the same q, under the SAME_Q reading) has a different S.
+// Every load is issued before any test, so their latencies overlap.
+template <int RANK>
+__device__ __forceinline__ bool is_b2(const RouteArgs& a, int64_t b)
+{
+    const int64_t pl = (int64_t)a.ny * a.nx;
+    const int sb = __ldg(a.s + b);
+    const unsigned em = a.m.b2_rule == 1 ? 0x3Fu : (unsigned)__ldg(a.eqm + b);
+    const int xl = __ldg(a.s + b - 1), xr = __ldg(a.s + b + 1);
+    const int yl = __ldg(a.s + b - a.nx), yr = __ldg(a.s + b + a.nx);
+    const int zl = RANK == 3 ? __ldg(a.s + b - pl) : sb, zr = RANK == 3 ? __ldg(a.s + b + pl) : sb;
+    const unsigned diff = (unsigned)(zl != sb) | (unsigned)(zr != sb) << 1 | (unsigned)(yl != sb) << 2 |
+                          (unsigned)(yr != sb) << 3 | (unsigned)(xl != sb) << 4 | (unsigned)(xr != sb) << 5;
+    return (diff & em) != 0;
+}
+
+__device__ __forceinline__ float query_output(const RouteArgs& a, const Query& e, int32_t d2)
+{
+    return compensate(__ldg(a.q + e.idx), e.d1code >> 2, d2, sign_of_code(e.d1code & 3), a.m);
+}
+
+// One warp per query: lane l evaluates offset 32 k + l of the table; the
+// lowest lane with a hit in the first chunk that has one holds the smallest
+// squared distance (the table is sorted by it).
+template <int RANK>
+__global__ void __launch_bounds__(256) k_query(RouteArgs a)
+{
+    volatile int* ctr = a.ctr;
+    if (ctr[kCtrDense]) return;
+    const int nq = ctr[kCtrQueries];
+    if (nq > a.qcap) {  // the list is incomplete: the dense route takes over
+        if (blockIdx.x == 0 && threadIdx.x == 0) ctr[kCtrDense] = 1;
+        return;
+    }
+    const int lane = threadIdx.x & 31;
+    const int* tab = RANK == 3 ? c_off.off3 : c_off.off2;
+    const int ntab = RANK == 3 ? kN3 : kN2;
+    const int plane = a.ny * a.nx;
+    const int wstride = gridDim.x * (blockDim.x >> 5);
+    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < nq; i += wstride) {
+        const Query e = a.qlist[i];
+        const int z = e.idx / plane, rem = e.idx - z * plane;
+        const int y = rem / a.nx, x = rem - y * a.nx;
+        // offset k of the table at this query: a B2 site? (r2 > max_r2: no)
+        auto probe = [&](int k, int& r2) -> bool {
+            const int o = k < ntab ? tab[k] : -1;
+            r2 = (int)((unsigned)o >> 24);
+            if (k >= ntab || r2 > a.max_r2) return false;
+            const int bx = x + (int)(int8_t)(o & 0xFF);
+            const int by = y + (int)(int8_t)((o >> 8) & 0xFF);
+            const int bz = z + (int)(int8_t)((o >> 16) & 0xFF);
+            // B2 lies on interior points only (extents of kept axes are >= 2)
+            const bool inner = (unsigned)(bx - 1) < (unsigned)(a.nx - 2) && (unsigned)(by - 1) < (unsigned)(a.ny - 2) &&
+                               (RANK == 2 || (unsigned)(bz - 1) < (unsigned)(a.nz - 2));
+            return inner && is_b2<RANK>(a, (int64_t)bz * plane + (int64_t)by * a.nx + bx);
+        };
+        int found = -1;
+        // the first 32 offsets (most queries end here), then 128 per step
+        // (four per lane, their loads in flight together)
+        for (int k0 = 0, step = 32; k0 < ntab && (int)((unsigned)tab[k0] >> 24) <= a.max_r2; k0 += step, step = 128) {
+            int r2[4];
+            bool hit[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                hit[u] = false;
+                r2[u] = 0;
+                if (u == 0 || step == 128) hit[u] = probe(k0 + 32 * u + lane, r2[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const unsigned h = __ballot_sync(kFull, hit[u]);
+                if (h && found < 0) found = __shfl_sync(kFull, r2[u], __ffs(h) - 1);
+            }
+            if (found >= 0) break;
+        }
+        if (lane == 0) {
+            if (found >= 0) {
+                a.out[e.idx] = query_output(a, e, found);
+            } else {
+                const int k = atomicAdd(a.ctr + kCtrFailed, 1);
+                if (k < a.fcap) {
+                    a.flist[k] = e;
+                    a.fmin[k] = kDistInf;
+                }
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t load4_u8(const void* base, int64_t off, int x0, int nx, bool vec)
+{
+    const uint8_t* p = static_cast<const uint8_t*>(base) + off;
+    if (vec) return x0 < nx ? __ldg(reinterpret_cast<const uint32_t*>(p + x0)) : 0u;
+    uint32_t w = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (x0 + j < nx) w |= (uint32_t)__ldg(p + x0 + j) << (8 * j);
+    return w;
+}
+
+// Appends B2 site (x, y, z) to the list (warp-aggregated: one atomic per warp).
+__device__ __forceinline__ void append_sites(const RouteArgs& a, unsigned nib, int x0, int y, int z)
+{
+    const int lane = threadIdx.x & 31;
+    if (!__ballot_sync(kFull, nib != 0)) return;
+    const int cnt = __popc(nib);
+    int incl = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int v = __shfl_up_sync(kFull, incl, d);
+        if (lane >= d) incl += v;
+    }
+    int base = 0;
+    if (lane == 31) base = atomicAdd(a.ctr + kCtrB2, incl);
+    base = __shfl_sync(kFull, base, 31) + incl - cnt;
+    uint2* list = reinterpret_cast<uint2*>(a.b2list);
+    for (int j = 0; j < 4; ++j) {
+        if (!((nib >> j) & 1u)) continue;
+        if (base < a.b2cap) list[base] = make_uint2((uint32_t)(x0 + j) | ((uint32_t)y << 16), (uint32_t)z);
+        ++base;
+    }
+}
+
+// The B2 sites, from the signed set: a site has S != 0 or an axis neighbour
+// with S != 0 (GetBoundary(S) compares S across a pair), so every site is a
+// signed point or an axis neighbour of one. Each signed point tests itself and
+// its neighbours with S = 0; a neighbour with S = 0 is tested only by its
+// signed neighbour of smallest linear index, so no site is listed twice.
+// Runs when some query needs the list and the signed set is complete.
+template <int RANK>
+__global__ void __launch_bounds__(256) k_b2dilate(RouteArgs a)
+{
+    volatile int* ctr = a.ctr;
+    if (ctr[kCtrDense] || ctr[kCtrFailed] == 0 || ctr[kCtrSignedOver] || ctr[kCtrSigned] > a.scap) return;
+    const int ns = ctr[kCtrSigned], nq = ctr[kCtrQueries];
+    const int plane = a.ny * a.nx;
+    constexpr int nb = 2 * RANK;
+    auto nbr_off = [&](int j) -> int {  // z-, z+, y-, y+, x-, x+ (rank 3); y-, y+, x-, x+ (rank 2)
+        const int ax = RANK == 3 ? j >> 1 : (j >> 1) + 1;
+        const int step = ax == 0 ? plane : (ax == 1 ? a.nx : 1);
+        return (j & 1) ? step : -step;
+    };
+    const int total = (ns + nq) * (nb + 1);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t - (int)threadIdx.x < total; t += gridDim.x * blockDim.x) {
+        unsigned site = 0;
+        int bx = 0, by = 0, bz = 0;
+        if (t < total) {
+            const int item = t / (nb + 1), j = t - item * (nb + 1);
+            const int p = item < ns ? a.slist[item] : a.qlist[item - ns].idx;
+            const int b = j == nb ? p : p + nbr_off(j);
+            bz = b / plane;
+            const int rem = b - bz * plane;
+            by = rem / a.nx;
+            bx = rem - by * a.nx;
+            const bool inner = (unsigned)(bx - 1) < (unsigned)(a.nx - 2) && (unsigned)(by - 1) < (unsigned)(a.ny - 2) &&
+                               (RANK == 2 || (unsigned)(bz - 1) < (unsigned)(a.nz - 2));
+            // p +- step stays inside the field when b is interior; a neighbour
+            // off the interior is never a site, whatever wrapped index it has
+            bool own = inner;
+            if (own && j != nb) {
+                // b has S = 0 and p is its signed neighbour of smallest index
+                int sv[2 * RANK];
+#pragma unroll
+                for (int k = 0; k < 2 * RANK; ++k) sv[k] = __ldg(a.s + b + nbr_off(k));
+                own = __ldg(a.s + b) == 0;
+#pragma unroll
+                for (int k = 0; k < 2 * RANK; ++k)
+                    if (b + nbr_off(k) < p && sv[k] != 0) own = false;
+            }
+            site = own && is_b2<RANK>(a, (int64_t)b) ? 1u : 0u;
+        }
+        append_sites(a, site, bx, by, bz);
+    }
+}
+
+__device__ __forceinline__ uint32_t load4_s8(const int8_t* p, int x0, int nx, bool vec)
+{
+    if (vec) return x0 < nx ? __ldg(reinterpret_cast<const uint32_t*>(p + x0)) : 0u;
+    uint32_t w = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (x0 + j < nx) w |= (uint32_t)(uint8_t)__ldg(p + x0 + j) << (8 * j);
+    return w;
+}
+
+// Every B2 site of the field, for the case where the signed set overflowed
+// its list. One warp per interior row, 128 points per step (4 per lane).
+template <int RANK>
+__global__ void __launch_bounds__(256) k_b2list(RouteArgs a, int vec)
+{
+    volatile int* ctr = a.ctr;
+    if (ctr[kCtrDense] || ctr[kCtrFailed] == 0 || !(ctr[kCtrSignedOver] || ctr[kCtrSigned] > a.scap)) return;
+    const int lane = threadIdx.x & 31;
+    const int rows = a.nz * a.ny;
+    const int plane = a.ny * a.nx;
+    const uint8_t* eqm = a.eqm;
+    const bool literal = a.m.b2_rule == 1;
+    const int wstride = gridDim.x * (blockDim.x >> 5);
+    for (int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += wstride) {
+        const int z = row / a.ny, y = row - z * a.ny;
+        if (y < 1 || y > a.ny - 2 || (RANK == 3 && (z < 1 || z > a.nz - 2))) continue;  // warp-uniform
+        const int8_t* sr = a.s + (int64_t)row * a.nx;
+        const uint8_t* er = eqm + (int64_t)row * a.nx;
+        uint32_t carry = 0;  // S word of the previous step (its byte 3 is the left neighbour)
+        for (int x0s = 0; x0s < a.nx; x0s += 128) {
+            const int x0 = x0s + 4 * lane;
+            const uint32_t cw = load4_s8(sr, x0, a.nx, vec);
+            uint32_t xmw = __shfl_up_sync(kFull, cw, 1);
+            uint32_t xpw = __shfl_down_sync(kFull, cw, 1);
+            const uint32_t last = __shfl_sync(kFull, cw, 31);
+            if (lane == 0) xmw = carry;
+            if (lane == 31) xpw = x0 + 4 < a.nx ? (uint32_t)(uint8_t)__ldg(sr + x0 + 4) : 0u;
+            carry = last;
+            const uint32_t eqw = literal ? 0xFFFFFFFFu : load4_s8(reinterpret_cast<const int8_t*>(er), x0, a.nx, vec);
+            // byte k of sel(bit) = 0xFF if bit `bit` of equal-q mask byte k is set
+            auto sel = [&](int bit) -> uint32_t { return __vcmpne4(eqw & (0x01010101u << bit), 0u); };
+            uint32_t b2 = (__vcmpne4(__byte_perm(xmw, cw, 0x6543), cw) & sel(4)) |
+                          (__vcmpne4(__byte_perm(cw, xpw, 0x4321), cw) & sel(5)) |
+                          (__vcmpne4(load4_s8(sr - a.nx, x0, a.nx, vec), cw) & sel(2)) |
+                          (__vcmpne4(load4_s8(sr + a.nx, x0, a.nx, vec), cw) & sel(3));
+            if (RANK == 3) {
+                b2 |= (__vcmpne4(load4_s8(sr - plane, x0, a.nx, vec), cw) & sel(0)) |
+                      (__vcmpne4(load4_s8(sr + plane, x0, a.nx, vec), cw) & sel(1));
+            }
+            unsigned nib = ((b2 & 0x80808080u) * 0x00204081u) >> 28;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)  // interior along x; bytes past the row end are not points
+                if (x0 + j < 1 || x0 + j > a.nx - 2) nib &= ~(1u << j);
+            append_sites(a, nib, x0, y, z);
+        }
+    }
+}
+
+// Exact Dist2 of each query left by k_query: min over the listed B2 sites.
+// CTA i takes 256 queries (block i % qb) against one slice of the site list
+// (i / qb), staged through shared memory; each thread folds its minimum into
+// fmin with an atomic, and the last CTA to finish writes the outputs.
+constexpr int kBruteChunk = 1024;
+__global__ void __launch_bounds__(256) k_brute(RouteArgs a)
+{
+    volatile int* ctr = a.ctr;
+    if (ctr[kCtrDense]) return;
+    const int nf = ctr[kCtrFailed];
+    if (nf == 0) return;
+    const int nb = ctr[kCtrB2];
+    const int qblocks = (nf + blockDim.x - 1) / blockDim.x;
+    if (nf > a.fcap || nb > a.b2cap || (long long)nf * nb > a.brute_budget || qblocks > (int)gridDim.x) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) ctr[kCtrDense] = 1;
+        return;
+    }
+    __shared__ uint2 sites[kBruteChunk];
+    __shared__ int last;
+    const uint2* list = reinterpret_cast<const uint2*>(a.b2list);
+    const int plane = a.ny * a.nx;
+    const int qb = qblocks;
+    const int slices = max(1, (int)gridDim.x / qb);
+    const int qblk = blockIdx.x % qb, slice = blockIdx.x / qb;
+    if (slice < slices) {
+        const int per = (nb + slices - 1) / slices;
+        const int b0 = min(nb, slice * per), b1 = min(nb, b0 + per);
+        const int f = qblk * blockDim.x + threadIdx.x;
+        int x = 0, y = 0, z = 0;
+        if (f < nf) {
+            const int idx = a.flist[f].idx;
+            z = idx / plane;
+            const int rem = idx - z * plane;
+            y = rem / a.nx;
+            x = rem - y * a.nx;
+        }
+        int best = kDistInf;
+        for (int c0 = b0; c0 < b1; c0 += kBruteChunk) {
+            const int n = min(kBruteChunk, b1 - c0);
+            __syncthreads();
+            for (int i = threadIdx.x; i < n; i += blockDim.x) sites[i] = list[c0 + i];
+            __syncthreads();
+            for (int i = 0; i < n; ++i) {
+                const uint2 b = sites[i];
+                const int dx = (int)(b.x & 0xFFFFu) - x, dy = (int)(b.x >> 16) - y, dz = (int)b.y - z;
+                best = min(best, dz * dz + dy * dy + dx * dx);
+            }
+        }
+        if (f < nf && best < kDistInf) atomicMin(a.fmin + f, best);
+    }
+    // the last CTA writes every output (no B2 at all: Dist2 = INF, w = 1)
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(a.ctr + kCtrBruteDone, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        for (int f = threadIdx.x; f < nf; f += blockDim.x) {
+            const Query e = a.flist[f];
+            a.out[e.idx] = query_output(a, e, *static_cast<volatile int32_t*>(a.fmin + f));
+        }
+    }
+}
+
+}  // namespace
+
+int route_table_r2() { return kTableR2; }
+
+cudaError_t launch_route_query(const RouteArgs& a, int blocks, cudaStream_t st)
+{
+    if (a.rank == 3) k_query<3><<<blocks, 256, 0, st>>>(a);
+    else k_query<2><<<blocks, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_route_b2dilate(const RouteArgs& a, int blocks, cudaStream_t st)
+{
+    if (a.rank == 3) k_b2dilate<3><<<blocks, 256, 0, st>>>(a);
+    else k_b2dilate<2><<<blocks, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_route_b2list(const RouteArgs& a, int blocks, cudaStream_t st)
+{
+    auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 3) == 0; };
+    const int vec = (a.nx % 4 == 0) && al(a.s) && al(a.eqm);
+    if (a.rank == 3) k_b2list<3><<<blocks, 256, 0, st>>>(a, vec);
+    else k_b2list<2><<<blocks, 256, 0, st>>>(a, vec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_route_brute(const RouteArgs& a, int blocks, cudaStream_t st)
+{
+    k_brute<<<blocks, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace qai

@@ -14,10 +14,13 @@ namespace {
 // Workspace of the largest accepted field: at most 12 bytes per point (the
 // rank-3 layout: equal-q mask 1, Dist1 4, S 1, xwords 2, ywords 4), a uint16
 // count per column of the last column pass (at most one byte per point, since
-// that pass has at least two rows) and the 256-byte alignment of its six
-// slices.
+// that pass has at least two rows), the lists of the signed-point route
+// (N / 128 + 1024 queries of 8 bytes, N / 256 + 1024 signed boundary points of
+// 4 bytes, at most 65536 queries for the brute-force search at 12 bytes,
+// N / 256 + 1024 B2 sites of 8 bytes; under N / 8 + 1 MiB with the counters)
+// and the 256-byte alignment of its slices (inside that MiB).
 constexpr int64_t kMaxPoints = QAI_STATIC_MAX_POINTS;
-constexpr size_t kScratchBytes = (size_t)13 * (size_t)kMaxPoints + 6 * 256;
+constexpr size_t kScratchBytes = (size_t)13 * (size_t)kMaxPoints + (size_t)kMaxPoints / 8 + ((size_t)1 << 20);
 
 __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 

@@ -11,8 +11,8 @@ Names follow the C ABI in ``include/qai.h``:
   ``debug=True`` also returns the per-step maps B1, S_B, Dist1, I1, S, B2, Dist2.
 * :func:`mitigate_host` -- the same from/to host (pinned) tensors, with the
   copies made by the library on the stream.
-* :func:`workspace_size`, :func:`profile_enable`, :func:`profile_read`,
-  :func:`launch_count`.
+* :func:`workspace_size`, :func:`route_counts`, :func:`profile_enable`,
+  :func:`profile_read`, :func:`launch_count`.
 """
 from __future__ import annotations
 
@@ -65,6 +65,7 @@ SIGNATURES = {
     "qai_workspace_size": (ctypes.c_int, [ctypes.c_int, P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_size_t)]),
     "qai_mitigate": (ctypes.c_int, [P, P, ctypes.c_int, P, ctypes.c_double, ctypes.POINTER(Params),
                                     P, ctypes.c_size_t, P, ctypes.POINTER(DebugOut)]),
+    "qai_route_counts": (ctypes.c_int, [P, ctypes.c_int, P, P, P]),
     "qai_workspace_size_host": (ctypes.c_int, [ctypes.c_int, P, ctypes.POINTER(ctypes.c_size_t)]),
     "qai_mitigate_host": (ctypes.c_int, [P, P, ctypes.c_int, P, ctypes.c_double, ctypes.POINTER(Params),
                                          P, ctypes.c_size_t, P]),
@@ -202,6 +203,19 @@ def mitigate(q: torch.Tensor, eb: float, eta: float = 0.9, idw_power: float = 1.
                           ctypes.byref(dbg) if dbg is not None else None)
     _check(rc)
     return (out, maps) if debug else out
+
+
+def route_counts(workspace: torch.Tensor, shape, stream=None) -> dict:
+    """How the last plain :func:`mitigate` on ``workspace`` (rank 2 or 3)
+    computed the second EDT: ``queries`` (points with S != 0 off B1, where
+    Dist2 matters), ``list_searched`` (those the shell search left to the
+    search over all B2 sites), ``b2_sites`` (sites listed for it), ``dense``
+    (the dense second EDT ran) and ``signed_b1`` (B1 points with S != 0, -1
+    when too many to list). Synchronises the stream."""
+    c = (ctypes.c_int32 * 5)()
+    _check(load().qai_route_counts(workspace.data_ptr(), len(shape), _dims(shape), c, _stream(stream)))
+    return {"queries": c[0], "list_searched": c[1], "b2_sites": c[2], "dense": bool(c[3]),
+            "signed_b1": c[4]}
 
 
 def mitigate_host(q_host: torch.Tensor, eb: float, out_host: torch.Tensor | None = None,
