@@ -261,8 +261,18 @@ def run_qai(args):
     warm = max(3, args.warmup)
     for _ in range(warm):
         qai.mitigate(q, eb, out=out, workspace=ws)
+    # untimed pass with every kernel bracketed by events: the per-kernel
+    # breakdown and the dominant kernel; the timed region below brackets only
+    # that kernel, so the other launches run back to back as in real use
     qai.profile_read()
+    qai.profile_select(None)
     qai.profile_enable(True)
+    for _ in range(max(3, min(args.steps, 10))):
+        qai.mitigate(q, eb, out=out, workspace=ws)
+    torch.cuda.synchronize()
+    kstats = qai.profile_read()
+    dom_name = max(kstats.items(), key=lambda kv: kv[1][1])[0] if kstats else None
+    qai.profile_select(dom_name)
     barrier()
     n0 = qai.launch_count()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -283,8 +293,9 @@ def run_qai(args):
         tc1 = time.perf_counter()
         time.sleep(0.1)
     launches = qai.launch_count() - n0
-    kstats = qai.profile_read()
+    dstats = qai.profile_read()
     qai.profile_enable(False)
+    qai.profile_select(None)
     ms = ev0.elapsed_time(ev1) / args.steps
     t = torch.tensor([ms], device=dev, dtype=torch.float64)
     if world > 1:
@@ -319,7 +330,7 @@ def run_qai(args):
             dist.destroy_process_group()
         return 0
     peak, peak_src = hbm_peak()
-    dom = max(kstats.items(), key=lambda kv: kv[1][1]) if kstats else None
+    dom = (dom_name, dstats[dom_name]) if dom_name in dstats else None
     roof = None
     if dom:
         name, (nl, tot_ms, algo_bytes) = dom
@@ -333,6 +344,8 @@ def run_qai(args):
     kernels = {k: {"launches": v[0], "ms_per_launch": v[1] / v[0],
                    "algo_gbs": v[2] / (v[1] * 1e-3) / 1e9,
                    "share": v[1] / sum(s[1] for s in kstats.values())} for k, v in kstats.items()}
+    kernels_note = ("every kernel bracketed by CUDA events in an untimed pass right before the timed "
+                    "region; the roofline kernel is timed inside the timed region, alone")
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -361,6 +374,7 @@ def run_qai(args):
         "signed_route": route,
         "second_bound": second,
         "kernels": kernels,
+        "kernels_note": kernels_note,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

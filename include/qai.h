@@ -110,18 +110,24 @@ qai_status qai_mitigate(const int32_t* d_q, float* d_out, int rank, const int64_
                         double eb, const qai_params* params, void* d_ws, size_t ws_bytes,
                         cudaStream_t stream, const qai_debug_out* dbg);
 
-/* How the last plain qai_mitigate call on this workspace computed the second
- * EDT (step D) of a rank-2 or rank-3 field. Step E needs Dist2 only at the
- * points with S != 0 off B1 (elsewhere C = 0, or the weight is 1: Sec. VI-E),
- * so a plain call finds their nearest B2 site by an exact shell search, lists
- * the B2 sites and searches them all for the points the shell search leaves,
- * and runs the dense second EDT over the whole field only when one of those
- * lists overflows. Outputs are the same bits on every route.
+/* How the last plain qai_mitigate call on this workspace computed the two
+ * EDTs (steps B and D) of a rank-2 or rank-3 field. The first: where B1 is
+ * dense, every point's nearest B1 point is a few cells away, and a bounded
+ * exact search finds it (in order of distance, then linear index: the tie
+ * rule of Algorithm 1's passes); the separable passes run when it cannot.
+ * The second: step E needs Dist2 only at the points with S != 0 off B1
+ * (elsewhere C = 0, or the weight is 1: Sec. VI-E), so a plain call finds
+ * their nearest B2 site by an exact shell search, lists the B2 sites and
+ * searches them all for the points the shell search leaves, and runs the
+ * dense second EDT over the whole field only when one of those lists
+ * overflows. Outputs are the same bits on every route.
  *  d_ws     the workspace of that call (device), after the call completed
- *  counts   host int32[5]: points with S != 0 off B1; of them, those left to
+ *  counts   host int32[6]: points with S != 0 off B1; of them, those left to
  *           the list search; B2 sites listed (0 if the list was not needed);
  *           1 if the dense second EDT ran, else 0; B1 points with S != 0
- *           (-1 if there were too many to list)
+ *           (-1 if there were too many to list); 1 if the separable first
+ *           EDT ran because some point had no B1 point within squared
+ *           distance 8 (the first EDT's bounded search), else 0
  * Synchronises `stream`. Returns QAI_ERR_SHAPE for rank-1 fields (no such
  * route) or an unsupported shape, QAI_ERR_INVALID_ARG for NULL pointers. */
 qai_status qai_route_counts(const void* d_ws, int rank, const int64_t* dims, int32_t* counts,
@@ -309,6 +315,11 @@ typedef struct {
 
 qai_status qai_profile_enable(int on);
 int qai_profile_read(qai_kernel_stat* out, int cap);
+
+/* Restricts the per-kernel timing to the kernels named `name` (a copy is
+ * kept; NULL or "" times every kernel again). Fewer events on the stream
+ * disturb the timed work less. */
+qai_status qai_profile_select(const char* name);
 
 /* Number of kernel launches made by the library since load (all entry points). */
 int64_t qai_launch_count(void);

@@ -56,6 +56,7 @@ struct Stat {
 };
 std::mutex g_prof_mu;
 bool g_prof_on = false;
+std::string g_prof_only;  // time only kernels of this name ("" = all)
 std::vector<Pending> g_pending;
 std::vector<Stat> g_stats;
 std::vector<cudaEvent_t> g_event_pool;
@@ -80,7 +81,7 @@ cudaError_t timed(const char* name, double algo_bytes, cudaStream_t st, F&& fn)
     bool prof;
     {
         std::lock_guard<std::mutex> lk(g_prof_mu);
-        prof = g_prof_on;
+        prof = g_prof_on && (g_prof_only.empty() || g_prof_only == name);
         if (prof) {
             a = take_event();
             b = take_event();
@@ -228,6 +229,15 @@ Route signed_route()
     return Route::Auto;
 }
 
+// First EDT of plain calls with the signed-point route: the local search with
+// the separable passes behind it (default), or QAI_FIRST_EDT = "separable"
+// (the separable passes alone). Read on every call; both give the same bits.
+bool local_first_edt()
+{
+    const char* v = getenv("QAI_FIRST_EDT");
+    return !(v && !strcmp(v, "separable"));
+}
+
 // CTAs of the last EDT2 pass (the sums it leaves in the partials array).
 int final_pass_blocks(const Shape& sh)
 {
@@ -264,13 +274,37 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
     const Route route = signed_route();
     const bool signed_route_on = !debug && !grad && sh.rank >= 2 && route != Route::Off;
     int* ctr = signed_route_on ? reinterpret_cast<int*>(ws + lay.ctr) : nullptr;
+    const bool local = ctr && local_first_edt();
+    const int* local_fail = local ? ctr + qai::kCtrLocalFail : nullptr;  // gate of the separable first EDT
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (ctr) {
+        if ((e = cudaMemsetAsync(ctr, 0, qai::kCtrWords * sizeof(int), st)) != cudaSuccess)
+            return cuda_fail(e, "route counters");
+    }
+    if (local) {
+        // Steps A-C by the bounded nearest-site search; the separable passes
+        // below run only if some point has no B1 point within reach.
+        qai::LocalArgs la{};
+        la.rank = sh.rank; la.nz = sh.nz; la.ny = sh.ny; la.nx = sh.nx;
+        la.q = d_q; la.eqm = eqm; la.s = s; la.dist1 = dist1; la.out = d_out; la.ctr = ctr;
+        la.qlist = reinterpret_cast<qai::Query*>(ws + lay.qlist); la.qcap = lay.qcap;
+        la.slist = reinterpret_cast<int32_t*>(ws + lay.slist); la.scap = lay.scap;
+        la.m = m;
+        auto al = [](const void* p, int b) { return (reinterpret_cast<uintptr_t>(p) % b) == 0; };
+        la.vec = (sh.nx % 4 == 0) && al(d_q, 16) && al(d_out, 16) && al(eqm, 4);
+        e = timed("detect", N * 9.0, st, [&] { return qai::launch_local_detect(la, 8 * sms, st); });
+        if (e != cudaSuccess) return cuda_fail(e, "step A");
+        e = timed("near", N * 2.0, st, [&] { return qai::launch_local_near(la, 8 * sms, st); });
+        if (e != cudaSuccess) return cuda_fail(e, "nearest-site search");
+    }
 
     // Step A + EDT-x of B1 (rank 1: the whole first EDT).
     qai::RowArgs r1{};
     r1.rank = sh.rank; r1.nz = sh.nz; r1.ny = sh.ny; r1.nx = sh.nx;
     r1.q = d_q; r1.eqm = eqm; r1.m = m;
     r1.dbg_b1 = d.b1; r1.dbg_sb = d.sb;
-    if (ctr) { r1.out_pre = d_out; r1.route_ctr = ctr; }
+    if (ctr) { r1.out_pre = d_out; r1.route_ctr = ctr; r1.gate = local_fail; }
     const bool final1 = sh.rank == 1;
     if (final1) { r1.dist1 = dist1; r1.s_out = s; r1.dbg_idx = d.idx1; }
     else { r1.xw = xw; r1.dbg_idx = d.idx1 ? (sh.rank == 3 ? d.idx1 : idx_tmp) : nullptr; }
@@ -309,6 +343,7 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
         if (!ctr) return;
         c.route_ctr = ctr; c.qlist = qlist; c.qcap = lay.qcap;
         c.slist = reinterpret_cast<int32_t*>(ws + lay.slist); c.scap = lay.scap;
+        c.gate = local_fail;
     };
     if (sh.rank == 2) {
         qai::ColArgs c = y_args(xw);
@@ -319,6 +354,7 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
     } else if (sh.rank == 3) {
         qai::ColArgs c = y_args(xw);
         c.out_w = yw;
+        c.gate = local_fail;
         if (d.idx1) { c.dbg_idx_in = d.idx1; c.dbg_idx_out = idx_tmp; }
         if ((st_ = colpass(1, 2, false, c, "colpass1_y", 2 + 4)) != QAI_OK) return st_;
         qai::ColArgs cz = z_args(yw);
@@ -347,13 +383,11 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
         ra.brute_budget = 1LL << 28;
         ra.m = m;
         if (route == Route::Dense) ra.qcap = -1;  // every count is over it: hand over at once
-        int dev = 0, sms = 152;
-        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         e = timed("signed_query", 0.0, st, [&] { return qai::launch_route_query(ra, 4 * sms, st); });
         if (e != cudaSuccess) return cuda_fail(e, "signed-point shell search");
-        e = timed("signed_b2dilate", 0.0, st, [&] { return qai::launch_route_b2dilate(ra, 4 * sms, st); });
-        if (e != cudaSuccess) return cuda_fail(e, "B2 sites from the signed points");
-        e = timed("signed_b2list", N * 2.0, st, [&] { return qai::launch_route_b2list(ra, 8 * sms, st); });
+        e = timed("signed_query_far", 0.0, st, [&] { return qai::launch_route_query_far(ra, 4 * sms, st); });
+        if (e != cudaSuccess) return cuda_fail(e, "signed-point shell search, second phase");
+        e = timed("signed_b2sites", 0.0, st, [&] { return qai::launch_route_b2sites(ra, 8 * sms, st); });
         if (e != cudaSuccess) return cuda_fail(e, "B2 site list");
         e = timed("signed_brute", 0.0, st, [&] { return qai::launch_route_brute(ra, 2 * sms, st); });
         if (e != cudaSuccess) return cuda_fail(e, "brute-force search");
@@ -366,7 +400,7 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
     r2.dbg_b2 = d.b2;
     if (final1) { r2.dist1_in = dist1; r2.out = d_out; r2.dbg_dist2 = d.dist2; }
     else r2.xw = xw;
-    r2.route_ctr = ctr;
+    r2.gate = ctr ? ctr + qai::kCtrDense : nullptr;
     e = timed(final1 ? "rowpass2_final" : "rowpass2", N * (final1 ? 14.0 : 4.0), st,
               [&] { return qai::launch_rowpass(2, final1, r2, debug, st); });
     if (e != cudaSuccess) return cuda_fail(e, "row pass 2");
@@ -374,7 +408,10 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
     // EDT2 along y (and z), the last pass fused with step E.
     auto fuse_e = [&](qai::ColArgs& c) {
         c.out = d_out; c.q = d_q; c.dist1_in = dist1; c.s_in = s; c.dbg_dist2 = d.dist2;
-        c.col_count_in = cflag; c.route_ctr = ctr;
+        // the per-column counts exist only when the separable first EDT ran
+        c.col_count_in = local ? nullptr : cflag;
+        c.route_ctr = ctr;
+        c.gate = ctr ? ctr + qai::kCtrDense : nullptr;
     };
     // Adjoint mode: the last pass reads G, Dist1, S and the input words.
     auto last_grad = [&](qai::ColArgs& c, int in_bytes, const char* name) -> qai_status {
@@ -397,7 +434,7 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
     } else if (sh.rank == 3) {
         qai::ColArgs c = y_args(xw);
         c.out_w = yw;
-        c.route_ctr = ctr;
+        c.gate = ctr ? ctr + qai::kCtrDense : nullptr;
         if ((st_ = colpass(2, 2, false, c, "colpass2_y", 2 + 4)) != QAI_OK) return st_;
         qai::ColArgs cz = z_args(yw);
         if (grad) return last_grad(cz, 4, "colpass2_z_grad");
@@ -482,10 +519,11 @@ qai_status qai_route_counts(const void* d_ws, int rank, const int64_t* dims, int
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return cuda_fail(e, "read route counters");
     counts[0] = c[qai::kCtrQueries];
-    counts[1] = c[qai::kCtrFailed];
+    counts[1] = c[qai::kCtrUnresolved];
     counts[2] = c[qai::kCtrB2];
     counts[3] = c[qai::kCtrDense] != 0;
     counts[4] = c[qai::kCtrSignedOver] ? -1 : c[qai::kCtrSigned];
+    counts[5] = c[qai::kCtrLocalFail] != 0;
     return QAI_OK;
 }
 
@@ -748,6 +786,13 @@ qai_status qai_profile_enable(int on)
 {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     g_prof_on = on != 0;
+    return QAI_OK;
+}
+
+qai_status qai_profile_select(const char* name)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_only = name ? name : "";
     return QAI_OK;
 }
 

@@ -157,8 +157,6 @@ __device__ __forceinline__ void emit_point(const ColArgs& a, int idx, int src, i
 template <int PHASE, int IN, bool FINAL, bool DEBUG, bool NARROW, bool GRAD = false>
 __device__ __forceinline__ void colpass_tile(const ColArgs& a, const int blk)
 {
-    if (PHASE == 2 && a.route_ctr && *static_cast<volatile int*>(a.route_ctr + kCtrDense) == 0)
-        return;  // the signed-point route handled the second EDT
     GradAcc acc;
     using Word = std::conditional_t<IN == 2, uint16_t, uint32_t>;
     constexpr Word kWInf = IN == 2 ? (Word)kInf16 : (Word)kInf32;
@@ -655,21 +653,21 @@ __device__ __forceinline__ void colpass_tile(const ColArgs& a, const int blk)
         }
     }}
 
-// One tile per CTA, or (a grid smaller than the tile count: the dense second
-// EDT behind the signed-point route, which mostly finds nothing to do) a loop
-// over the tiles.
+// One tile per CTA, or (a gated launch: the passes behind the signed-point
+// route and the local first EDT, which mostly find nothing to do) a resident
+// grid that loops over the tiles.
 template <int PHASE, int IN, bool FINAL, bool DEBUG, bool NARROW>
 __global__ void __launch_bounds__(512, IN == 2 ? 3 : 2) k_colpass(ColArgs a)
 {
-    if constexpr (PHASE == 1) {
+    if (!a.gate) {
         colpass_tile<PHASE, IN, FINAL, DEBUG, NARROW>(a, blockIdx.x);
-    } else {
-        if (a.route_ctr && *static_cast<volatile int*>(a.route_ctr + kCtrDense) == 0) return;
-        const int tiles = ((a.C + (int)blockDim.x - 1) / (int)blockDim.x) * a.P;
-        for (int blk = blockIdx.x; blk < tiles; blk += gridDim.x) {
-            colpass_tile<PHASE, IN, FINAL, DEBUG, NARROW>(a, blk);
-            __syncthreads();
-        }
+        return;
+    }
+    if (*static_cast<const volatile int*>(a.gate) == 0) return;  // the flag is not set
+    const int tiles = ((a.C + (int)blockDim.x - 1) / (int)blockDim.x) * a.P;
+    for (int blk = blockIdx.x; blk < tiles; blk += gridDim.x) {
+        colpass_tile<PHASE, IN, FINAL, DEBUG, NARROW>(a, blk);
+        __syncthreads();
     }
 }
 
@@ -705,7 +703,7 @@ cudaError_t go(ColArgs& a, bool debug, bool narrow, dim3 grid, dim3 block, size_
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         dim3 g = grid;
-        if (PHASE == 2 && a.route_ctr) g.x = std::min<unsigned>(g.x, resident_grid(kern, block, smem));
+        if (a.gate) g.x = std::min<unsigned>(g.x, resident_grid(kern, block, smem));
         kern<<<g, block, smem, st>>>(a);
         return cudaGetLastError();
     };

@@ -54,6 +54,9 @@ enum RouteCtr : int {
     kCtrSigned = 4,    // B1 points with S != 0 appended (the rest of the signed set)
     kCtrSignedOver = 5,// != 0: a tile had more of them than it could buffer
     kCtrBruteDone = 6, // CTAs of the brute-force search that finished
+    kCtrUnresolved = 7,// queries left to the brute-force search by both shell searches
+    kCtrLocalFail = 15,// != 0: the local first EDT left a point without its site;
+                       // the separable first EDT runs (and zeroes the words before)
     kCtrWords = 16
 };
 // A query: linear index and (Dist1 << 2) | sign code of S.
@@ -82,9 +85,11 @@ struct RowArgs {
     int32_t* dbg_dist2;      // phase 2 final (rank 1)
     // Signed-point route (rank 2 and 3, plain calls): phase 1 writes the
     // output at every point (D' + S_B eta eps on B1, D' elsewhere) and zeroes
-    // the counters; phase 2 runs only when route_ctr[kCtrDense] != 0.
+    // the counters below kCtrLocalFail. gate: the kernel runs only when *gate
+    // != 0 (then on a resident grid that loops over the rows).
     float* out_pre;
     int* route_ctr;
+    const int* gate;
     MethodArgs m;
 };
 
@@ -119,10 +124,11 @@ struct ColArgs {
     const uint16_t* col_count_in;
     // Signed-point route (plain calls). Phase 1 final: Dist1 is written only
     // where S != 0 and each query is appended to qlist (at most qcap; the
-    // count goes on past it); phase 2: the pass runs only when
-    // route_ctr[kCtrDense] != 0, and the last pass writes only points with
-    // S != 0 (row pass 1 wrote every other output).
+    // count goes on past it); phase 2 final writes only points with S != 0
+    // (the first EDT wrote every other output). gate: the pass runs only when
+    // *gate != 0 (then on a resident grid that loops over the tiles).
     int* route_ctr;
+    const int* gate;
     Query* qlist;
     int qcap;
     int32_t* slist;          // B1 points with S != 0 (linear indices), at most scap
@@ -149,6 +155,24 @@ struct RouteArgs {
     int b2cap;
     int max_r2;              // local search radius^2 (<= the offset table's)
     long long brute_budget;  // largest failed x sites product searched by brute force
+    MethodArgs m;
+};
+
+// The local first EDT (qai_local.cu): step A, then the nearest B1 site of
+// every point by a bounded exact search, S and the signed-point lists.
+struct LocalArgs {
+    int rank, nz, ny, nx;
+    const int32_t* q;
+    uint8_t* eqm;            // equal-q mask (bits 0-5) and sign code of S_B (bits 6-7)
+    int8_t* s;               // S
+    int32_t* dist1;          // Dist1 where S != 0
+    float* out;              // D' + S_B eta eps on B1, D' elsewhere
+    int* ctr;                // RouteCtr words
+    Query* qlist;
+    int qcap;
+    int32_t* slist;
+    int scap;
+    int vec;                 // 128-bit loads of q usable
     MethodArgs m;
 };
 

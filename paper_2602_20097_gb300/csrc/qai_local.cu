@@ -1,0 +1,462 @@
+// qai_local.cu -- the local first EDT: steps A, B and C of Algorithm 4 for
+// fields whose quantization boundary is dense.
+//
+// Step B needs, at every point, the nearest point of B1 (Eq. 2) with the
+// smallest linear index among equally near ones (the tie rule of the
+// separable passes of Algorithm 1), and step C its sign S = S_B[I1]
+// (Algorithm 3). Where B1 is dense -- a rough field or a small error bound,
+// where almost every point differs from a neighbour -- the nearest site is a
+// few cells away, and a bounded search finds it exactly:
+//
+//   k_detect  step A (Algorithm 2) at every point: the equal-q mask with the
+//             sign code of S_B packed in (a point is on B1 iff it is interior
+//             and some neighbour differs; points off the interior get the
+//             all-equal mask), the output wherever Dist2 does not matter
+//             (D' + S_B eta eps on B1, D' elsewhere), and the list of B1
+//             points with S != 0.
+//   k_near    every point off B1 scans the lattice offsets of squared length
+//             <= 8 in order of (squared length, dz, dy, dx) -- for points
+//             inside the field that is the order of (distance, linear index)
+//             -- and takes the first B1 point it meets: Dist1 and I1 exactly,
+//             since any point outside that ball is at squared distance >= 9.
+//             It writes S everywhere, Dist1 where S != 0, and lists the
+//             queries of the second EDT (S != 0 off B1).
+//
+// A point with no B1 point within that ball sets kCtrLocalFail; the separable
+// first EDT (row pass 1, column passes 1) then runs and rewrites all of it.
+#include "qai_detect.cuh"
+#include "qai_device.cuh"
+#include "qai_launch.h"
+
+namespace qai {
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// Offsets of squared length 1..8, sorted by (r2, dz, dy, dx): (r2 << 24) |
+// (dz & 0xFF) << 16 | (dy & 0xFF) << 8 | (dx & 0xFF). near3 spans three axes,
+// near2 two (dz = 0).
+constexpr int kNearR2 = 8;
+constexpr int kNearN3 = 92, kNearN2 = 24;
+struct NearTable {
+    int off3[kNearN3];
+    int off2[kNearN2];
+};
+constexpr int pack_near(int r2, int dz, int dy, int dx)
+{
+    return (int)(((unsigned)r2 << 24) | ((unsigned)(dz & 0xFF) << 16) | ((unsigned)(dy & 0xFF) << 8) |
+                 (unsigned)(dx & 0xFF));
+}
+constexpr NearTable make_near()
+{
+    NearTable t{};
+    int n3 = 0, n2 = 0;
+    for (int r2 = 1; r2 <= kNearR2; ++r2)
+        for (int dz = -2; dz <= 2; ++dz)
+            for (int dy = -2; dy <= 2; ++dy)
+                for (int dx = -2; dx <= 2; ++dx)
+                    if (dz * dz + dy * dy + dx * dx == r2) {
+                        t.off3[n3++] = pack_near(r2, dz, dy, dx);
+                        if (dz == 0) t.off2[n2++] = pack_near(r2, 0, dy, dx);
+                    }
+    return t;
+}
+__constant__ NearTable c_near = make_near();
+
+// Per-CTA collection of list entries before one global atomic per CTA.
+constexpr int kSignedCta = 1024;
+constexpr int kQueryCta = 512;
+
+// Step A on one warp-segment of 128 points (4 per lane) of row `row`.
+template <int RANK, bool VEC>
+__device__ __forceinline__ void detect_segment(const LocalArgs& a, int row, int z, int y, int x0, int32_t* sbuf,
+                                               int* sn)
+{
+    const int lane = threadIdx.x & 31;
+    const int nx = a.nx;
+    const int rbase = row * nx;
+    const int plane = a.ny * nx;
+    const bool row_inner = y >= 1 && y <= a.ny - 2 && (RANK == 2 || (z >= 1 && z <= a.nz - 2));
+    int c[4], yl[4] = {0, 0, 0, 0}, yr[4] = {0, 0, 0, 0}, zl[4] = {0, 0, 0, 0}, zr[4] = {0, 0, 0, 0};
+    load4_i32(a.q + rbase, x0, nx, VEC, c);
+    int xm = __shfl_up_sync(kFull, c[3], 1);
+    int xp = __shfl_down_sync(kFull, c[0], 1);
+    if (lane == 0) xm = x0 > 0 ? __ldg(a.q + rbase + x0 - 1) : 0;
+    if (lane == 31) xp = x0 + 4 < nx ? __ldg(a.q + rbase + x0 + 4) : 0;
+    unsigned em = 0x3F3F3F3Fu;  // all equal: off the interior nothing is on B1
+    unsigned codes = 0;         // 2-bit sign code of S_B per point (B1 points only)
+    if (row_inner) {            // warp-uniform
+        load4_i32(a.q + rbase - nx, x0, nx, VEC, yl);
+        load4_i32(a.q + rbase + nx, x0, nx, VEC, yr);
+        if (RANK == 3) {
+            load4_i32(a.q + rbase - plane, x0, nx, VEC, zl);
+            load4_i32(a.q + rbase + plane, x0, nx, VEC, zr);
+        }
+        // 32-bit sums are exact while every |q| < 2^27; OR of the raw values
+        // is below 2^27 exactly when all are in [0, 2^27), the common case
+        unsigned acc = (unsigned)xm | (unsigned)xp;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc |= (unsigned)c[j] | (unsigned)yl[j] | (unsigned)yr[j] | (unsigned)zl[j] | (unsigned)zr[j];
+        bool narrow = acc < (1u << 27);
+        if (!__all_sync(kFull, narrow)) {
+            acc = (unsigned)(xm ^ (xm >> 31)) | (unsigned)(xp ^ (xp >> 31));
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                acc |= (unsigned)(c[j] ^ (c[j] >> 31)) | (unsigned)(yl[j] ^ (yl[j] >> 31)) |
+                       (unsigned)(yr[j] ^ (yr[j] >> 31)) | (unsigned)(zl[j] ^ (zl[j] >> 31)) |
+                       (unsigned)(zr[j] ^ (zr[j] >> 31));
+            narrow = acc < (1u << 27);
+        }
+        const bool wide = __any_sync(kFull, !narrow);
+        // interior along x: only the first and the last lanes of a row have
+        // points off it
+        const unsigned inner_bits = (x0 >= 1 && x0 + 4 <= nx - 1)
+                                        ? 0xFu
+                                        : ((x0 >= 1 && x0 <= nx - 2) ? 1u : 0u) | ((x0 + 1 >= 1 && x0 + 1 <= nx - 2) ? 2u : 0u) |
+                                              ((x0 + 2 <= nx - 2) ? 4u : 0u) | ((x0 + 3 <= nx - 2) ? 8u : 0u);
+        em = 0;
+        if (!wide && a.m.sign_rule == 0) {
+            // the common case in two steps: masks and the fast-varying test
+            // at every point, the sign only where a boundary keeps it
+            const int thm1 = a.m.grad_threshold - 1;
+            const unsigned lim = 2u * (unsigned)thm1;
+            unsigned keep = 0;  // bit j: point j is on B1 and not fast-varying
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int q0 = c[j];
+                const int l = j == 0 ? xm : c[j - 1];
+                const int r = j == 3 ? xp : c[j + 1];
+                unsigned mk = (l == q0 ? 0x10u : 0u) | (r == q0 ? 0x20u : 0u);
+                bool fast = (unsigned)(r - l + thm1) > lim;
+                mk |= (yl[j] == q0 ? 0x4u : 0u) | (yr[j] == q0 ? 0x8u : 0u);
+                fast |= (unsigned)(yr[j] - yl[j] + thm1) > lim;
+                if (RANK == 3) {
+                    mk |= (zl[j] == q0 ? 0x1u : 0u) | (zr[j] == q0 ? 0x2u : 0u);
+                    fast |= (unsigned)(zr[j] - zl[j] + thm1) > lim;
+                } else {
+                    mk |= 0x3u;
+                }
+                const bool inner = (inner_bits >> j) & 1u;
+                keep |= (inner && mk != 0x3Fu && !fast) ? 1u << j : 0u;
+                em |= (inner ? mk : 0x3Fu) << (8 * j);
+            }
+            if (__any_sync(kFull, keep != 0)) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (!((keep >> j) & 1u)) continue;
+                    const int l = j == 0 ? xm : c[j - 1];
+                    const int r = j == 3 ? xp : c[j + 1];
+                    int sum = l + r + yl[j] + yr[j] - 2 * RANK * c[j];
+                    if (RANK == 3) sum += zl[j] + zr[j];
+                    const unsigned cd = sum > 0 ? 1u : (sum < 0 ? 2u : 0u);
+                    em |= cd << (8 * j + 6);
+                    codes |= cd << (2 * j);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const bool inner = (inner_bits >> j) & 1u;
+                const int l = j == 0 ? xm : c[j - 1];
+                const int r = j == 3 ? xp : c[j + 1];
+                unsigned mk;
+                bool site;
+                int code;
+                if (!wide) detect_point<RANK, false>(c[j], zl[j], zr[j], yl[j], yr[j], l, r, inner, a.m, mk, site, code);
+                else detect_point<RANK, true>(c[j], zl[j], zr[j], yl[j], yr[j], l, r, inner, a.m, mk, site, code);
+                const unsigned cd = (unsigned)code;  // 0 off the interior
+                em |= ((inner ? mk : 0x3Fu) | cd << 6) << (8 * j);
+                codes |= cd << (2 * j);
+            }
+        }
+    }
+    // outputs where Dist2 does not matter: the expressions of compensate()
+    // (with C = +0 the fma is the product)
+    float o[4];
+    if (__any_sync(kFull, codes != 0)) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const unsigned cd = (codes >> (2 * j)) & 3u;
+            const float cc = (cd == 1u ? 1.0f : (cd == 2u ? -1.0f : 0.0f)) * a.m.eta_eb;
+            o[j] = a.m.output_c ? cc : fmaf((float)c[j], a.m.two_eb, cc);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) o[j] = a.m.output_c ? 0.0f : (float)c[j] * a.m.two_eb;
+    }
+    if (VEC) {
+        if (x0 < nx) {
+            *reinterpret_cast<uint32_t*>(a.eqm + rbase + x0) = em;
+            *reinterpret_cast<float4*>(a.out + rbase + x0) = make_float4(o[0], o[1], o[2], o[3]);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (x0 + j < nx) {
+                a.eqm[rbase + x0 + j] = (uint8_t)(em >> (8 * j));
+                a.out[rbase + x0 + j] = o[j];
+            }
+    }
+    // B1 points with S != 0: Dist1 = 0 there, and the signed set lists them
+    if (codes) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (((codes >> (2 * j)) & 3u) == 0u) continue;
+            a.dist1[rbase + x0 + j] = 0;
+            const int k = atomicAdd(sn, 1);
+            if (k < kSignedCta) sbuf[k] = rbase + x0 + j;
+        }
+    }
+}
+
+template <int RANK, bool VEC>
+__global__ void __launch_bounds__(256) k_detect(LocalArgs a)
+{
+    __shared__ int32_t sbuf[kSignedCta];
+    __shared__ int sn, sbase;
+    if (threadIdx.x == 0) sn = 0;
+    __syncthreads();
+    const int rows = a.nz * a.ny;
+    const int wstride = gridDim.x * (blockDim.x >> 5);
+    for (int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += wstride) {
+        const int z = RANK == 3 ? row / a.ny : 0;
+        const int y = row - z * a.ny;
+        for (int x0 = 4 * (threadIdx.x & 31); x0 - 4 * (int)(threadIdx.x & 31) < a.nx; x0 += 128)
+            detect_segment<RANK, VEC>(a, row, z, y, x0, sbuf, &sn);
+    }
+    __syncthreads();
+    const int n = sn;
+    if (threadIdx.x == 0) {
+        sbase = -1;
+        if (n > kSignedCta) *static_cast<volatile int*>(a.ctr + kCtrSignedOver) = 1;
+        else if (n > 0) sbase = atomicAdd(a.ctr + kCtrSigned, n);
+    }
+    __syncthreads();
+    if (sbase >= 0)
+        for (int i = threadIdx.x; i < n && sbase + i < a.scap; i += blockDim.x) a.slist[sbase + i] = sbuf[i];
+}
+
+// The nearest B1 point of p (off B1): its squared distance and the sign code
+// it carries, or r2 = -1 when none lies within squared distance 8.
+// The nearest B1 point of p (off B1) among table entries k0.. (the first 6,
+// or 4 in 2-D, are the squared distance 1): its squared distance and the sign
+// code it carries, or r2 = -1 when none lies within squared distance 8. The table is scanned in chunks of eight entries whose
+// loads are issued together; the first B1 point in table order is the answer.
+template <int RANK>
+__device__ __forceinline__ void nearest_site(const LocalArgs& a, int p, int z, int y, int x, int k0, int& r2,
+                                             unsigned& code)
+{
+    const int plane = a.ny * a.nx;
+    const int* tab = RANK == 3 ? c_near.off3 : c_near.off2;
+    constexpr int ntab = RANK == 3 ? kNearN3 : kNearN2;
+    r2 = -1;
+    code = 0;
+    for (; k0 < ntab; k0 += 8) {
+        unsigned e[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            e[u] = 0x3Fu;
+            const int k = k0 + u;
+            if (k >= ntab) continue;
+            const int o = tab[k];
+            const int dx = (int)(int8_t)(o & 0xFF), dy = (int)(int8_t)((o >> 8) & 0xFF);
+            const int dz = (int)(int8_t)((o >> 16) & 0xFF);
+            const bool in = (unsigned)(x + dx) < (unsigned)a.nx && (unsigned)(y + dy) < (unsigned)a.ny &&
+                            (RANK == 2 || (unsigned)(z + dz) < (unsigned)a.nz);
+            if (in) e[u] = __ldg(a.eqm + p + dz * plane + dy * a.nx + dx);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (k0 + u < ntab && (e[u] & 0x3Fu) != 0x3Fu) {
+                r2 = (int)((unsigned)tab[k0 + u] >> 24);
+                code = e[u] >> 6;
+                return;
+            }
+        }
+    }
+}
+
+// Four bytes of a row at x0.. (0x3F, "not on B1", past the row end).
+__device__ __forceinline__ uint32_t load4_em(const uint8_t* row, int x0, int nx, bool vec)
+{
+    if (vec) return x0 < nx ? __ldg(reinterpret_cast<const uint32_t*>(row + x0)) : 0x3F3F3F3Fu;
+    uint32_t w = 0x3F3F3F3Fu;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (x0 + j < nx) w = (w & ~(0xFFu << (8 * j))) | (uint32_t)__ldg(row + x0 + j) << (8 * j);
+    return w;
+}
+
+// Byte k = 0xFF where byte k of the mask word marks a B1 point (some of its
+// six equal-q bits clear): t = the clear bits, at most 0x3F per byte, so
+// t + 0x3F sets bit 6 of a byte exactly when t is not zero, with no carry.
+__device__ __forceinline__ uint32_t site_bytes(uint32_t w)
+{
+    const uint32_t t = ~w & 0x3F3F3F3Fu;
+    return (((t + 0x3F3F3F3Fu) & 0x40404040u) >> 6) * 0xFFu;
+}
+
+// S at every point, Dist1 where S != 0 off B1, and the queries. One warp per
+// row; a lane holds WPL words of four points (WPL = 4: one 128-bit load per
+// row when the rows are 16-byte multiples). The six neighbours at squared
+// distance 1 are tested for four points at once, byte-wise, in the tie order
+// z-, y-, x-, x+, y+, z+ (increasing linear index); the rare point with none
+// of them on B1 scans the rest of the table alone.
+template <int RANK, int WPL>
+__global__ void __launch_bounds__(256) k_near(LocalArgs a)
+{
+    constexpr int PPL = 4 * WPL;   // points per lane and step
+    constexpr int STEP = 32 * PPL; // points per warp and step
+    __shared__ Query qbuf[kQueryCta];
+    __shared__ int qn, qbase;
+    if (threadIdx.x == 0) qn = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int rows = a.nz * a.ny;
+    const int plane = a.ny * a.nx;
+    const int wstride = gridDim.x * (blockDim.x >> 5);
+    bool fail = false;
+    // WPL words of a row at x0 (0x3F: no point)
+    auto load_row = [&](const uint8_t* row, int x0) -> uint4 {
+        if (WPL == 4)
+            return x0 < a.nx ? __ldg(reinterpret_cast<const uint4*>(row + x0))
+                             : make_uint4(0x3F3F3F3Fu, 0x3F3F3F3Fu, 0x3F3F3F3Fu, 0x3F3F3F3Fu);
+        return make_uint4(load4_em(row, x0, a.nx, false), 0u, 0u, 0u);
+    };
+    auto word = [](const uint4& v, int k) -> uint32_t { return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w)); };
+    const uint4 none = make_uint4(0x3F3F3F3Fu, 0x3F3F3F3Fu, 0x3F3F3F3Fu, 0x3F3F3F3Fu);
+    for (int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += wstride) {
+        const int z = RANK == 3 ? row / a.ny : 0;
+        const int y = row - z * a.ny;
+        const uint8_t* er = a.eqm + (int64_t)row * a.nx;
+        int8_t* sr = a.s + (int64_t)row * a.nx;
+        uint32_t carry = 0x3F3F3F3Fu;  // last word of the previous step (its byte 3 is x - 1 of byte 0)
+        for (int xs = 0; xs < a.nx; xs += STEP) {
+            const int x0 = xs + PPL * lane;
+            // words of the row and of its four neighbour rows (absent: no B1 point)
+            const uint4 c = load_row(er, x0);
+            const uint4 yl = y > 0 ? load_row(er - a.nx, x0) : none;
+            const uint4 yr = y < a.ny - 1 ? load_row(er + a.nx, x0) : none;
+            const uint4 zl = RANK == 3 && z > 0 ? load_row(er - plane, x0) : none;
+            const uint4 zr = RANK == 3 && z < a.nz - 1 ? load_row(er + plane, x0) : none;
+            uint32_t prev = __shfl_up_sync(kFull, word(c, WPL - 1), 1);
+            uint32_t next = __shfl_down_sync(kFull, c.x, 1);
+            const uint32_t last = __shfl_sync(kFull, word(c, WPL - 1), 31);
+            if (lane == 0) prev = carry;
+            if (lane == 31) next = x0 + PPL < a.nx ? (uint32_t)__ldg(er + x0 + PPL) : 0x3Fu;
+            carry = last;
+            uint32_t sw[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+            for (int k = 0; k < WPL; ++k) {
+                const int xk = x0 + 4 * k;
+                const uint32_t cw = word(c, k);
+                const uint32_t xlw = __byte_perm(k == 0 ? prev : word(c, k - 1), cw, 0x6543);  // byte j: x - 1
+                const uint32_t xrw = __byte_perm(cw, k == WPL - 1 ? next : word(c, k + 1), 0x4321);
+                // the first B1 neighbour in tie order: select from the last to the first
+                const uint32_t own = site_bytes(cw);
+                uint32_t found = 0, pick = 0x3F3F3F3Fu;
+                auto take = [&](uint32_t w) {
+                    const uint32_t m = site_bytes(w);
+                    pick = (w & m) | (pick & ~m);
+                    found |= m;
+                };
+                take(word(zr, k));
+                take(word(yr, k));
+                take(xrw);
+                take(xlw);
+                take(word(yl, k));
+                take(word(zl, k));
+                // codes: own on B1, else the neighbour's; Dist1 = 1 where resolved
+                // off B1 (bytes past the row end, and x - 1 of x = 0, read 0x3F)
+                const int nvalid = min(4, a.nx - xk);
+                const uint32_t valid = nvalid >= 4 ? 0xFFFFFFFFu : (nvalid <= 0 ? 0u : (1u << (8 * nvalid)) - 1u);
+                uint32_t cw2 = ((own & cw) | (~own & pick)) >> 6 & 0x03030303u;
+                const uint32_t need = ~own & ~found & valid;  // no site within r2 = 1: scan the table
+                uint32_t d1w = ~own & 0x01010101u;
+                if (need) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        if (!((need >> (8 * j)) & 0xFFu)) continue;
+                        int r2;
+                        unsigned code;
+                        nearest_site<RANK>(a, row * a.nx + xk + j, z, y, xk + j, RANK == 3 ? 6 : 4, r2, code);
+                        if (r2 < 0) {
+                            fail = true;
+                            r2 = 0;
+                            code = 0;
+                        }
+                        cw2 = (cw2 & ~(0xFFu << (8 * j))) | code << (8 * j);
+                        d1w = (d1w & ~(0xFFu << (8 * j))) | (uint32_t)r2 << (8 * j);
+                    }
+                }
+                // S bytes: code 1 -> +1, code 2 -> -1
+                const uint32_t pos = cw2 & 0x01010101u, neg = (cw2 >> 1) & 0x01010101u;
+                sw[k] = pos | (neg * 0xFFu);
+                // queries: S != 0 off B1
+                const uint32_t qmask = (pos | neg) & ~own & valid;
+                if (qmask) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        if (!((qmask >> (8 * j)) & 1u)) continue;
+                        const int p = row * a.nx + xk + j;
+                        const int r2 = (int)((d1w >> (8 * j)) & 0xFFu);
+                        const unsigned code = (cw2 >> (8 * j)) & 3u;
+                        a.dist1[p] = r2;
+                        const Query qe{p, (r2 << 2) | (int)code};
+                        const int kq = atomicAdd(&qn, 1);
+                        if (kq < kQueryCta) {
+                            qbuf[kq] = qe;
+                        } else {
+                            const int g = atomicAdd(a.ctr + kCtrQueries, 1);
+                            if (g < a.qcap) a.qlist[g] = qe;
+                        }
+                    }
+                }
+            }
+            if (WPL == 4) {
+                if (x0 < a.nx)
+                    *reinterpret_cast<uint4*>(sr + x0) = make_uint4(sw[0], sw[1], sw[2], sw[3]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (x0 + j < a.nx) sr[x0 + j] = (int8_t)(sw[0] >> (8 * j));
+            }
+        }
+    }
+    if (__any_sync(kFull, fail) && lane == 0) *static_cast<volatile int*>(a.ctr + kCtrLocalFail) = 1;
+    __syncthreads();
+    const int n = min(qn, kQueryCta);
+    if (threadIdx.x == 0) qbase = n > 0 ? atomicAdd(a.ctr + kCtrQueries, n) : 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n && qbase + i < a.qcap; i += blockDim.x) a.qlist[qbase + i] = qbuf[i];
+}
+
+}  // namespace
+
+cudaError_t launch_local_detect(const LocalArgs& a, int blocks, cudaStream_t st)
+{
+    if (a.rank == 3) {
+        if (a.vec) k_detect<3, true><<<blocks, 256, 0, st>>>(a);
+        else k_detect<3, false><<<blocks, 256, 0, st>>>(a);
+    } else {
+        if (a.vec) k_detect<2, true><<<blocks, 256, 0, st>>>(a);
+        else k_detect<2, false><<<blocks, 256, 0, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_local_near(const LocalArgs& a, int blocks, cudaStream_t st)
+{
+    auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+    const bool wide = (a.nx % 16 == 0) && al(a.eqm) && al(a.s);  // 16-byte rows
+    if (a.rank == 3) {
+        if (wide) k_near<3, 4><<<blocks, 256, 0, st>>>(a);
+        else k_near<3, 1><<<blocks, 256, 0, st>>>(a);
+    } else {
+        if (wide) k_near<2, 4><<<blocks, 256, 0, st>>>(a);
+        else k_near<2, 1><<<blocks, 256, 0, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace qai

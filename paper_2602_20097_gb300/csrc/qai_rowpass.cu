@@ -25,6 +25,7 @@
 // (where a sum of six differences could overflow) takes a 64-bit path.
 #include <algorithm>
 
+#include "qai_detect.cuh"
 #include "qai_device.cuh"
 #include "qai_launch.h"
 
@@ -55,21 +56,6 @@ struct RowSmem {
     int* nextr;       // [nseg] first site ref right of the segment
 };
 
-__device__ __forceinline__ void load4_i32(const int32_t* p, int x0, int nx, bool vec, int v[4])
-{
-    if (vec) {
-        if (x0 < nx) {
-            const int4 t = __ldg(reinterpret_cast<const int4*>(p + x0));
-            v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
-        } else {
-            v[0] = v[1] = v[2] = v[3] = 0;
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) v[j] = (x0 + j < nx) ? __ldg(p + x0 + j) : 0;
-    }
-}
-
 __device__ __forceinline__ uint32_t load4_u8(const void* base, int x0, int nx, bool vec)
 {
     const uint8_t* p = static_cast<const uint8_t*>(base);
@@ -79,101 +65,6 @@ __device__ __forceinline__ uint32_t load4_u8(const void* base, int x0, int nx, b
     for (int j = 0; j < 4; ++j)
         if (x0 + j < nx) w |= (uint32_t)__ldg(p + x0 + j) << (8 * j);
     return w;
-}
-
-// Step A for one point: the equal-q neighbour mask (bits z-, z+, y-, y+, x-,
-// x+; absent axes count as equal), whether it is a boundary, its sign code.
-template <int RANK, bool WIDE>
-__device__ __forceinline__ void detect_point(int q0, int zl, int zr, int yl, int yr, int xl, int xr,
-                                             bool inner, const MethodArgs& m, unsigned& mask,
-                                             bool& site, int& code)
-{
-    mask = (unsigned)(xl == q0) << 4 | (unsigned)(xr == q0) << 5;
-    if (RANK >= 2) mask |= (unsigned)(yl == q0) << 2 | (unsigned)(yr == q0) << 3;
-    else mask |= 0xCu;
-    if (RANK >= 3) mask |= (unsigned)(zl == q0) | (unsigned)(zr == q0) << 1;
-    else mask |= 0x3u;
-    site = inner && mask != 0x3Fu;
-    int sg, first = 0;
-    bool fast;
-    if (!WIDE) {
-        int sum = (xl - q0) + (xr - q0);
-        const unsigned thm1 = (unsigned)m.grad_threshold - 1u, lim = 2u * thm1;
-        fast = (unsigned)(xr - xl + (int)thm1) > lim;
-        if (RANK >= 2) { sum += (yl - q0) + (yr - q0); fast |= (unsigned)(yr - yl + (int)thm1) > lim; }
-        if (RANK >= 3) { sum += (zl - q0) + (zr - q0); fast |= (unsigned)(zr - zl + (int)thm1) > lim; }
-        sg = (sum > 0) - (sum < 0);
-        if (m.sign_rule == 1) {
-            // first differing neighbour in the order z-, z+, y-, y+, x-, x+
-            first = xr != q0 ? (xr > q0 ? 1 : -1) : 0;
-            first = xl != q0 ? (xl > q0 ? 1 : -1) : first;
-            if (RANK >= 2) {
-                first = yr != q0 ? (yr > q0 ? 1 : -1) : first;
-                first = yl != q0 ? (yl > q0 ? 1 : -1) : first;
-            }
-            if (RANK >= 3) {
-                first = zr != q0 ? (zr > q0 ? 1 : -1) : first;
-                first = zl != q0 ? (zl > q0 ? 1 : -1) : first;
-            }
-        }
-    } else {
-        const int64_t Q = q0;
-        int64_t sum = ((int64_t)xl - Q) + ((int64_t)xr - Q);
-        auto gr = [&](int lo, int hi) {
-            int64_t g = (int64_t)hi - lo;
-            return (g < 0 ? -g : g) >= (int64_t)m.grad_threshold;
-        };
-        fast = gr(xl, xr);
-        if (RANK >= 2) { sum += ((int64_t)yl - Q) + ((int64_t)yr - Q); fast |= gr(yl, yr); }
-        if (RANK >= 3) { sum += ((int64_t)zl - Q) + ((int64_t)zr - Q); fast |= gr(zl, zr); }
-        sg = (sum > 0) - (sum < 0);
-        if (m.sign_rule == 1) {
-            first = xr != q0 ? (xr > q0 ? 1 : -1) : 0;
-            first = xl != q0 ? (xl > q0 ? 1 : -1) : first;
-            if (RANK >= 2) {
-                first = yr != q0 ? (yr > q0 ? 1 : -1) : first;
-                first = yl != q0 ? (yl > q0 ? 1 : -1) : first;
-            }
-            if (RANK >= 3) {
-                first = zr != q0 ? (zr > q0 ? 1 : -1) : first;
-                first = zl != q0 ? (zl > q0 ? 1 : -1) : first;
-            }
-        }
-    }
-    if (m.sign_rule == 1) sg = first;
-    code = (site && !fast) ? sign_code(sg) : 0;
-}
-
-// The common case of detect_point: sign rule SUM and every |q| < 2^27, so
-// that the sum of the neighbour differences fits 32 bits.
-template <int RANK>
-__device__ __forceinline__ void detect_sum32(int q0, int zl, int zr, int yl, int yr, int xl, int xr,
-                                             bool inner, int thm1, unsigned lim, unsigned& mask,
-                                             unsigned& site, unsigned& code)
-{
-    unsigned mk = (xl == q0 ? 0x10u : 0u) | (xr == q0 ? 0x20u : 0u);
-    int sum = xl + xr;
-    bool fast = (unsigned)(xr - xl + thm1) > lim;
-    if (RANK >= 2) {
-        mk |= (yl == q0 ? 0x4u : 0u) | (yr == q0 ? 0x8u : 0u);
-        sum += yl + yr;
-        fast |= (unsigned)(yr - yl + thm1) > lim;
-    } else {
-        mk |= 0xCu;
-    }
-    if (RANK >= 3) {
-        mk |= (zl == q0 ? 0x1u : 0u) | (zr == q0 ? 0x2u : 0u);
-        sum += zl + zr;
-        fast |= (unsigned)(zr - zl + thm1) > lim;
-    } else {
-        mk |= 0x3u;
-    }
-    sum -= 2 * RANK * q0;
-    const bool s = inner && mk != 0x3Fu;
-    const unsigned cd = sum > 0 ? 1u : (sum < 0 ? 2u : 0u);
-    code = (s && !fast) ? cd : 0u;
-    site = s ? 1u : 0u;
-    mask = mk;
 }
 
 // One warp's work: x-row `row` of the field `a`, with `wsm` this warp's
@@ -461,15 +352,11 @@ template <int PHASE, int RANK, bool FINAL, bool DEBUG, bool VEC>
 __global__ void __launch_bounds__(256) k_rowpass(RowArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    if (a.route_ctr) {
-        // signed-point route: row pass 1 starts the counters; row pass 2 (the
-        // dense second EDT) runs only when that route handed the field over
-        if (PHASE == 1) {
-            if (blockIdx.x == 0 && threadIdx.x < kCtrWords) a.route_ctr[threadIdx.x] = 0;
-        } else if (*static_cast<volatile int*>(a.route_ctr + kCtrDense) == 0) {
-            return;
-        }
-    }
+    // gated launches (signed-point route): run only when the flag is set
+    if (a.gate && *static_cast<const volatile int*>(a.gate) == 0) return;
+    // row pass 1 of the route starts its counters (not the local-EDT flag)
+    if (PHASE == 1 && a.route_ctr && blockIdx.x == 0 && threadIdx.x < kCtrLocalFail)
+        a.route_ctr[threadIdx.x] = 0;
     const int warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
     // one row per warp, or (a grid smaller than the rows: the dense second EDT
     // behind the signed-point route) a loop over them; only warp-level sync
@@ -508,7 +395,7 @@ cudaError_t go(const RowArgs& a, bool debug, bool vec, dim3 grid, dim3 block, si
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         dim3 g = grid;
-        if (PHASE == 2 && a.route_ctr) {  // gated: a resident grid that loops over the rows
+        if (a.gate) {  // gated: a resident grid that loops over the rows
             int dev = 0, sms = 152, per = 1;
             if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, (int)block.x, smem) != cudaSuccess || per < 1)

@@ -9,15 +9,15 @@
 // kernels then give the exact Dist2 of every query, Eq. 2 over the
 // sign-flipping boundary B2 of Algorithm 3:
 //
-//   k_query    a shell search around the query (one warp each): lattice
-//              offsets in order of squared length, GetBoundary(S) evaluated at
-//              each candidate from S and the equal-q mask; the first hit is
-//              the minimum. A query with no B2 site within the search radius
-//              goes to a second list.
-//   k_b2dilate (only when such queries exist) lists the B2 sites from the
-//              signed points and their axis neighbours;
-//   k_b2list   (idem, when the list of signed points overflowed) lists them
-//              from a pass over the whole field;
+//   k_query    a shell search around the query (one warp each, then one CTA
+//              each for the queries the first offsets leave): lattice offsets
+//              in order of squared length, GetBoundary(S) evaluated at each
+//              candidate from S and the equal-q mask; the first hit is the
+//              minimum. A query with no B2 site within the search radius is
+//              left to the brute-force search.
+//   k_b2sites  (only when such queries exist) lists the B2 sites from the
+//              signed points and their axis neighbours, or, when the list of
+//              signed points overflowed, from a pass over the whole field;
 //   k_brute    (idem) min over the site list for each remaining query.
 //
 // A count over a capacity, or a brute-force product over its budget, sets the
@@ -85,9 +85,41 @@ __device__ __forceinline__ float query_output(const RouteArgs& a, const Query& e
     return compensate(__ldg(a.q + e.idx), e.d1code >> 2, d2, sign_of_code(e.d1code & 3), a.m);
 }
 
-// One warp per query: lane l evaluates offset 32 k + l of the table; the
-// lowest lane with a hit in the first chunk that has one holds the smallest
-// squared distance (the table is sorted by it).
+// Offset k of the table at query (x, y, z): a B2 site? r2 = its squared
+// length (r2 > max_r2, or k past the table: no).
+template <int RANK>
+__device__ __forceinline__ bool probe(const RouteArgs& a, int x, int y, int z, int k, int& r2)
+{
+    const int* tab = RANK == 3 ? c_off.off3 : c_off.off2;
+    constexpr int ntab = RANK == 3 ? kN3 : kN2;
+    const int o = k < ntab ? tab[k] : -1;
+    r2 = (int)((unsigned)o >> 24);
+    if (k >= ntab || r2 > a.max_r2) return false;
+    const int bx = x + (int)(int8_t)(o & 0xFF);
+    const int by = y + (int)(int8_t)((o >> 8) & 0xFF);
+    const int bz = z + (int)(int8_t)((o >> 16) & 0xFF);
+    // B2 lies on interior points only (extents of kept axes are >= 2)
+    const bool inner = (unsigned)(bx - 1) < (unsigned)(a.nx - 2) && (unsigned)(by - 1) < (unsigned)(a.ny - 2) &&
+                       (RANK == 2 || (unsigned)(bz - 1) < (unsigned)(a.nz - 2));
+    return inner && is_b2<RANK>(a, (int64_t)bz * a.ny * a.nx + (int64_t)by * a.nx + bx);
+}
+
+__device__ __forceinline__ void coords(const RouteArgs& a, int idx, int& x, int& y, int& z)
+{
+    const int plane = a.ny * a.nx;
+    z = idx / plane;
+    const int rem = idx - z * plane;
+    y = rem / a.nx;
+    x = rem - y * a.nx;
+}
+
+// The shell search runs in two phases: one warp per query over the first
+// kPhase1 offsets of the table (most queries end there), then one CTA per
+// query left over the rest, four offsets per thread with their loads in
+// flight together. The first hit in table order has the smallest squared
+// distance (the table is sorted by it).
+constexpr int kPhase1 = 160;
+
 template <int RANK>
 __global__ void __launch_bounds__(256) k_query(RouteArgs a)
 {
@@ -99,45 +131,28 @@ __global__ void __launch_bounds__(256) k_query(RouteArgs a)
         return;
     }
     const int lane = threadIdx.x & 31;
-    const int* tab = RANK == 3 ? c_off.off3 : c_off.off2;
-    const int ntab = RANK == 3 ? kN3 : kN2;
-    const int plane = a.ny * a.nx;
     const int wstride = gridDim.x * (blockDim.x >> 5);
     for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < nq; i += wstride) {
         const Query e = a.qlist[i];
-        const int z = e.idx / plane, rem = e.idx - z * plane;
-        const int y = rem / a.nx, x = rem - y * a.nx;
-        // offset k of the table at this query: a B2 site? (r2 > max_r2: no)
-        auto probe = [&](int k, int& r2) -> bool {
-            const int o = k < ntab ? tab[k] : -1;
-            r2 = (int)((unsigned)o >> 24);
-            if (k >= ntab || r2 > a.max_r2) return false;
-            const int bx = x + (int)(int8_t)(o & 0xFF);
-            const int by = y + (int)(int8_t)((o >> 8) & 0xFF);
-            const int bz = z + (int)(int8_t)((o >> 16) & 0xFF);
-            // B2 lies on interior points only (extents of kept axes are >= 2)
-            const bool inner = (unsigned)(bx - 1) < (unsigned)(a.nx - 2) && (unsigned)(by - 1) < (unsigned)(a.ny - 2) &&
-                               (RANK == 2 || (unsigned)(bz - 1) < (unsigned)(a.nz - 2));
-            return inner && is_b2<RANK>(a, (int64_t)bz * plane + (int64_t)by * a.nx + bx);
-        };
+        int x, y, z;
+        coords(a, e.idx, x, y, z);
         int found = -1;
-        // the first 32 offsets (most queries end here), then 128 per step
-        // (four per lane, their loads in flight together)
-        for (int k0 = 0, step = 32; k0 < ntab && (int)((unsigned)tab[k0] >> 24) <= a.max_r2; k0 += step, step = 128) {
+        // the first 32 offsets, then 128 (four per lane)
+        {
+            int r2;
+            const unsigned h = __ballot_sync(kFull, probe<RANK>(a, x, y, z, lane, r2));
+            if (h) found = __shfl_sync(kFull, r2, __ffs(h) - 1);
+        }
+        if (found < 0) {
             int r2[4];
             bool hit[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                hit[u] = false;
-                r2[u] = 0;
-                if (u == 0 || step == 128) hit[u] = probe(k0 + 32 * u + lane, r2[u]);
-            }
+            for (int u = 0; u < 4; ++u) hit[u] = probe<RANK>(a, x, y, z, 32 + 32 * u + lane, r2[u]);
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const unsigned h = __ballot_sync(kFull, hit[u]);
                 if (h && found < 0) found = __shfl_sync(kFull, r2[u], __ffs(h) - 1);
             }
-            if (found >= 0) break;
         }
         if (lane == 0) {
             if (found >= 0) {
@@ -153,6 +168,49 @@ __global__ void __launch_bounds__(256) k_query(RouteArgs a)
     }
 }
 
+// Second phase: one CTA per query the first left, over table offsets
+// kPhase1 .. (4 per thread: 1024 cover the 3-D table). A hit writes the
+// output and marks the query done (fmin = -1); a miss leaves it to the
+// brute-force search.
+template <int RANK>
+__global__ void __launch_bounds__(256) k_query_far(RouteArgs a)
+{
+    volatile int* ctr = a.ctr;
+    if (ctr[kCtrDense]) return;
+    const int nf = ctr[kCtrFailed];
+    if (nf > a.fcap) {  // the list is incomplete: the dense route takes over
+        if (blockIdx.x == 0 && threadIdx.x == 0) ctr[kCtrDense] = 1;
+        return;
+    }
+    __shared__ int sbest[8];
+    for (int f = blockIdx.x; f < nf; f += gridDim.x) {
+        const Query e = a.flist[f];
+        int x, y, z;
+        coords(a, e.idx, x, y, z);
+        int best = 0x7FFFFFFF;  // smallest table index with a hit
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int k = kPhase1 + (int)threadIdx.x + (int)blockDim.x * u;
+            int r2;
+            if (probe<RANK>(a, x, y, z, k, r2)) best = min(best, k);
+        }
+        best = __reduce_min_sync(kFull, best);
+        if ((threadIdx.x & 31) == 0) sbest[threadIdx.x >> 5] = best;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) best = min(best, sbest[w]);
+            if (best != 0x7FFFFFFF) {
+                const int* tab = RANK == 3 ? c_off.off3 : c_off.off2;
+                a.out[e.idx] = query_output(a, e, (int)((unsigned)tab[best] >> 24));
+                a.fmin[f] = -1;
+            } else {
+                atomicAdd(a.ctr + kCtrUnresolved, 1);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 __device__ __forceinline__ uint32_t load4_u8(const void* base, int64_t off, int x0, int nx, bool vec)
 {
     const uint8_t* p = static_cast<const uint8_t*>(base) + off;
@@ -164,8 +222,16 @@ __device__ __forceinline__ uint32_t load4_u8(const void* base, int64_t off, int 
     return w;
 }
 
-// Appends B2 site (x, y, z) to the list (warp-aggregated: one atomic per warp).
-__device__ __forceinline__ void append_sites(const RouteArgs& a, unsigned nib, int x0, int y, int z)
+// B2 sites found by one CTA, flushed to the global list with one atomic.
+constexpr int kSiteBuf = 1024;
+struct SiteBuf {
+    uint2* e;  // [kSiteBuf] in shared memory
+    int* n;    // shared count
+};
+
+// Appends the B2 sites x0 + j (bit j of nib) of row (y, z): into the CTA's
+// buffer (warp-aggregated), or, when it is full, to the global list.
+__device__ __forceinline__ void append_sites(const RouteArgs& a, const SiteBuf& sb, unsigned nib, int x0, int y, int z)
 {
     const int lane = threadIdx.x & 31;
     if (!__ballot_sync(kFull, nib != 0)) return;
@@ -177,14 +243,33 @@ __device__ __forceinline__ void append_sites(const RouteArgs& a, unsigned nib, i
         if (lane >= d) incl += v;
     }
     int base = 0;
-    if (lane == 31) base = atomicAdd(a.ctr + kCtrB2, incl);
+    bool global = false;
+    if (lane == 31) {
+        base = atomicAdd(sb.n, incl);
+        if (base + incl > kSiteBuf) {
+            global = true;
+            base = atomicAdd(a.ctr + kCtrB2, incl);
+        }
+    }
+    global = __shfl_sync(kFull, global, 31);
     base = __shfl_sync(kFull, base, 31) + incl - cnt;
-    uint2* list = reinterpret_cast<uint2*>(a.b2list);
+    uint2* list = global ? reinterpret_cast<uint2*>(a.b2list) : sb.e;
+    const int cap = global ? a.b2cap : kSiteBuf;
     for (int j = 0; j < 4; ++j) {
         if (!((nib >> j) & 1u)) continue;
-        if (base < a.b2cap) list[base] = make_uint2((uint32_t)(x0 + j) | ((uint32_t)y << 16), (uint32_t)z);
+        if (base < cap) list[base] = make_uint2((uint32_t)(x0 + j) | ((uint32_t)y << 16), (uint32_t)z);
         ++base;
     }
+}
+
+__device__ __forceinline__ void flush_sites(const RouteArgs& a, const SiteBuf& sb, int* sbase)
+{
+    __syncthreads();
+    const int n = min(*sb.n, kSiteBuf);
+    if (threadIdx.x == 0) *sbase = n > 0 ? atomicAdd(a.ctr + kCtrB2, n) : 0;
+    __syncthreads();
+    uint2* list = reinterpret_cast<uint2*>(a.b2list);
+    for (int i = threadIdx.x; i < n && *sbase + i < a.b2cap; i += blockDim.x) list[*sbase + i] = sb.e[i];
 }
 
 // The B2 sites, from the signed set: a site has S != 0 or an axis neighbour
@@ -194,10 +279,23 @@ __device__ __forceinline__ void append_sites(const RouteArgs& a, unsigned nib, i
 // signed neighbour of smallest linear index, so no site is listed twice.
 // Runs when some query needs the list and the signed set is complete.
 template <int RANK>
-__global__ void __launch_bounds__(256) k_b2dilate(RouteArgs a)
+__device__ __forceinline__ void b2_from_field(const RouteArgs& a, const SiteBuf& sb, int vec);
+
+template <int RANK>
+__global__ void __launch_bounds__(256) k_b2sites(RouteArgs a, int vec)
 {
     volatile int* ctr = a.ctr;
-    if (ctr[kCtrDense] || ctr[kCtrFailed] == 0 || ctr[kCtrSignedOver] || ctr[kCtrSigned] > a.scap) return;
+    if (ctr[kCtrDense] || ctr[kCtrUnresolved] == 0) return;
+    __shared__ uint2 sbuf[kSiteBuf];
+    __shared__ int sn, sbase;
+    if (threadIdx.x == 0) sn = 0;
+    __syncthreads();
+    const SiteBuf sb{sbuf, &sn};
+    if (ctr[kCtrSignedOver] || ctr[kCtrSigned] > a.scap) {  // the signed set overflowed its list
+        b2_from_field<RANK>(a, sb, vec);
+        flush_sites(a, sb, &sbase);
+        return;
+    }
     const int ns = ctr[kCtrSigned], nq = ctr[kCtrQueries];
     const int plane = a.ny * a.nx;
     constexpr int nb = 2 * RANK;
@@ -235,8 +333,9 @@ __global__ void __launch_bounds__(256) k_b2dilate(RouteArgs a)
             }
             site = own && is_b2<RANK>(a, (int64_t)b) ? 1u : 0u;
         }
-        append_sites(a, site, bx, by, bz);
+        append_sites(a, sb, site, bx, by, bz);
     }
+    flush_sites(a, sb, &sbase);
 }
 
 __device__ __forceinline__ uint32_t load4_s8(const int8_t* p, int x0, int nx, bool vec)
@@ -252,10 +351,8 @@ __device__ __forceinline__ uint32_t load4_s8(const int8_t* p, int x0, int nx, bo
 // Every B2 site of the field, for the case where the signed set overflowed
 // its list. One warp per interior row, 128 points per step (4 per lane).
 template <int RANK>
-__global__ void __launch_bounds__(256) k_b2list(RouteArgs a, int vec)
+__device__ __forceinline__ void b2_from_field(const RouteArgs& a, const SiteBuf& sb, int vec)
 {
-    volatile int* ctr = a.ctr;
-    if (ctr[kCtrDense] || ctr[kCtrFailed] == 0 || !(ctr[kCtrSignedOver] || ctr[kCtrSigned] > a.scap)) return;
     const int lane = threadIdx.x & 31;
     const int rows = a.nz * a.ny;
     const int plane = a.ny * a.nx;
@@ -292,7 +389,7 @@ __global__ void __launch_bounds__(256) k_b2list(RouteArgs a, int vec)
 #pragma unroll
             for (int j = 0; j < 4; ++j)  // interior along x; bytes past the row end are not points
                 if (x0 + j < 1 || x0 + j > a.nx - 2) nib &= ~(1u << j);
-            append_sites(a, nib, x0, y, z);
+            append_sites(a, sb, nib, x0, y, z);
         }
     }
 }
@@ -305,9 +402,8 @@ constexpr int kBruteChunk = 1024;
 __global__ void __launch_bounds__(256) k_brute(RouteArgs a)
 {
     volatile int* ctr = a.ctr;
-    if (ctr[kCtrDense]) return;
+    if (ctr[kCtrDense] || ctr[kCtrUnresolved] == 0) return;
     const int nf = ctr[kCtrFailed];
-    if (nf == 0) return;
     const int nb = ctr[kCtrB2];
     const int qblocks = (nf + blockDim.x - 1) / blockDim.x;
     if (nf > a.fcap || nb > a.b2cap || (long long)nf * nb > a.brute_budget || qblocks > (int)gridDim.x) {
@@ -345,7 +441,7 @@ __global__ void __launch_bounds__(256) k_brute(RouteArgs a)
                 best = min(best, dz * dz + dy * dy + dx * dx);
             }
         }
-        if (f < nf && best < kDistInf) atomicMin(a.fmin + f, best);
+        if (f < nf && best < kDistInf) atomicMin(a.fmin + f, best);  // -1 (done) stays
     }
     // the last CTA writes every output (no B2 at all: Dist2 = INF, w = 1)
     __threadfence();
@@ -355,8 +451,10 @@ __global__ void __launch_bounds__(256) k_brute(RouteArgs a)
     if (last) {
         __threadfence();
         for (int f = threadIdx.x; f < nf; f += blockDim.x) {
+            const int32_t d2 = *static_cast<volatile int32_t*>(a.fmin + f);
+            if (d2 < 0) continue;  // the second shell search found it
             const Query e = a.flist[f];
-            a.out[e.idx] = query_output(a, e, *static_cast<volatile int32_t*>(a.fmin + f));
+            a.out[e.idx] = query_output(a, e, d2);
         }
     }
 }
@@ -372,19 +470,19 @@ cudaError_t launch_route_query(const RouteArgs& a, int blocks, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_route_b2dilate(const RouteArgs& a, int blocks, cudaStream_t st)
+cudaError_t launch_route_query_far(const RouteArgs& a, int blocks, cudaStream_t st)
 {
-    if (a.rank == 3) k_b2dilate<3><<<blocks, 256, 0, st>>>(a);
-    else k_b2dilate<2><<<blocks, 256, 0, st>>>(a);
+    if (a.rank == 3) k_query_far<3><<<blocks, 256, 0, st>>>(a);
+    else k_query_far<2><<<blocks, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_route_b2list(const RouteArgs& a, int blocks, cudaStream_t st)
+cudaError_t launch_route_b2sites(const RouteArgs& a, int blocks, cudaStream_t st)
 {
     auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 3) == 0; };
     const int vec = (a.nx % 4 == 0) && al(a.s) && al(a.eqm);
-    if (a.rank == 3) k_b2list<3><<<blocks, 256, 0, st>>>(a, vec);
-    else k_b2list<2><<<blocks, 256, 0, st>>>(a, vec);
+    if (a.rank == 3) k_b2sites<3><<<blocks, 256, 0, st>>>(a, vec);
+    else k_b2sites<2><<<blocks, 256, 0, st>>>(a, vec);
     return cudaGetLastError();
 }
 

@@ -85,6 +85,7 @@ SIGNATURES = {
                                             ctypes.c_size_t, P, ctypes.POINTER(BatchChoice)]),
     "qai_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "qai_profile_read": (ctypes.c_int, [ctypes.POINTER(KernelStat), ctypes.c_int]),
+    "qai_profile_select": (ctypes.c_int, [ctypes.c_char_p]),
     "qai_workspace_size_quality": (ctypes.c_int, [ctypes.c_int, P, ctypes.c_int, ctypes.c_int,
                                                   ctypes.POINTER(ctypes.c_size_t)]),
     "qai_quality": (ctypes.c_int, [P, P, ctypes.c_int, P, ctypes.c_int, ctypes.c_int, P, P, P,
@@ -207,15 +208,17 @@ def mitigate(q: torch.Tensor, eb: float, eta: float = 0.9, idw_power: float = 1.
 
 def route_counts(workspace: torch.Tensor, shape, stream=None) -> dict:
     """How the last plain :func:`mitigate` on ``workspace`` (rank 2 or 3)
-    computed the second EDT: ``queries`` (points with S != 0 off B1, where
+    computed the EDTs: ``queries`` (points with S != 0 off B1, where
     Dist2 matters), ``list_searched`` (those the shell search left to the
     search over all B2 sites), ``b2_sites`` (sites listed for it), ``dense``
-    (the dense second EDT ran) and ``signed_b1`` (B1 points with S != 0, -1
-    when too many to list). Synchronises the stream."""
-    c = (ctypes.c_int32 * 5)()
+    (the dense second EDT ran), ``signed_b1`` (B1 points with S != 0, -1
+    when too many to list) and ``separable_first_edt`` (the bounded search of
+    the first EDT fell short and the separable passes ran). Synchronises the
+    stream."""
+    c = (ctypes.c_int32 * 6)()
     _check(load().qai_route_counts(workspace.data_ptr(), len(shape), _dims(shape), c, _stream(stream)))
     return {"queries": c[0], "list_searched": c[1], "b2_sites": c[2], "dense": bool(c[3]),
-            "signed_b1": c[4]}
+            "signed_b1": c[4], "separable_first_edt": bool(c[5])}
 
 
 def mitigate_host(q_host: torch.Tensor, eb: float, out_host: torch.Tensor | None = None,
@@ -469,6 +472,11 @@ def mitigate_static(q: torch.Tensor, eb: float, out: torch.Tensor | None = None,
 
 def profile_enable(on: bool = True):
     _check(load().qai_profile_enable(1 if on else 0))
+
+
+def profile_select(name: str | None = None):
+    """Time only the kernels called ``name`` (None: all of them)."""
+    _check(load().qai_profile_select(name.encode() if name else None))
 
 
 def profile_read():

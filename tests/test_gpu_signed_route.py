@@ -24,8 +24,9 @@ pytestmark = pytest.mark.gpu
 ROUTES = ["auto", "brute", "dense", "off"]
 
 
-def _plain_and_debug(q, eb, route, monkeypatch, **kw):
+def _plain_and_debug(q, eb, route, monkeypatch, first_edt="local", **kw):
     monkeypatch.setenv("QAI_SIGNED_ROUTE", route)
+    monkeypatch.setenv("QAI_FIRST_EDT", first_edt)
     ws = qai.alloc_workspace(qai.workspace_size(tuple(q.shape)))
     plain = qai.mitigate(q, eb, workspace=ws, **kw)
     counts = qai.route_counts(ws, tuple(q.shape)) if route != "off" and _rank(q) >= 2 else None
@@ -44,19 +45,22 @@ def _field(name, shape, seed):
     return synth.grf_front(shape, seed=seed, device="cuda")
 
 
+@pytest.mark.parametrize("first_edt", ["local", "separable"])
 @pytest.mark.parametrize("route", ROUTES)
 @pytest.mark.parametrize("name,shape,rel_eb", [("grf", (96, 128, 160), 1e-3), ("grf", (96, 128, 160), 1e-2),
                                                ("front", (64, 200, 72), 1e-3), ("front", (300, 500), 1e-3),
                                                ("grf", (700, 900), 1e-2), ("front", (40, 1, 64), 3e-3)],
                          ids=str)
-def test_routes_match_the_dense_evaluation(route, name, shape, rel_eb, monkeypatch):
+def test_routes_match_the_dense_evaluation(route, first_edt, name, shape, rel_eb, monkeypatch):
     x = _field(name, tuple(n for n in shape if n > 1), 31).reshape(shape)
     eb = rel_eb * synth.value_range(x)
     q = synth.quantize(x, eb).contiguous()
-    plain, full, maps, counts = _plain_and_debug(q, eb, route, monkeypatch)
+    plain, full, maps, counts = _plain_and_debug(q, eb, route, monkeypatch, first_edt)
     assert torch.equal(plain, full), f"{route}: {(plain != full).sum().item()} points differ"
-    plain_c, full_c, _, _ = _plain_and_debug(q, eb, route, monkeypatch, output_c=True)
+    plain_c, full_c, _, _ = _plain_and_debug(q, eb, route, monkeypatch, first_edt, output_c=True)
     assert torch.equal(plain_c, full_c)
+    if counts is not None and first_edt == "separable":
+        assert not counts["separable_first_edt"]
     if counts is not None:
         want = int(((maps["s"] != 0) & (maps["dist1"] > 0)).sum().item())
         if route == "dense":
@@ -94,6 +98,23 @@ def test_routes_under_rule_variants(kw, route, monkeypatch):
     assert torch.equal(plain, full)
 
 
+@pytest.mark.parametrize("shape", [(5, 7), (17, 33), (3, 4, 5), (2, 2, 2), (7, 9, 33), (33, 17, 65), (4, 4, 4096),
+                                   (2, 3, 16383), (4096, 2, 3), (37, 1025)], ids=str)
+@pytest.mark.parametrize("kind", ["noisy", "extreme", "checker"])
+def test_local_first_edt_on_index_fields(shape, kind, monkeypatch):
+    """Dense B1 (noise, |q| near 2^31, a checkerboard): the bounded search
+    decides every point; edges, odd extents and the 64-bit stencil path."""
+    rng = np.random.default_rng(zlib.crc32(repr((shape, kind, "local")).encode()))
+    qn = oc.random_index_field(rng, shape, kind)
+    q = torch.from_numpy(qn).cuda()
+    plain, full, _, counts = _plain_and_debug(q, 0.01, "auto", monkeypatch)
+    assert torch.equal(plain, full)
+    ref = oracle.mitigate(qn, 0.01)["out"]
+    rng_q = 2.0 * 0.01 * max(1, int(qn.max()) - int(qn.min()))
+    tol = 1e-6 * rng_q + 4.0 * np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64)
+    assert np.all(np.abs(plain.cpu().numpy().astype(np.float64) - ref) <= tol)
+
+
 def test_step_field_without_b2_takes_the_list_search_with_no_sites(monkeypatch):
     """One quantization step across x: every point off the two boundary planes
     is a query, and B2 is empty (each q region has a single sign), so Dist2 is
@@ -103,6 +124,7 @@ def test_step_field_without_b2_takes_the_list_search_with_no_sites(monkeypatch):
     q = torch.from_numpy(qn).cuda()
     plain, full, maps, counts = _plain_and_debug(q, 0.05, "auto", monkeypatch)
     assert torch.equal(plain, full)
+    assert counts["separable_first_edt"]          # x = 0 is 4 cells from B1: beyond the bounded search
     assert not counts["dense"] and counts["b2_sites"] == 0
     assert counts["queries"] == counts["list_searched"] > 0
     assert int((maps["b2"] != 0).sum().item()) == 0
@@ -152,7 +174,7 @@ def test_grf_512_eb_1e3_stays_on_the_signed_route(monkeypatch):
     ws = qai.alloc_workspace(qai.workspace_size(tuple(q.shape)))
     plain = qai.mitigate(q, eb, workspace=ws)
     counts = qai.route_counts(ws, tuple(q.shape))
-    assert not counts["dense"] and counts["queries"] > 0
+    assert not counts["dense"] and counts["queries"] > 0 and not counts["separable_first_edt"]
     monkeypatch.setenv("QAI_SIGNED_ROUTE", "off")
     dense = qai.mitigate(q, eb, workspace=ws)
     torch.cuda.synchronize()
