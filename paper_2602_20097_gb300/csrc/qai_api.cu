@@ -160,6 +160,7 @@ Layout layout_for(const Shape& s, uint32_t flags)
         l.ctr = take(qai::kCtrWords * 4);
         l.qlist = take((size_t)l.qcap * sizeof(qai::Query));
         l.slist = take((size_t)l.scap * 4);
+        l.mlist = take((size_t)l.qcap * sizeof(qai::Query));
         l.flist = take((size_t)l.fcap * sizeof(qai::Query));
         l.fmin = take((size_t)l.fcap * 4);
         l.b2list = take((size_t)l.b2cap * 8);
@@ -293,9 +294,9 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
         la.m = m;
         auto al = [](const void* p, int b) { return (reinterpret_cast<uintptr_t>(p) % b) == 0; };
         la.vec = (sh.nx % 4 == 0) && al(d_q, 16) && al(d_out, 16) && al(eqm, 4);
-        e = timed("detect", N * 9.0, st, [&] { return qai::launch_local_detect(la, 8 * sms, st); });
+        e = timed("detect", N * 9.0, st, [&] { return qai::launch_local_detect(la, st); });
         if (e != cudaSuccess) return cuda_fail(e, "step A");
-        e = timed("near", N * 2.0, st, [&] { return qai::launch_local_near(la, 8 * sms, st); });
+        e = timed("near", N * 2.0, st, [&] { return qai::launch_local_near(la, st); });
         if (e != cudaSuccess) return cuda_fail(e, "nearest-site search");
     }
 
@@ -376,6 +377,7 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
         ra.q = d_q; ra.eqm = eqm; ra.s = s; ra.out = d_out; ra.ctr = ctr;
         ra.qlist = qlist; ra.qcap = lay.qcap;
         ra.slist = reinterpret_cast<const int32_t*>(ws + lay.slist); ra.scap = lay.scap;
+        ra.mlist = reinterpret_cast<qai::Query*>(ws + lay.mlist);
         ra.flist = reinterpret_cast<qai::Query*>(ws + lay.flist); ra.fcap = lay.fcap;
         ra.fmin = reinterpret_cast<int32_t*>(ws + lay.fmin);
         ra.b2list = reinterpret_cast<int32_t*>(ws + lay.b2list); ra.b2cap = lay.b2cap;
@@ -385,8 +387,10 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
         if (route == Route::Dense) ra.qcap = -1;  // every count is over it: hand over at once
         e = timed("signed_query", 0.0, st, [&] { return qai::launch_route_query(ra, 4 * sms, st); });
         if (e != cudaSuccess) return cuda_fail(e, "signed-point shell search");
-        e = timed("signed_query_far", 0.0, st, [&] { return qai::launch_route_query_far(ra, 4 * sms, st); });
+        e = timed("signed_query_mid", 0.0, st, [&] { return qai::launch_route_query_mid(ra, 4 * sms, st); });
         if (e != cudaSuccess) return cuda_fail(e, "signed-point shell search, second phase");
+        e = timed("signed_query_far", 0.0, st, [&] { return qai::launch_route_query_far(ra, 4 * sms, st); });
+        if (e != cudaSuccess) return cuda_fail(e, "signed-point shell search, third phase");
         e = timed("signed_b2sites", 0.0, st, [&] { return qai::launch_route_b2sites(ra, 8 * sms, st); });
         if (e != cudaSuccess) return cuda_fail(e, "B2 site list");
         e = timed("signed_brute", 0.0, st, [&] { return qai::launch_route_brute(ra, 2 * sms, st); });
@@ -408,8 +412,12 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
     // EDT2 along y (and z), the last pass fused with step E.
     auto fuse_e = [&](qai::ColArgs& c) {
         c.out = d_out; c.q = d_q; c.dist1_in = dist1; c.s_in = s; c.dbg_dist2 = d.dist2;
-        // the per-column counts exist only when the separable first EDT ran
+        // the per-column counts exist only when the separable first EDT ran;
+        // after the local one, B1 comes from the mask byte (Dist1 = 0 there
+        // is not stored) -- the separable passes, when they ran, rewrote the
+        // mask bytes on B1 without clearing any other bit pattern's meaning
         c.col_count_in = local ? nullptr : cflag;
+        c.b1_eqm = local ? eqm : nullptr;
         c.route_ctr = ctr;
         c.gate = ctr ? ctr + qai::kCtrDense : nullptr;
     };

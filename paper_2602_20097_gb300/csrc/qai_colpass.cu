@@ -85,6 +85,15 @@ __device__ __forceinline__ void cp_async(void* dst, const void* src, int bytes)
 // Writes the result of one point: `val` is its squared distance, `w` the
 // input word of the winning row (phase 1: carries the sign code), `src` the
 // element index of that row in the same column (phase 1 index carry).
+// Dist1 of point idx for step E (0 on B1 when the local first EDT left it
+// unstored there).
+__device__ __forceinline__ int32_t dist1_at(const ColArgs& a, int64_t idx)
+{
+    const int32_t d = __ldg(a.dist1_in + idx);
+    if (!a.b1_eqm) return d;
+    return (__ldg(a.b1_eqm + idx) & 0x3Fu) != 0x3Fu ? 0 : d;
+}
+
 // Points of the signed-point route collected by one CTA of the last pass of
 // the first EDT before they go to the global lists: the queries (S != 0 off
 // B1) and the B1 points with S != 0.
@@ -145,7 +154,7 @@ __device__ __forceinline__ void emit_point(const ColArgs& a, int idx, int src, i
             const int sv = __ldg(a.s_in + idx);
             // signed-point route: row pass 1 wrote every point with S = 0
             if (!a.route_ctr || sv != 0)
-                a.out[idx] = compensate(__ldg(a.q + idx), __ldg(a.dist1_in + idx), d, sv, a.m);
+                a.out[idx] = compensate(__ldg(a.q + idx), dist1_at(a, idx), d, sv, a.m);
             if (DEBUG && a.dbg_dist2) a.dbg_dist2[idx] = d;
         }
     }
@@ -552,7 +561,7 @@ __device__ __forceinline__ void colpass_tile(const ColArgs& a, const int blk)
     if (kFuseE) {
         if (GRAD) pg = __ldg(a.grad_out + idx);
         else pq = __ldg(a.q + idx);
-        pd1 = __ldg(a.dist1_in + idx);
+        pd1 = dist1_at(a, idx);
         ps = __ldg(a.s_in + idx);
     }
     for (int r = r0; r < r1; ++r) {
@@ -561,7 +570,7 @@ __device__ __forceinline__ void colpass_tile(const ColArgs& a, const int blk)
         if (kFuseE && r + 1 < r1) {
             if (GRAD) ng = __ldg(a.grad_out + idx + RS);
             else nq = __ldg(a.q + idx + RS);
-            nd1 = __ldg(a.dist1_in + idx + RS);
+            nd1 = dist1_at(a, idx + RS);
             nsg = __ldg(a.s_in + idx + RS);
         }
         while (pos_n >= 0 && g + (h - r) * (h - r) > gn + (hn - r) * (hn - r)) {

@@ -55,6 +55,7 @@ enum RouteCtr : int {
     kCtrSignedOver = 5,// != 0: a tile had more of them than it could buffer
     kCtrBruteDone = 6, // CTAs of the brute-force search that finished
     kCtrUnresolved = 7,// queries left to the brute-force search by both shell searches
+    kCtrMid = 8,       // queries the first (per-thread) shell search left
     kCtrLocalFail = 15,// != 0: the local first EDT left a point without its site;
                        // the separable first EDT runs (and zeroes the words before)
     kCtrWords = 16
@@ -129,6 +130,10 @@ struct ColArgs {
     // *gate != 0 (then on a resident grid that loops over the tiles).
     int* route_ctr;
     const int* gate;
+    // Phase 2 final after the local first EDT: Dist1 is not stored on B1;
+    // a point is on B1 where its equal-q mask byte has a clear bit, and its
+    // Dist1 is 0 there.
+    const uint8_t* b1_eqm;
     Query* qlist;
     int qcap;
     int32_t* slist;          // B1 points with S != 0 (linear indices), at most scap
@@ -148,6 +153,7 @@ struct RouteArgs {
     int qcap;
     const int32_t* slist;    // B1 points with S != 0
     int scap;
+    Query* mlist;            // queries left by the first shell search (qcap entries)
     Query* flist;            // queries left to the brute-force search
     int32_t* fmin;           // their Dist2, min-reduced by the brute-force CTAs
     int fcap;

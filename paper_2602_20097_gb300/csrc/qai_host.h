@@ -23,7 +23,7 @@ struct Layout {
     size_t eqm, xw, yw, dist1, s, idx, cflag;
     // signed-point route (rank 2 and 3): counters, queries, queries left to
     // the brute-force search, B2 sites; capacities in entries
-    size_t ctr, qlist, slist, flist, fmin, b2list;
+    size_t ctr, qlist, slist, mlist, flist, fmin, b2list;
     int qcap, scap, fcap, b2cap;
     size_t total;
 };

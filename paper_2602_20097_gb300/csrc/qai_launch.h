@@ -46,14 +46,15 @@ cudaError_t launch_colpass(int phase, int in_bytes, bool final_pass, ColArgs& a,
 // reads the route counters and does nothing when it is not needed.
 int route_table_r2();
 cudaError_t launch_route_query(const RouteArgs& a, int blocks, cudaStream_t st);
+cudaError_t launch_route_query_mid(const RouteArgs& a, int blocks, cudaStream_t st);
 cudaError_t launch_route_query_far(const RouteArgs& a, int blocks, cudaStream_t st);
 cudaError_t launch_route_b2sites(const RouteArgs& a, int blocks, cudaStream_t st);
 cudaError_t launch_route_brute(const RouteArgs& a, int blocks, cudaStream_t st);
 
 // The local first EDT (qai_local.cu): step A with the pre-written output,
 // then S, Dist1 and the signed-point lists by a bounded nearest-site search.
-cudaError_t launch_local_detect(const LocalArgs& a, int blocks, cudaStream_t st);
-cudaError_t launch_local_near(const LocalArgs& a, int blocks, cudaStream_t st);
+cudaError_t launch_local_detect(const LocalArgs& a, cudaStream_t st);
+cudaError_t launch_local_near(const LocalArgs& a, cudaStream_t st);
 
 // Adjoint reduction of step E (qai_backward.cu).
 cudaError_t launch_backward(const BackArgs& a, cudaStream_t st);

@@ -13,7 +13,8 @@
 //             and some neighbour differs; points off the interior get the
 //             all-equal mask), the output wherever Dist2 does not matter
 //             (D' + S_B eta eps on B1, D' elsewhere), and the list of B1
-//             points with S != 0.
+//             points with S != 0. Dist1 = 0 on B1 is not stored: readers take
+//             B1 from the mask byte.
 //   k_near    every point off B1 scans the lattice offsets of squared length
 //             <= 8 in order of (squared length, dz, dy, dx) -- for points
 //             inside the field that is the order of (distance, linear index)
@@ -63,9 +64,21 @@ constexpr NearTable make_near()
 }
 __constant__ NearTable c_near = make_near();
 
+// Minimum resident CTAs per SM the kernels are compiled for (register cap).
+#ifndef QAI_DETECT_MINB
+#define QAI_DETECT_MINB 5
+#endif
+#ifndef QAI_NEAR_MINB
+#define QAI_NEAR_MINB 5
+#endif
+// Grid of the step-A kernel in resident waves.
+#ifndef QAI_DETECT_WAVES
+#define QAI_DETECT_WAVES 2
+#endif
+
 // Per-CTA collection of list entries before one global atomic per CTA.
 constexpr int kSignedCta = 1024;
-constexpr int kQueryCta = 512;
+constexpr int kQueryCta = 2048;
 
 // Step A on one warp-segment of 128 points (4 per lane) of row `row`.
 template <int RANK, bool VEC>
@@ -197,12 +210,12 @@ __device__ __forceinline__ void detect_segment(const LocalArgs& a, int row, int 
                 a.out[rbase + x0 + j] = o[j];
             }
     }
-    // B1 points with S != 0: Dist1 = 0 there, and the signed set lists them
-    if (codes) {
+    // B1 points with S != 0: the signed set lists them (Dist1 = 0 there is
+    // not stored; the mask byte tells B1), until the CTA's buffer is full
+    if (codes && *static_cast<volatile int*>(sn) <= kSignedCta) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             if (((codes >> (2 * j)) & 3u) == 0u) continue;
-            a.dist1[rbase + x0 + j] = 0;
             const int k = atomicAdd(sn, 1);
             if (k < kSignedCta) sbuf[k] = rbase + x0 + j;
         }
@@ -210,7 +223,7 @@ __device__ __forceinline__ void detect_segment(const LocalArgs& a, int row, int 
 }
 
 template <int RANK, bool VEC>
-__global__ void __launch_bounds__(256) k_detect(LocalArgs a)
+__global__ void __launch_bounds__(256, QAI_DETECT_MINB) k_detect(LocalArgs a)
 {
     __shared__ int32_t sbuf[kSignedCta];
     __shared__ int sn, sbase;
@@ -289,11 +302,15 @@ __device__ __forceinline__ uint32_t load4_em(const uint8_t* row, int x0, int nx,
 
 // Byte k = 0xFF where byte k of the mask word marks a B1 point (some of its
 // six equal-q bits clear): t = the clear bits, at most 0x3F per byte, so
-// t + 0x3F sets bit 6 of a byte exactly when t is not zero, with no carry.
+// t + 0x7F sets bit 7 of a byte exactly when t is not zero, with no carry;
+// the byte permute with selector nibbles 8..B copies each byte's bit 7 over
+// the byte.
 __device__ __forceinline__ uint32_t site_bytes(uint32_t w)
 {
-    const uint32_t t = ~w & 0x3F3F3F3Fu;
-    return (((t + 0x3F3F3F3Fu) & 0x40404040u) >> 6) * 0xFFu;
+    const uint32_t t = (~w & 0x3F3F3F3Fu) + 0x7F7F7F7Fu;
+    uint32_t r;
+    asm("prmt.b32 %0, %1, 0, 0xBA98;" : "=r"(r) : "r"(t));  // sign-replicating byte permute
+    return r;
 }
 
 // S at every point, Dist1 where S != 0 off B1, and the queries. One warp per
@@ -303,7 +320,7 @@ __device__ __forceinline__ uint32_t site_bytes(uint32_t w)
 // z-, y-, x-, x+, y+, z+ (increasing linear index); the rare point with none
 // of them on B1 scans the rest of the table alone.
 template <int RANK, int WPL>
-__global__ void __launch_bounds__(256) k_near(LocalArgs a)
+__global__ void __launch_bounds__(256, QAI_NEAR_MINB) k_near(LocalArgs a)
 {
     constexpr int PPL = 4 * WPL;   // points per lane and step
     constexpr int STEP = 32 * PPL; // points per warp and step
@@ -345,27 +362,35 @@ __global__ void __launch_bounds__(256) k_near(LocalArgs a)
             if (lane == 0) prev = carry;
             if (lane == 31) next = x0 + PPL < a.nx ? (uint32_t)__ldg(er + x0 + PPL) : 0x3Fu;
             carry = last;
+            // site masks of the row's words (and of the words either side);
+            // those of the x - 1 and x + 1 neighbours are byte shifts of them
+            const uint32_t mprev = site_bytes(prev), mnext = site_bytes(next);
+            uint32_t mown[4];
+#pragma unroll
+            for (int k = 0; k < WPL; ++k) mown[k] = site_bytes(word(c, k));
             uint32_t sw[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
             for (int k = 0; k < WPL; ++k) {
                 const int xk = x0 + 4 * k;
                 const uint32_t cw = word(c, k);
-                const uint32_t xlw = __byte_perm(k == 0 ? prev : word(c, k - 1), cw, 0x6543);  // byte j: x - 1
-                const uint32_t xrw = __byte_perm(cw, k == WPL - 1 ? next : word(c, k + 1), 0x4321);
+                const uint32_t pw = k == 0 ? prev : word(c, k - 1), nw = k == WPL - 1 ? next : word(c, k + 1);
+                const uint32_t pm = k == 0 ? mprev : mown[k > 0 ? k - 1 : 0];
+                const uint32_t nm = k == WPL - 1 ? mnext : mown[k + 1 < WPL ? k + 1 : 0];
+                const uint32_t xlw = __byte_perm(pw, cw, 0x6543), xlm = __byte_perm(pm, mown[k], 0x6543);  // x - 1
+                const uint32_t xrw = __byte_perm(cw, nw, 0x4321), xrm = __byte_perm(mown[k], nm, 0x4321);  // x + 1
                 // the first B1 neighbour in tie order: select from the last to the first
-                const uint32_t own = site_bytes(cw);
+                const uint32_t own = mown[k];
                 uint32_t found = 0, pick = 0x3F3F3F3Fu;
-                auto take = [&](uint32_t w) {
-                    const uint32_t m = site_bytes(w);
+                auto take = [&](uint32_t w, uint32_t m) {
                     pick = (w & m) | (pick & ~m);
                     found |= m;
                 };
-                take(word(zr, k));
-                take(word(yr, k));
-                take(xrw);
-                take(xlw);
-                take(word(yl, k));
-                take(word(zl, k));
+                take(word(zr, k), site_bytes(word(zr, k)));
+                take(word(yr, k), site_bytes(word(yr, k)));
+                take(xrw, xrm);
+                take(xlw, xlm);
+                take(word(yl, k), site_bytes(word(yl, k)));
+                take(word(zl, k), site_bytes(word(zl, k)));
                 // codes: own on B1, else the neighbour's; Dist1 = 1 where resolved
                 // off B1 (bytes past the row end, and x - 1 of x = 0, read 0x3F)
                 const int nvalid = min(4, a.nx - xk);
@@ -433,30 +458,38 @@ __global__ void __launch_bounds__(256) k_near(LocalArgs a)
 
 }  // namespace
 
-cudaError_t launch_local_detect(const LocalArgs& a, int blocks, cudaStream_t st)
+namespace {
+// A grid-stride kernel's grid: every CTA resident at once (one wave).
+template <class K>
+int one_wave(K kern, int waves = 1)
 {
-    if (a.rank == 3) {
-        if (a.vec) k_detect<3, true><<<blocks, 256, 0, st>>>(a);
-        else k_detect<3, false><<<blocks, 256, 0, st>>>(a);
-    } else {
-        if (a.vec) k_detect<2, true><<<blocks, 256, 0, st>>>(a);
-        else k_detect<2, false><<<blocks, 256, 0, st>>>(a);
-    }
-    return cudaGetLastError();
+    int dev = 0, sms = 152, per = 1;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, 0) != cudaSuccess || per < 1) per = 1;
+    return sms * per * waves;
+}
+}  // namespace
+
+cudaError_t launch_local_detect(const LocalArgs& a, cudaStream_t st)
+{
+    auto run = [&](auto kern) {
+        kern<<<one_wave(kern, QAI_DETECT_WAVES), 256, 0, st>>>(a);
+        return cudaGetLastError();
+    };
+    if (a.rank == 3) return a.vec ? run(k_detect<3, true>) : run(k_detect<3, false>);
+    return a.vec ? run(k_detect<2, true>) : run(k_detect<2, false>);
 }
 
-cudaError_t launch_local_near(const LocalArgs& a, int blocks, cudaStream_t st)
+cudaError_t launch_local_near(const LocalArgs& a, cudaStream_t st)
 {
     auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
     const bool wide = (a.nx % 16 == 0) && al(a.eqm) && al(a.s);  // 16-byte rows
-    if (a.rank == 3) {
-        if (wide) k_near<3, 4><<<blocks, 256, 0, st>>>(a);
-        else k_near<3, 1><<<blocks, 256, 0, st>>>(a);
-    } else {
-        if (wide) k_near<2, 4><<<blocks, 256, 0, st>>>(a);
-        else k_near<2, 1><<<blocks, 256, 0, st>>>(a);
-    }
-    return cudaGetLastError();
+    auto run = [&](auto kern) {
+        kern<<<one_wave(kern), 256, 0, st>>>(a);
+        return cudaGetLastError();
+    };
+    if (a.rank == 3) return wide ? run(k_near<3, 4>) : run(k_near<3, 1>);
+    return wide ? run(k_near<2, 4>) : run(k_near<2, 1>);
 }
 
 }  // namespace qai

@@ -155,6 +155,11 @@ __device__ __forceinline__ void rowpass_row(const RowArgs& a, const int row, uns
                         codes |= (unsigned)code << (2 * j);
                     }
                 }
+                // off the interior along x nothing is on B1: the all-equal
+                // mask there (readers take B1 from a clear bit)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (x0 + j == 0 || x0 + j == nx - 1) eq = (eq & ~(0xFFu << (8 * j))) | (0x3Fu << (8 * j));
                 if (VEC) {
                     if (x0 < nx) *reinterpret_cast<uint32_t*>(a.eqm + rbase + x0) = eq;
                 } else {

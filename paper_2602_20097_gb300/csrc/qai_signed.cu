@@ -9,12 +9,13 @@
 // kernels then give the exact Dist2 of every query, Eq. 2 over the
 // sign-flipping boundary B2 of Algorithm 3:
 //
-//   k_query    a shell search around the query (one warp each, then one CTA
-//              each for the queries the first offsets leave): lattice offsets
-//              in order of squared length, GetBoundary(S) evaluated at each
-//              candidate from S and the equal-q mask; the first hit is the
-//              minimum. A query with no B2 site within the search radius is
-//              left to the brute-force search.
+//   k_query    a shell search around the query (one thread each, then one
+//              warp, then one CTA each for the queries the phase before
+//              left): lattice offsets in order of squared length,
+//              GetBoundary(S) evaluated at each candidate from S and the
+//              equal-q mask; the first hit is the minimum. A query with no B2
+//              site within the search radius is left to the brute-force
+//              search.
 //   k_b2sites  (only when such queries exist) lists the B2 sites from the
 //              signed points and their axis neighbours, or, when the list of
 //              signed points overflowed, from a pass over the whole field;
@@ -113,12 +114,13 @@ __device__ __forceinline__ void coords(const RouteArgs& a, int idx, int& x, int&
     x = rem - y * a.nx;
 }
 
-// The shell search runs in two phases: one warp per query over the first
-// kPhase1 offsets of the table (most queries end there), then one CTA per
-// query left over the rest, four offsets per thread with their loads in
-// flight together. The first hit in table order has the smallest squared
-// distance (the table is sorted by it).
+// The shell search runs in three phases, each on the queries the one before
+// left: one thread per query over the offsets of squared length 0 and 1
+// (most queries end there), one warp per query over the offsets up to
+// kPhase1, one CTA per query over the rest of the table. The first hit in
+// table order has the smallest squared distance (the table is sorted by it).
 constexpr int kPhase1 = 160;
+constexpr int kMidBuf = 2048;  // per-CTA buffer of the first phase's leftovers
 
 template <int RANK>
 __global__ void __launch_bounds__(256) k_query(RouteArgs a)
@@ -130,29 +132,69 @@ __global__ void __launch_bounds__(256) k_query(RouteArgs a)
         if (blockIdx.x == 0 && threadIdx.x == 0) ctr[kCtrDense] = 1;
         return;
     }
-    const int lane = threadIdx.x & 31;
-    const int wstride = gridDim.x * (blockDim.x >> 5);
-    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < nq; i += wstride) {
+    constexpr int n0 = RANK == 3 ? 7 : 5;  // offsets of squared length 0 and 1
+    __shared__ Query mbuf[kMidBuf];
+    __shared__ int mn, mbase;
+    if (threadIdx.x == 0) mn = 0;
+    __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += gridDim.x * blockDim.x) {
         const Query e = a.qlist[i];
         int x, y, z;
         coords(a, e.idx, x, y, z);
+        bool hit[n0];
+        int r2[n0];
+#pragma unroll
+        for (int k = 0; k < n0; ++k) hit[k] = probe<RANK>(a, x, y, z, k, r2[k]);
         int found = -1;
-        // the first 32 offsets, then 128 (four per lane)
-        {
-            int r2;
-            const unsigned h = __ballot_sync(kFull, probe<RANK>(a, x, y, z, lane, r2));
-            if (h) found = __shfl_sync(kFull, r2, __ffs(h) - 1);
-        }
-        if (found < 0) {
-            int r2[4];
-            bool hit[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) hit[u] = probe<RANK>(a, x, y, z, 32 + 32 * u + lane, r2[u]);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const unsigned h = __ballot_sync(kFull, hit[u]);
-                if (h && found < 0) found = __shfl_sync(kFull, r2[u], __ffs(h) - 1);
+        for (int k = n0 - 1; k >= 0; --k)
+            if (hit[k]) found = r2[k];
+        if (found >= 0) {
+            a.out[e.idx] = query_output(a, e, found);
+        } else {
+            const int k = atomicAdd(&mn, 1);
+            if (k < kMidBuf) {
+                mbuf[k] = e;
+            } else {
+                const int g = atomicAdd(a.ctr + kCtrMid, 1);
+                if (g < a.qcap) a.mlist[g] = e;
             }
+        }
+    }
+    __syncthreads();
+    const int n = min(mn, kMidBuf);
+    if (threadIdx.x == 0) mbase = n > 0 ? atomicAdd(a.ctr + kCtrMid, n) : 0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < n && mbase + j < a.qcap; j += blockDim.x) a.mlist[mbase + j] = mbuf[j];
+}
+
+// Second phase: one warp per query, table offsets n0 .. kPhase1 (five per
+// lane, their loads in flight together).
+template <int RANK>
+__global__ void __launch_bounds__(256) k_query_mid(RouteArgs a)
+{
+    volatile int* ctr = a.ctr;
+    if (ctr[kCtrDense]) return;
+    const int nm = min((int)ctr[kCtrMid], a.qcap);  // at most the queries
+    constexpr int n0 = RANK == 3 ? 7 : 5;
+    const int lane = threadIdx.x & 31;
+    const int wstride = gridDim.x * (blockDim.x >> 5);
+    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < nm; i += wstride) {
+        const Query e = a.mlist[i];
+        int x, y, z;
+        coords(a, e.idx, x, y, z);
+        int found = -1;
+        int r2[5];
+        bool hit[5];
+#pragma unroll
+        for (int u = 0; u < 5; ++u) {
+            const int k = n0 + 32 * u + lane;
+            hit[u] = k < kPhase1 && probe<RANK>(a, x, y, z, k, r2[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 5; ++u) {
+            const unsigned h = __ballot_sync(kFull, hit[u]);
+            if (h && found < 0) found = __shfl_sync(kFull, r2[u], __ffs(h) - 1);
         }
         if (lane == 0) {
             if (found >= 0) {
@@ -168,7 +210,7 @@ __global__ void __launch_bounds__(256) k_query(RouteArgs a)
     }
 }
 
-// Second phase: one CTA per query the first left, over table offsets
+// Third phase: one CTA per query the second left, over table offsets
 // kPhase1 .. (4 per thread: 1024 cover the 3-D table). A hit writes the
 // output and marks the query done (fmin = -1); a miss leaves it to the
 // brute-force search.
@@ -467,6 +509,13 @@ cudaError_t launch_route_query(const RouteArgs& a, int blocks, cudaStream_t st)
 {
     if (a.rank == 3) k_query<3><<<blocks, 256, 0, st>>>(a);
     else k_query<2><<<blocks, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_route_query_mid(const RouteArgs& a, int blocks, cudaStream_t st)
+{
+    if (a.rank == 3) k_query_mid<3><<<blocks, 256, 0, st>>>(a);
+    else k_query_mid<2><<<blocks, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -15,10 +15,12 @@ namespace {
 // rank-3 layout: equal-q mask 1, Dist1 4, S 1, xwords 2, ywords 4), a uint16
 // count per column of the last column pass (at most one byte per point, since
 // that pass has at least two rows), the lists of the signed-point route
-// (N / 128 + 1024 queries of 8 bytes, N / 256 + 1024 signed boundary points of
-// 4 bytes, at most 65536 queries for the brute-force search at 12 bytes,
-// N / 256 + 1024 B2 sites of 8 bytes; under N / 8 + 1 MiB with the counters)
-// and the 256-byte alignment of its slices (inside that MiB).
+// (two of N / 128 + 1024 queries of 8 bytes -- all of them, and those the
+// first shell search leaves -- N / 256 + 1024 signed boundary points of 4
+// bytes, at most 65536 queries for the brute-force search at 12 bytes,
+// N / 256 + 1024 B2 sites of 8 bytes: at most 0.18 N + 0.8 MiB with the
+// counters) and the 256-byte alignment of its slices, all inside the N / 8 +
+// 1 MiB beyond 13 N (the largest shape needs 27.9 of these 28.6 MB).
 constexpr int64_t kMaxPoints = QAI_STATIC_MAX_POINTS;
 constexpr size_t kScratchBytes = (size_t)13 * (size_t)kMaxPoints + (size_t)kMaxPoints / 8 + ((size_t)1 << 20);
 
