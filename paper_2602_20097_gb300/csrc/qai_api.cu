@@ -381,7 +381,7 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
         ra.flist = reinterpret_cast<qai::Query*>(ws + lay.flist); ra.fcap = lay.fcap;
         ra.fmin = reinterpret_cast<int32_t*>(ws + lay.fmin);
         ra.b2list = reinterpret_cast<int32_t*>(ws + lay.b2list); ra.b2cap = lay.b2cap;
-        ra.max_r2 = route == Route::Brute ? -1 : qai::route_table_r2();
+        ra.max_r2 = route == Route::Brute ? -1 : qai::route_table_r2(sh.rank);
         ra.brute_budget = 1LL << 28;
         ra.m = m;
         if (route == Route::Dense) ra.qcap = -1;  // every count is over it: hand over at once

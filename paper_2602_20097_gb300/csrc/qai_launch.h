@@ -44,7 +44,7 @@ cudaError_t launch_colpass(int phase, int in_bytes, bool final_pass, ColArgs& a,
 // Signed-point route of the second EDT (qai_signed.cu): the shell search at
 // the queries, the list of B2 sites and the brute-force search; each kernel
 // reads the route counters and does nothing when it is not needed.
-int route_table_r2();
+int route_table_r2(int rank);
 cudaError_t launch_route_query(const RouteArgs& a, int blocks, cudaStream_t st);
 cudaError_t launch_route_query_mid(const RouteArgs& a, int blocks, cudaStream_t st);
 cudaError_t launch_route_query_far(const RouteArgs& a, int blocks, cudaStream_t st);

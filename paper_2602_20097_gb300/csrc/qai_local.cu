@@ -62,6 +62,16 @@ constexpr NearTable make_near()
                     }
     return t;
 }
+constexpr int count_near(bool three)
+{
+    int n = 0;
+    for (int dz = three ? -2 : 0; dz <= (three ? 2 : 0); ++dz)
+        for (int dy = -2; dy <= 2; ++dy)
+            for (int dx = -2; dx <= 2; ++dx)
+                if (dz * dz + dy * dy + dx * dx >= 1 && dz * dz + dy * dy + dx * dx <= kNearR2) ++n;
+    return n;
+}
+static_assert(count_near(true) == kNearN3 && count_near(false) == kNearN2, "nearest-site table size");
 __constant__ NearTable c_near = make_near();
 
 // Minimum resident CTAs per SM the kernels are compiled for (register cap).

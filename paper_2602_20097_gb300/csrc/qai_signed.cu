@@ -33,12 +33,16 @@ namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
-// Lattice offsets with squared length <= kTableR2, in order of squared
-// length: (r2 << 24) | (dz & 0xFF) << 16 | (dy & 0xFF) << 8 | (dx & 0xFF).
-// off3 spans three axes, off2 two (dz = 0).
+// Lattice offsets in order of squared length, then (dz, dy, dx):
+// (r2 << 24) | (dz & 0xFF) << 16 | (dy & 0xFF) << 8 | (dx & 0xFF), so r2 <=
+// 255. off3 spans three axes up to squared length kTableR2 (radius 6), off2
+// two axes (dz = 0) up to kTableR2_2 (radius 15.9); the search phases take
+// at most 1184 offsets (160 by a warp, 1024 by a CTA).
 constexpr int kTableR2 = 36;
 constexpr int kTableR = 6;
-constexpr int kN3 = 925, kN2 = 113;
+constexpr int kTableR2_2 = 255;
+constexpr int kTableR_2 = 15;
+constexpr int kN3 = 925, kN2 = 793;
 struct OffsetTable {
     int off3[kN3];
     int off2[kN2];
@@ -48,6 +52,12 @@ constexpr int pack_offset(int r2, int dz, int dy, int dx)
     return (int)(((unsigned)r2 << 24) | ((unsigned)(dz & 0xFF) << 16) | ((unsigned)(dy & 0xFF) << 8) |
                  (unsigned)(dx & 0xFF));
 }
+constexpr int isqrt_c(int v)
+{
+    int r = 0;
+    while ((r + 1) * (r + 1) <= v) ++r;
+    return r;
+}
 constexpr OffsetTable make_offsets()
 {
     OffsetTable t{};
@@ -56,12 +66,31 @@ constexpr OffsetTable make_offsets()
         for (int dz = -kTableR; dz <= kTableR; ++dz)
             for (int dy = -kTableR; dy <= kTableR; ++dy)
                 for (int dx = -kTableR; dx <= kTableR; ++dx)
-                    if (dz * dz + dy * dy + dx * dx == r2) {
-                        t.off3[n3++] = pack_offset(r2, dz, dy, dx);
-                        if (dz == 0) t.off2[n2++] = pack_offset(r2, 0, dy, dx);
-                    }
+                    if (dz * dz + dy * dy + dx * dx == r2) t.off3[n3++] = pack_offset(r2, dz, dy, dx);
+    for (int r2 = 0; r2 <= kTableR2_2; ++r2)
+        for (int dy = -kTableR_2; dy <= kTableR_2; ++dy) {
+            const int rest = r2 - dy * dy;
+            if (rest < 0) continue;
+            const int dx = isqrt_c(rest);
+            if (dx * dx != rest) continue;
+            t.off2[n2++] = pack_offset(r2, 0, dy, -dx);  // increasing dx
+            if (dx > 0) t.off2[n2++] = pack_offset(r2, 0, dy, dx);
+        }
     return t;
 }
+// the tables hold exactly kN3 and kN2 offsets
+constexpr int count_offsets(int r2max, int r, bool three)
+{
+    int n = 0;
+    for (int dz = three ? -r : 0; dz <= (three ? r : 0); ++dz)
+        for (int dy = -r; dy <= r; ++dy)
+            for (int dx = -r; dx <= r; ++dx)
+                if (dz * dz + dy * dy + dx * dx <= r2max) ++n;
+    return n;
+}
+static_assert(count_offsets(kTableR2, kTableR, true) == kN3, "3-D offset table size");
+static_assert(count_offsets(kTableR2_2, kTableR_2, false) == kN2, "2-D offset table size");
+static_assert(kTableR2_2 <= 255 && (kTableR_2 + 1) * (kTableR_2 + 1) > kTableR2_2, "2-D table radius");
 __constant__ OffsetTable c_off = make_offsets();
 
 // GetBoundary(S) of Algorithm 3 at an interior point b: an axis neighbour
@@ -503,7 +532,7 @@ __global__ void __launch_bounds__(256) k_brute(RouteArgs a)
 
 }  // namespace
 
-int route_table_r2() { return kTableR2; }
+int route_table_r2(int rank) { return rank == 2 ? kTableR2_2 : kTableR2; }
 
 cudaError_t launch_route_query(const RouteArgs& a, int blocks, cudaStream_t st)
 {
