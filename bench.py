@@ -445,8 +445,7 @@ def run_batch96(args):
                       "sequential": {"value": npts * 4 / (ms_s * 1e-3) / 1e9, "ms_per_step": ms_s,
                                      "launches": seq_launches},
                       "batched_kernels_per_graph": launches, "identical_to_sequential": same,
-                      "autotuned": {str(k): {"rows_per_band": v[0], "max_w": v[1],
-                                             "order": "largest first" if v[2] else "as given"}
+                      "autotuned": {str(k): {"streams": v[0], "order": "largest first" if v[1] else "as given"}
                                     for k, v in choice.items()}}), flush=True)
 
 

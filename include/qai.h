@@ -195,14 +195,17 @@ qai_status qai_mitigate_backward(const int32_t* d_q, const float* d_grad_out, fl
 /* ---- Batched form (no counterpart in the paper) ---------------------------
  * n independent fields in one call: field i is d_q[i] -> d_out[i] (device
  * buffers), rank ranks[i], extents dims[3*i .. 3*i + ranks[i]) (slowest first),
- * bound eb[i]; params are shared. Each pipeline stage runs as one grouped
- * kernel over all fields of the same rank, and the whole launch sequence is
- * captured into a CUDA graph the first time a batch is seen (keyed by every
- * pointer, extent and parameter) and replayed afterwards: a repeated batch is
- * one graph launch on `stream`. When `stream` is already capturing, the
- * launches are recorded into the caller's graph instead. Results equal those
- * of n qai_mitigate calls. Column-pass tile shapes and the field order come
- * from qai_autotune_batched when it has seen a batch of the same shapes. */
+ * bound eb[i]; params are shared. Rank-2 and rank-3 fields each run the
+ * launch sequence of a plain qai_mitigate call, dealt round robin onto a few
+ * streams forked from `stream` and joined back (the small fields' kernels
+ * overlap); rank-1 fields run as two grouped kernels over all of them. The
+ * whole launch sequence is captured into a CUDA graph the first time a batch
+ * is seen (keyed by every pointer, extent and parameter) and replayed
+ * afterwards: a repeated batch is one graph launch on `stream`. When `stream`
+ * is already capturing, the launches are recorded into the caller's graph
+ * instead. Results equal those of n qai_mitigate calls. The stream count and
+ * the field order come from qai_autotune_batched when it has seen a batch of
+ * the same shapes. */
 
 /* Device workspace of a batch: the sum of the fields' workspaces. */
 qai_status qai_workspace_size_batched(int n, const int32_t* ranks, const int64_t* dims, size_t* bytes);
@@ -216,17 +219,16 @@ qai_status qai_mitigate_batched(int n, const int32_t* const* d_q, float* const* 
 typedef struct {
     int32_t rank;           /* 1, 2 or 3 (0: no field of this rank)           */
     int32_t fields;
-    int32_t rows_per_band;  /* rows per band of the column passes             */
-    int32_t max_w;          /* columns per CTA, at most                       */
+    int32_t streams;        /* streams the fields are dealt onto (rank 1: 1)  */
     int32_t order;          /* 0: fields as given, 1: largest field first     */
-    float ms;               /* time of the group's stages with this choice    */
+    float ms;               /* time of the group's launches with this choice  */
 } qai_batch_choice;
 
-/* Times every candidate tile shape and field order on this batch (running
- * its stages several times; the outputs hold a correct result afterwards),
- * keeps the fastest per rank group for later qai_mitigate_batched calls with
- * the same shapes, and reports it in choices[0..2] (ranks 1..3) when non-NULL.
- * Synchronises `stream`. */
+/* Times every candidate stream count (1, 2, 4, 8) and field order on this
+ * batch (running its launches several times; the outputs hold a correct
+ * result afterwards), keeps the fastest per rank group for later
+ * qai_mitigate_batched calls with the same shapes, and reports it in
+ * choices[0..2] (ranks 1..3) when non-NULL. Synchronises `stream`. */
 qai_status qai_autotune_batched(int n, const int32_t* const* d_q, float* const* d_out,
                                 const int32_t* ranks, const int64_t* dims, const double* eb,
                                 const qai_params* params, void* d_ws, size_t ws_bytes,
@@ -282,8 +284,8 @@ qai_status qai_quality(const float* d_x, const float* d_y, int rank, const int64
  * no counterpart; it is a deployment convenience of this library.
  *
  * Instead of a workspace it uses one scratch array compiled into the library
- * (a 256-byte aligned __device__ array of 13.125 * QAI_STATIC_MAX_POINTS +
- * 1 MiB bytes, about 27.3 MiB). Every GPU that loads the library holds that array
+ * (a 256-byte aligned __device__ array of 13.5 * QAI_STATIC_MAX_POINTS +
+ * 1 MiB bytes, about 28 MiB). Every GPU that loads the library holds that array
  * until the process exits. The call itself allocates nothing: no cudaMalloc,
  * no cudaFree, no library routine that allocates.
  *  d_q, d_out, rank, dims, eb, params, stream: as for qai_mitigate (the

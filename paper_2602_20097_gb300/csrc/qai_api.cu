@@ -56,6 +56,7 @@ struct Stat {
 };
 std::mutex g_prof_mu;
 bool g_prof_on = false;
+thread_local int* g_launch_sink = nullptr;  // set: count launches here, no events
 std::string g_prof_only;  // time only kernels of this name ("" = all)
 std::vector<Pending> g_pending;
 std::vector<Stat> g_stats;
@@ -77,6 +78,10 @@ cudaEvent_t take_event()
 template <class F>
 cudaError_t timed(const char* name, double algo_bytes, cudaStream_t st, F&& fn)
 {
+    if (g_launch_sink) {  // recorded into a graph: counted when the graph runs
+        ++*g_launch_sink;
+        return fn();
+    }
     cudaEvent_t a = nullptr, b = nullptr;
     bool prof;
     {
@@ -156,7 +161,7 @@ Layout layout_for(const Shape& s, uint32_t flags)
         l.qcap = (int)(N / 128 + 1024);
         l.scap = (int)(N / 256 + 1024);
         l.fcap = std::min(l.qcap, 1 << 16);
-        l.b2cap = (int)(N / 256 + 1024);
+        l.b2cap = (int)(N / 32 + 4096);  // B2 sites up to ~3 % of the points
         l.ctr = take(qai::kCtrWords * 4);
         l.qlist = take((size_t)l.qcap * sizeof(qai::Query));
         l.slist = take((size_t)l.scap * 4);
@@ -453,6 +458,21 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
 }
 
 }  // namespace
+
+namespace qai {
+namespace host {
+
+LaunchSink::LaunchSink(int* counter) : prev_(g_launch_sink) { g_launch_sink = counter; }
+LaunchSink::~LaunchSink() { g_launch_sink = prev_; }
+
+qai_status run_plain(const int32_t* d_q, float* d_out, const Shape& sh, const MethodArgs& m, char* ws,
+                     const Layout& lay, cudaStream_t st)
+{
+    return run_pipeline(d_q, d_out, sh, m, ws, lay, st, nullptr);
+}
+
+}  // namespace host
+}  // namespace qai
 
 void qai::set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
 

@@ -1,14 +1,16 @@
 // qai_batched.cu -- many fields in one call (see include/qai.h).
 //
-// Fields are grouped by rank (after squeezing). Each stage of Algorithm 4's
-// pipeline runs as one grouped kernel over every field of a group (row pass
-// 1, y pass, z pass, row pass 2, y pass, fused z pass + step E): a CTA finds
-// its field in a table passed by value in the kernel parameters. The launch
-// sequence of a batch is captured once into a CUDA graph and replayed, so a
-// repeated batch costs one graph launch. Per group, the column-pass tile
-// shape (rows per band, columns per CTA) and the field order (as given, or
-// largest first) come from an autotuner that times the candidates on the
-// batch itself and caches the winner by the group's shape signature.
+// Fields are grouped by rank (after squeezing). Rank-2 and rank-3 fields run
+// their own plain launch sequence (qai_mitigate without per-step outputs:
+// the local first EDT and the signed-point route), dealt round robin onto a
+// few streams forked from the caller's, so the small fields' short, latency-
+// bound kernels overlap; rank-1 fields run as two grouped row-pass kernels
+// over all of them (a CTA finds its field in a table passed by value in the
+// kernel parameters). The whole launch sequence of a batch is captured once
+// into a CUDA graph and replayed, so a repeated batch costs one graph launch.
+// Per group, the stream count and the field order (as given, or largest
+// first) come from an autotuner that times the candidates on the batch itself
+// and caches the winner by the group's shape signature.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -26,10 +28,33 @@ using namespace qai::host;
 namespace {
 
 struct GroupCfg {
-    int rows_per_band = 32;
-    int max_w = 16;
-    int order = 1;  // 0: as given, 1: largest field first
+    int order = 1;    // 0: as given, 1: largest field first
+    int streams = 4;  // rank 2 and 3: streams the fields' launch sequences are dealt onto
 };
+constexpr int kMaxStreams = 8;
+
+// Streams forked from a caller's stream (an event recorded there, waited on
+// by each) and joined back (one event per stream, waited on by the caller's
+// stream). Works inside a stream capture: the forked streams join it.
+struct Forker {
+    cudaStream_t s[kMaxStreams] = {};
+    cudaEvent_t fork_ev = nullptr;
+    cudaEvent_t join_ev[kMaxStreams] = {};
+    bool ok = false;
+};
+Forker* forker()
+{
+    thread_local Forker f;
+    if (!f.ok) {
+        bool good = cudaEventCreateWithFlags(&f.fork_ev, cudaEventDisableTiming) == cudaSuccess;
+        for (int i = 0; good && i < kMaxStreams; ++i)
+            good = cudaStreamCreateWithFlags(&f.s[i], cudaStreamNonBlocking) == cudaSuccess &&
+                   cudaEventCreateWithFlags(&f.join_ev[i], cudaEventDisableTiming) == cudaSuccess;
+        if (!good) return nullptr;
+        f.ok = true;
+    }
+    return &f;
+}
 
 struct Field {
     int index;
@@ -114,36 +139,16 @@ qai_status plan(int n, const int32_t* const* d_q, float* const* d_out, const int
     return QAI_OK;
 }
 
-// The stage launches of one group (same order and arguments as the single
-// field pipeline, qai_api.cu). Returns the number of kernels launched.
-qai_status launch_group(const Batch& bt, int rank, const GroupCfg& cfg, char* ws, cudaStream_t st,
-                        int* kernels)
+// Rank-1 fields: the grouped row passes (phase 1 writes Dist1 and S, phase 2
+// GetBoundary(S), the EDT of B2 and step E), at most kMaxGroup fields a launch.
+qai_status launch_rank1(const Batch& bt, const std::vector<int>& order, char* ws, cudaStream_t st, int* kernels)
 {
-    std::vector<int> order = bt.group[rank];
-    if (order.empty()) return QAI_OK;
-    if (cfg.order == 1)
-        std::stable_sort(order.begin(), order.end(),
-                         [&](int a, int b) { return bt.f[a].sh.N > bt.f[b].sh.N; });
-    const bool final1 = rank == 1;
     for (size_t c0 = 0; c0 < order.size(); c0 += kMaxGroup) {
         const int cn = (int)std::min(order.size() - c0, (size_t)kMaxGroup);
         auto F = [&](int k) -> const Field& { return bt.f[order[c0 + k]]; };
-        auto ptrs = [&](const Field& f, uint8_t*& eqm, int32_t*& dist1, int8_t*& s, uint16_t*& xw, uint32_t*& yw) {
-            char* b = ws + f.ws_off;
-            eqm = reinterpret_cast<uint8_t*>(b + f.lay.eqm);
-            dist1 = reinterpret_cast<int32_t*>(b + f.lay.dist1);
-            s = reinterpret_cast<int8_t*>(b + f.lay.s);
-            xw = rank >= 2 ? reinterpret_cast<uint16_t*>(b + f.lay.xw) : nullptr;
-            yw = rank >= 3 ? reinterpret_cast<uint32_t*>(b + f.lay.yw) : nullptr;
-        };
-        int max_nx = 0, max_ny = 0, max_nz = 0;
-        for (int k = 0; k < cn; ++k) {
-            max_nx = std::max(max_nx, F(k).sh.nx);
-            max_ny = std::max(max_ny, F(k).sh.ny);
-            max_nz = std::max(max_nz, F(k).sh.nz);
-        }
-        // row passes (phase 1 and 2)
-        auto rows = [&](int phase) -> qai_status {
+        int max_nx = 0;
+        for (int k = 0; k < cn; ++k) max_nx = std::max(max_nx, F(k).sh.nx);
+        for (int phase = 1; phase <= 2; ++phase) {
             thread_local RowTable rt;  // large: built on the host, copied into the launch
             std::memset(&rt, 0, sizeof rt);
             rt.n = cn;
@@ -152,16 +157,16 @@ qai_status launch_group(const Batch& bt, int rank, const GroupCfg& cfg, char* ws
             int acc = 0;
             for (int k = 0; k < cn; ++k) {
                 const Field& f = F(k);
-                uint8_t* eqm; int32_t* dist1; int8_t* s; uint16_t* xw; uint32_t* yw;
-                ptrs(f, eqm, dist1, s, xw, yw);
+                char* b = ws + f.ws_off;
                 RowArgs r{};
-                r.rank = rank; r.nz = f.sh.nz; r.ny = f.sh.ny; r.nx = f.sh.nx;
-                r.q = f.q; r.eqm = eqm; r.m = f.m;
+                r.rank = 1; r.nz = f.sh.nz; r.ny = f.sh.ny; r.nx = f.sh.nx;
+                r.q = f.q; r.eqm = reinterpret_cast<uint8_t*>(b + f.lay.eqm); r.m = f.m;
+                int32_t* dist1 = reinterpret_cast<int32_t*>(b + f.lay.dist1);
+                int8_t* s = reinterpret_cast<int8_t*>(b + f.lay.s);
                 if (phase == 1) {
-                    if (final1) { r.dist1 = dist1; r.s_out = s; } else r.xw = xw;
+                    r.dist1 = dist1; r.s_out = s;
                 } else {
-                    r.s_in = s;
-                    if (final1) { r.dist1_in = dist1; r.out = f.out; } else r.xw = xw;
+                    r.s_in = s; r.dist1_in = dist1; r.out = f.out;
                 }
                 prepare_rowpass(r);
                 rt.args[k] = r;
@@ -169,65 +174,50 @@ qai_status launch_group(const Batch& bt, int rank, const GroupCfg& cfg, char* ws
                 acc += f.sh.nz * f.sh.ny;
             }
             rt.first_row[cn] = acc;
-            cudaError_t e = launch_rowpass_grouped(phase, final1, rt, st);
+            cudaError_t e = launch_rowpass_grouped(phase, true, rt, st);
             ++*kernels;
-            return e == cudaSuccess ? QAI_OK : cuda_fail(e, "grouped row pass");
-        };
-        // column passes: axis 1 = y, 2 = z
-        auto cols = [&](int phase, int axis, bool fin) -> qai_status {
-            thread_local ColTable ct;
-            std::memset(&ct, 0, sizeof ct);
-            const int in_bytes = axis == 1 ? 2 : 4;
-            ColConfig cc;
-            const int maxL = axis == 1 ? max_ny : max_nz;
-            if (!choose_colpass_with(maxL, in_bytes, cfg.rows_per_band, cfg.max_w, &cc))
-                return fail(QAI_ERR_SHAPE, "line length %d does not fit shared memory", maxL);
-            ct.n = cn;
-            int acc = 0;
-            for (int k = 0; k < cn; ++k) {
-                const Field& f = F(k);
-                uint8_t* eqm; int32_t* dist1; int8_t* s; uint16_t* xw; uint32_t* yw;
-                ptrs(f, eqm, dist1, s, xw, yw);
-                ColArgs a{};
-                a.m = f.m;
-                if (axis == 1) {
-                    a.in = xw; a.L = f.sh.ny; a.C = f.sh.nx; a.P = f.sh.nz;
-                    a.row_stride = f.sh.nx; a.plane_stride = (int64_t)f.sh.ny * f.sh.nx;
-                } else {
-                    a.in = yw; a.L = f.sh.nz; a.C = f.sh.ny * f.sh.nx; a.P = 1;
-                    a.row_stride = (int64_t)f.sh.ny * f.sh.nx; a.plane_stride = 0;
-                }
-                uint16_t* cflag = reinterpret_cast<uint16_t*>(ws + f.ws_off + f.lay.cflag);
-                if (phase == 1) {
-                    if (fin) { a.dist1 = dist1; a.s_out = s; a.col_count_out = cflag; } else a.out_w = yw;
-                } else {
-                    if (fin) {
-                        a.out = f.out; a.q = f.q; a.dist1_in = dist1; a.s_in = s; a.col_count_in = cflag;
-                    } else {
-                        a.out_w = yw;
-                    }
-                }
-                const int64_t gx = (int64_t)(f.sh.nx - 1) * (f.sh.nx - 1);
-                const int64_t gxy = gx + (int64_t)(f.sh.ny - 1) * (f.sh.ny - 1);
-                prepare_colpass(a, in_bytes, cc, axis == 1 ? gx : gxy);
-                ct.args[k] = a;
-                ct.first_block[k] = acc;
-                acc += colpass_blocks(a, cc.W);
-            }
-            ct.first_block[cn] = acc;
-            cudaError_t e = launch_colpass_grouped(phase, in_bytes, fin, ct, cc, st);
-            ++*kernels;
-            return e == cudaSuccess ? QAI_OK : cuda_fail(e, "grouped column pass");
-        };
-        qai_status s;
-        if ((s = rows(1)) != QAI_OK) return s;
-        if (rank == 2 && (s = cols(1, 1, true)) != QAI_OK) return s;
-        if (rank == 3 && ((s = cols(1, 1, false)) != QAI_OK || (s = cols(1, 2, true)) != QAI_OK)) return s;
-        if ((s = rows(2)) != QAI_OK) return s;
-        if (rank == 2 && (s = cols(2, 1, true)) != QAI_OK) return s;
-        if (rank == 3 && ((s = cols(2, 1, false)) != QAI_OK || (s = cols(2, 2, true)) != QAI_OK)) return s;
+            if (e != cudaSuccess) return cuda_fail(e, "grouped row pass");
+        }
     }
     return QAI_OK;
+}
+
+// The launches of one rank group on `st` (rank 2 and 3: on cfg.streams
+// streams forked from it and joined back). Adds the kernels launched to
+// *kernels.
+qai_status launch_group(const Batch& bt, int rank, const GroupCfg& cfg, char* ws, cudaStream_t st,
+                        int* kernels)
+{
+    std::vector<int> order = bt.group[rank];
+    if (order.empty()) return QAI_OK;
+    if (cfg.order == 1)
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int a, int b) { return bt.f[a].sh.N > bt.f[b].sh.N; });
+    if (rank == 1) return launch_rank1(bt, order, ws, st, kernels);
+    const int ns = std::max(1, std::min(cfg.streams, kMaxStreams));
+    Forker* fk = ns > 1 ? forker() : nullptr;
+    if (ns > 1 && !fk) return cuda_fail(cudaGetLastError(), "batch streams");
+    cudaError_t e;
+    if (fk) {
+        if ((e = cudaEventRecord(fk->fork_ev, st)) != cudaSuccess) return cuda_fail(e, "fork");
+        for (int i = 0; i < ns; ++i)
+            if ((e = cudaStreamWaitEvent(fk->s[i], fk->fork_ev, 0)) != cudaSuccess) return cuda_fail(e, "fork");
+    }
+    qai_status s = QAI_OK;
+    {
+        LaunchSink sink(kernels);
+        for (size_t k = 0; k < order.size() && s == QAI_OK; ++k) {
+            const Field& f = bt.f[order[k]];
+            s = run_plain(f.q, f.out, f.sh, f.m, ws + f.ws_off, f.lay, fk ? fk->s[k % ns] : st);
+        }
+    }
+    if (fk) {  // join, also after an error, so no stream is left forked
+        for (int i = 0; i < ns; ++i) {
+            if ((e = cudaEventRecord(fk->join_ev[i], fk->s[i])) != cudaSuccess && s == QAI_OK) s = cuda_fail(e, "join");
+            if ((e = cudaStreamWaitEvent(st, fk->join_ev[i], 0)) != cudaSuccess && s == QAI_OK) s = cuda_fail(e, "join");
+        }
+    }
+    return s;
 }
 
 qai_status launch_all(const Batch& bt, const GroupCfg cfgs[4], char* ws, cudaStream_t st, int* kernels)
@@ -359,7 +349,7 @@ qai_status qai_autotune_batched(int n, const int32_t* const* d_q, float* const* 
     if (s != QAI_OK) return s;
     if ((s = check_ws(bt, d_ws, ws_bytes)) != QAI_OK) return s;
     char* ws = static_cast<char*>(d_ws);
-    static const GroupCfg cands[] = {{32, 16, 1}, {32, 16, 0}, {32, 32, 1}, {24, 16, 1}, {48, 16, 1}, {32, 8, 1}};
+    static const GroupCfg cands[] = {{1, 1}, {1, 2}, {1, 4}, {1, 8}, {0, 1}, {0, 2}, {0, 4}, {0, 8}};
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return cuda_fail(cudaGetLastError(), "event create");
@@ -369,6 +359,7 @@ qai_status qai_autotune_batched(int n, const int32_t* const* d_q, float* const* 
         float best_ms = 1e30f;
         GroupCfg best;
         for (const GroupCfg& c : cands) {
+            if (rank == 1 && c.streams != 1) continue;  // rank 1: one grouped launch per phase
             int kernels = 0;
             if ((s = launch_group(bt, rank, c, ws, stream, &kernels)) != QAI_OK) break;  // warm-up
             cudaEventRecord(e0, stream);
@@ -390,8 +381,7 @@ qai_status qai_autotune_batched(int n, const int32_t* const* d_q, float* const* 
             qai_batch_choice& ch = choices[rank - 1];
             ch.rank = rank;
             ch.fields = (int32_t)bt.group[rank].size();
-            ch.rows_per_band = best.rows_per_band;
-            ch.max_w = best.max_w;
+            ch.streams = best.streams;
             ch.order = best.order;
             ch.ms = best_ms;
         }

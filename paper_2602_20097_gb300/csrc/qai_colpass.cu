@@ -680,24 +680,6 @@ __global__ void __launch_bounds__(512, IN == 2 ? 3 : 2) k_colpass(ColArgs a)
     }
 }
 
-// Several fields in one launch: CTA b works on field f with
-// first_block[f] <= b < first_block[f + 1]. The table travels by value in the
-// kernel parameters.
-template <int PHASE, int IN, bool FINAL>
-__global__ void __launch_bounds__(512, IN == 2 ? 3 : 2) k_colpass_grouped(const __grid_constant__ ColTable t)
-{
-    const int b = blockIdx.x;
-    int lo = 0, hi = t.n - 1;
-    while (lo < hi) {  // last f with first_block[f] <= b
-        const int mid = (lo + hi + 1) >> 1;
-        if (t.first_block[mid] <= b) lo = mid;
-        else hi = mid - 1;
-    }
-    const ColArgs& a = t.args[lo];
-    if (a.narrow) colpass_tile<PHASE, IN, FINAL, false, true>(a, b - t.first_block[lo]);
-    else colpass_tile<PHASE, IN, FINAL, false, false>(a, b - t.first_block[lo]);
-}
-
 // The last phase-2 pass in adjoint mode (IN = 2: 2-D fields, 4: 3-D).
 template <int IN, bool NARROW>
 __global__ void __launch_bounds__(512, 2) k_colpass_grad(ColArgs a)
@@ -778,24 +760,6 @@ void prepare_colpass(ColArgs& a, int in_bytes, const ColConfig& cfg, int64_t max
 }
 
 int colpass_blocks(const ColArgs& a, int W) { return ((a.C + W - 1) / W) * a.P; }
-
-cudaError_t launch_colpass_grouped(int phase, int in_bytes, bool final_pass, const ColTable& t,
-                                   const ColConfig& cfg, cudaStream_t st)
-{
-    const dim3 grid(t.first_block[t.n]), block(cfg.W, cfg.B);
-    auto run = [&](auto kern) -> cudaError_t {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
-        if (e != cudaSuccess) return e;
-        kern<<<grid, block, cfg.smem, st>>>(t);
-        return cudaGetLastError();
-    };
-    if (phase == 1) {
-        if (in_bytes == 2) return final_pass ? run(k_colpass_grouped<1, 2, true>) : run(k_colpass_grouped<1, 2, false>);
-        return run(k_colpass_grouped<1, 4, true>);
-    }
-    if (in_bytes == 2) return final_pass ? run(k_colpass_grouped<2, 2, true>) : run(k_colpass_grouped<2, 2, false>);
-    return run(k_colpass_grouped<2, 4, true>);
-}
 
 cudaError_t launch_colpass(int phase, int in_bytes, bool final_pass, ColArgs& a, const ColConfig& cfg,
                            bool debug, int64_t max_g, cudaStream_t st)

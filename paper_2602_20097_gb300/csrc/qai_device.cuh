@@ -185,11 +185,6 @@ struct LocalArgs {
 // Grouped launches: several fields in one kernel, the per-field arguments
 // passed by value in the kernel parameters (at most kMaxGroup per launch).
 constexpr int kMaxGroup = 96;
-struct ColTable {
-    int n;                            // fields
-    int first_block[kMaxGroup + 1];   // CTA offsets; first_block[n] = grid size
-    ColArgs args[kMaxGroup];
-};
 struct RowTable {
     int n;
     int warps;                        // warps per CTA

@@ -37,5 +37,23 @@ qai_status check_params(const qai_params* p);
 MethodArgs method_args(const qai_params* p, double eb);
 void count_launch();
 
+// qai_mitigate's launch sequence without per-step outputs (a plain call) on a
+// validated shape and a workspace laid out by layout_for(sh, 0).
+qai_status run_plain(const int32_t* d_q, float* d_out, const Shape& sh, const MethodArgs& m, char* ws,
+                     const Layout& lay, cudaStream_t st);
+
+// While alive, the library's launches on this host thread are counted into
+// *counter and not timed or counted globally (launches recorded into a graph).
+class LaunchSink {
+public:
+    explicit LaunchSink(int* counter);
+    ~LaunchSink();
+    LaunchSink(const LaunchSink&) = delete;
+    LaunchSink& operator=(const LaunchSink&) = delete;
+
+private:
+    int* prev_;
+};
+
 }  // namespace host
 }  // namespace qai

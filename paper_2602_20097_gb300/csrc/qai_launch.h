@@ -34,8 +34,6 @@ int colpass_blocks(const ColArgs& a, int W);
 // The last phase-2 column pass in adjoint mode: a.grad_out, a.partials set,
 // one pair of FP64 sums per CTA (colpass_blocks(a, cfg.W) CTAs).
 cudaError_t launch_colpass_grad(int in_bytes, ColArgs& a, const ColConfig& cfg, int64_t max_g, cudaStream_t st);
-cudaError_t launch_colpass_grouped(int phase, int in_bytes, bool final_pass, const ColTable& t,
-                                   const ColConfig& cfg, cudaStream_t st);
 // max_g bounds the squared distances carried by the input words; it decides
 // whether RemoveEDT can run on 32-bit products.
 cudaError_t launch_colpass(int phase, int in_bytes, bool final_pass, ColArgs& a,

@@ -369,42 +369,74 @@ __global__ void __launch_bounds__(256) k_b2sites(RouteArgs a, int vec)
     }
     const int ns = ctr[kCtrSigned], nq = ctr[kCtrQueries];
     const int plane = a.ny * a.nx;
-    constexpr int nb = 2 * RANK;
-    auto nbr_off = [&](int j) -> int {  // z-, z+, y-, y+, x-, x+ (rank 3); y-, y+, x-, x+ (rank 2)
-        const int ax = RANK == 3 ? j >> 1 : (j >> 1) + 1;
-        const int step = ax == 0 ? plane : (ax == 1 ? a.nx : 1);
-        return (j & 1) ? step : -step;
-    };
-    const int total = (ns + nq) * (nb + 1);
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t - (int)threadIdx.x < total; t += gridDim.x * blockDim.x) {
-        unsigned site = 0;
-        int bx = 0, by = 0, bz = 0;
-        if (t < total) {
-            const int item = t / (nb + 1), j = t - item * (nb + 1);
-            const int p = item < ns ? a.slist[item] : a.qlist[item - ns].idx;
-            const int b = j == nb ? p : p + nbr_off(j);
-            bz = b / plane;
-            const int rem = b - bz * plane;
-            by = rem / a.nx;
-            bx = rem - by * a.nx;
+    // one thread per signed point p: its candidates are p and its axis
+    // neighbours, and every S they need lies within two axis steps of p, so
+    // all loads of the thread are issued together
+    for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < ns + nq; item += gridDim.x * blockDim.x) {
+        const int p = item < ns ? a.slist[item] : a.qlist[item - ns].idx;
+        int x, y, z;
+        coords(a, p, x, y, z);
+        // S at p + (dz, dy, dx), 0 outside the field (never read there: only
+        // interior candidates are tested, and their neighbours lie inside)
+        auto S = [&](int dz, int dy, int dx) -> int {
+            const bool in = (unsigned)(x + dx) < (unsigned)a.nx && (unsigned)(y + dy) < (unsigned)a.ny &&
+                            (RANK == 2 || (unsigned)(z + dz) < (unsigned)a.nz);
+            return in ? (int)__ldg(a.s + p + dz * plane + dy * a.nx + dx) : 0;
+        };
+        // candidate c: 0 = p, then z-, z+, y-, y+, x-, x+ (rank 2: y-, y+, x-, x+)
+#pragma unroll
+        for (int c = 0; c <= 2 * RANK; ++c) {
+            int cz = 0, cy = 0, cx = 0;
+            if (c > 0) {
+                const int ax = RANK == 3 ? (c - 1) >> 1 : ((c - 1) >> 1) + 1;
+                const int sg = (c - 1) & 1 ? 1 : -1;
+                (ax == 0 ? cz : (ax == 1 ? cy : cx)) = sg;
+            }
+            const int bx = x + cx, by = y + cy, bz = z + cz;
             const bool inner = (unsigned)(bx - 1) < (unsigned)(a.nx - 2) && (unsigned)(by - 1) < (unsigned)(a.ny - 2) &&
                                (RANK == 2 || (unsigned)(bz - 1) < (unsigned)(a.nz - 2));
-            // p +- step stays inside the field when b is interior; a neighbour
-            // off the interior is never a site, whatever wrapped index it has
-            bool own = inner;
-            if (own && j != nb) {
-                // b has S = 0 and p is its signed neighbour of smallest index
-                int sv[2 * RANK];
+            if (!inner) continue;
+            const int sb0 = S(cz, cy, cx);
+            // the six axis neighbours of the candidate: z-, z+, y-, y+, x-, x+
+            int nbv[6];
+            nbv[0] = RANK == 3 ? S(cz - 1, cy, cx) : sb0;
+            nbv[1] = RANK == 3 ? S(cz + 1, cy, cx) : sb0;
+            nbv[2] = S(cz, cy - 1, cx);
+            nbv[3] = S(cz, cy + 1, cx);
+            nbv[4] = S(cz, cy, cx - 1);
+            nbv[5] = S(cz, cy, cx + 1);
+            bool own = true;
+            if (c > 0) {
+                // an S = 0 candidate is tested by its signed neighbour of
+                // smallest linear index: p must precede every other one (an
+                // offset precedes 0 in (dz, dy, dx) order exactly when its
+                // point precedes p, for points inside the field)
+                own = sb0 == 0;
+                const int oz[6] = {cz - 1, cz + 1, cz, cz, cz, cz}, oy[6] = {cy, cy, cy - 1, cy + 1, cy, cy},
+                          ox[6] = {cx, cx, cx, cx, cx - 1, cx + 1};
 #pragma unroll
-                for (int k = 0; k < 2 * RANK; ++k) sv[k] = __ldg(a.s + b + nbr_off(k));
-                own = __ldg(a.s + b) == 0;
-#pragma unroll
-                for (int k = 0; k < 2 * RANK; ++k)
-                    if (b + nbr_off(k) < p && sv[k] != 0) own = false;
+                for (int k = 0; k < 6; ++k) {
+                    const bool before = oz[k] < 0 || (oz[k] == 0 && (oy[k] < 0 || (oy[k] == 0 && ox[k] < 0)));
+                    if (before && nbv[k] != 0) own = false;
+                }
             }
-            site = own && is_b2<RANK>(a, (int64_t)b) ? 1u : 0u;
+            if (!own) continue;
+            const unsigned em = a.m.b2_rule == 1 ? 0x3Fu
+                                                 : (unsigned)__ldg(a.eqm + p + cz * plane + cy * a.nx + cx);
+            unsigned diff = 0;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) diff |= (unsigned)(nbv[k] != sb0) << k;
+            if (diff & em) {
+                const int kk = atomicAdd(sb.n, 1);
+                const uint2 e = make_uint2((uint32_t)bx | ((uint32_t)by << 16), (uint32_t)bz);
+                if (kk < kSiteBuf) {
+                    sb.e[kk] = e;
+                } else {
+                    const int g = atomicAdd(a.ctr + kCtrB2, 1);
+                    if (g < a.b2cap) reinterpret_cast<uint2*>(a.b2list)[g] = e;
+                }
+            }
         }
-        append_sites(a, sb, site, bx, by, bz);
     }
     flush_sites(a, sb, &sbase);
 }

@@ -18,11 +18,11 @@ namespace {
 // (two of N / 128 + 1024 queries of 8 bytes -- all of them, and those the
 // first shell search leaves -- N / 256 + 1024 signed boundary points of 4
 // bytes, at most 65536 queries for the brute-force search at 12 bytes,
-// N / 256 + 1024 B2 sites of 8 bytes: at most 0.18 N + 0.8 MiB with the
-// counters) and the 256-byte alignment of its slices, all inside the N / 8 +
-// 1 MiB beyond 13 N (the largest shape needs 27.9 of these 28.6 MB).
+// N / 32 + 4096 B2 sites of 8 bytes: at most 0.39 N + 0.8 MiB with the
+// counters) and the 256-byte alignment of its slices, all inside the N / 2 +
+// 1 MiB beyond 13 N.
 constexpr int64_t kMaxPoints = QAI_STATIC_MAX_POINTS;
-constexpr size_t kScratchBytes = (size_t)13 * (size_t)kMaxPoints + (size_t)kMaxPoints / 8 + ((size_t)1 << 20);
+constexpr size_t kScratchBytes = (size_t)13 * (size_t)kMaxPoints + (size_t)kMaxPoints / 2 + ((size_t)1 << 20);
 
 __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 

@@ -50,8 +50,8 @@ class DebugOut(ctypes.Structure):
 
 
 class BatchChoice(ctypes.Structure):
-    _fields_ = [("rank", ctypes.c_int32), ("fields", ctypes.c_int32), ("rows_per_band", ctypes.c_int32),
-                ("max_w", ctypes.c_int32), ("order", ctypes.c_int32), ("ms", ctypes.c_float)]
+    _fields_ = [("rank", ctypes.c_int32), ("fields", ctypes.c_int32), ("streams", ctypes.c_int32),
+                ("order", ctypes.c_int32), ("ms", ctypes.c_float)]
 
 
 class KernelStat(ctypes.Structure):
@@ -387,8 +387,9 @@ class Batch:
 
 
 def mitigate_batched(batch: Batch, stream=None, **kw):
-    """Algorithm 4 on every field of ``batch`` in one call (grouped kernels,
-    replayed from a cached CUDA graph). Returns ``batch.outs``."""
+    """Algorithm 4 on every field of ``batch`` in one call (the fields' launch
+    sequences on forked streams, replayed from a cached CUDA graph). Returns
+    ``batch.outs``."""
     p = _params(kw.get("eta", 0.9), kw.get("idw_power", 1.0), kw.get("grad_threshold", 2),
                 kw.get("sign_rule", SIGN_SUM), kw.get("b2_rule", B2_SAME_Q))
     _check(load().qai_mitigate_batched(*batch._args(), ctypes.byref(p), batch.workspace.data_ptr(),
@@ -397,14 +398,14 @@ def mitigate_batched(batch: Batch, stream=None, **kw):
 
 
 def autotune_batched(batch: Batch, stream=None, **kw):
-    """Time the tile-shape and field-order candidates on ``batch`` and keep the
-    fastest per rank group; returns {rank: (rows_per_band, max_w, order, ms)}."""
+    """Time the stream-count and field-order candidates on ``batch`` and keep
+    the fastest per rank group; returns {rank: (streams, order, ms)}."""
     p = _params(kw.get("eta", 0.9), kw.get("idw_power", 1.0), kw.get("grad_threshold", 2),
                 kw.get("sign_rule", SIGN_SUM), kw.get("b2_rule", B2_SAME_Q))
     ch = (BatchChoice * 3)()
     _check(load().qai_autotune_batched(*batch._args(), ctypes.byref(p), batch.workspace.data_ptr(),
                                        batch.workspace.numel(), _stream(stream), ch))
-    return {c.rank: (c.rows_per_band, c.max_w, c.order, c.ms) for c in ch if c.rank}
+    return {c.rank: (c.streams, c.order, c.ms) for c in ch if c.rank}
 
 
 STATIC_MAX_POINTS = 2097152
