@@ -476,6 +476,15 @@ qai_status run_plain(const int32_t* d_q, float* d_out, const Shape& sh, const Me
 
 void qai::set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
 
+bool qai::chained_launches()
+{
+    static const bool on = [] {
+        const char* v = getenv("QAI_PDL");
+        return !(v && !strcmp(v, "0"));
+    }();
+    return on;
+}
+
 extern "C" {
 
 void qai_default_params(qai_params* p)

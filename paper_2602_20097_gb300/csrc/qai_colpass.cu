@@ -668,6 +668,7 @@ __device__ __forceinline__ void colpass_tile(const ColArgs& a, const int blk)
 template <int PHASE, int IN, bool FINAL, bool DEBUG, bool NARROW>
 __global__ void __launch_bounds__(512, IN == 2 ? 3 : 2) k_colpass(ColArgs a)
 {
+    wait_prior_grid();
     if (!a.gate) {
         colpass_tile<PHASE, IN, FINAL, DEBUG, NARROW>(a, blockIdx.x);
         return;
@@ -695,8 +696,7 @@ cudaError_t go(ColArgs& a, bool debug, bool narrow, dim3 grid, dim3 block, size_
         if (e != cudaSuccess) return e;
         dim3 g = grid;
         if (a.gate) g.x = std::min<unsigned>(g.x, resident_grid(kern, block, smem));
-        kern<<<g, block, smem, st>>>(a);
-        return cudaGetLastError();
+        return launch_chained(kern, g, block, smem, st, a);
     };
     if (debug) return narrow ? run(k_colpass<PHASE, IN, FINAL, true, true>)
                              : run(k_colpass<PHASE, IN, FINAL, true, false>);

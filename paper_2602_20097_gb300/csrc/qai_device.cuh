@@ -41,6 +41,13 @@ struct MethodArgs {
     int output_c;        // write the compensation C instead of D''
 };
 
+// Programmatic dependent launch: a kernel launched by launch_chained (see
+// qai_launch.h) may be scheduled while the kernel before it on the stream is
+// still finishing; it waits here, before it reads or writes any memory, for
+// that kernel to complete and its writes to be visible. Launched without the
+// attribute, the wait returns at once.
+__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Signed-point route of the second EDT (qai_signed.cu). Step E adds
 // C = S w eta eps: where S = 0 the output is D' whatever Dist2 is, and on B1
 // (Dist1 = 0) the weight is 1 whatever Dist2 is. Dist2 is needed only at the

@@ -8,6 +8,26 @@
 
 namespace qai {
 
+// Launches of the plain path's kernels with programmatic stream
+// serialization: the next kernel is scheduled while the previous one drains
+// (every such kernel starts with wait_prior_grid()). QAI_PDL=0 turns it off.
+bool chained_launches();
+template <class... P, class... A>
+cudaError_t launch_chained(void (*kern)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A&&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = chained_launches() ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<A&&>(args)...);
+}
+
 // Row pass (qai_rowpass.cu): phase 1 = step A + EDT-x of B1,
 // phase 2 = GetBoundary(S) + EDT-x of B2; final = the field is rank 1.
 int rowpass_warps(int nx);

@@ -91,30 +91,54 @@ constexpr int kSignedCta = 1024;
 constexpr int kQueryCta = 2048;
 
 // Step A on one warp-segment of 128 points (4 per lane) of row `row`.
+// The q values one lane needs for its four points of a segment: the row and
+// its four neighbour rows (zeros off the interior rows), and the value next
+// to the segment for the first lane (x0 - 1) and the last (x0 + 4).
+struct SegQ {
+    int c[4], yl[4], yr[4], zl[4], zr[4];
+    int edge;
+};
+
 template <int RANK, bool VEC>
-__device__ __forceinline__ void detect_segment(const LocalArgs& a, int row, int z, int y, int x0, int32_t* sbuf,
-                                               int* sn)
+__device__ __forceinline__ void load_segment(const LocalArgs& a, int row, int z, int y, int x0, SegQ& L)
 {
     const int lane = threadIdx.x & 31;
     const int nx = a.nx;
     const int rbase = row * nx;
     const int plane = a.ny * nx;
     const bool row_inner = y >= 1 && y <= a.ny - 2 && (RANK == 2 || (z >= 1 && z <= a.nz - 2));
-    int c[4], yl[4] = {0, 0, 0, 0}, yr[4] = {0, 0, 0, 0}, zl[4] = {0, 0, 0, 0}, zr[4] = {0, 0, 0, 0};
-    load4_i32(a.q + rbase, x0, nx, VEC, c);
+    load4_i32(a.q + rbase, x0, nx, VEC, L.c);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) L.yl[j] = L.yr[j] = L.zl[j] = L.zr[j] = 0;
+    if (row_inner) {
+        load4_i32(a.q + rbase - nx, x0, nx, VEC, L.yl);
+        load4_i32(a.q + rbase + nx, x0, nx, VEC, L.yr);
+        if (RANK == 3) {
+            load4_i32(a.q + rbase - plane, x0, nx, VEC, L.zl);
+            load4_i32(a.q + rbase + plane, x0, nx, VEC, L.zr);
+        }
+    }
+    L.edge = 0;
+    if (lane == 0 && x0 > 0) L.edge = __ldg(a.q + rbase + x0 - 1);
+    if (lane == 31 && x0 + 4 < nx) L.edge = __ldg(a.q + rbase + x0 + 4);
+}
+
+template <int RANK, bool VEC>
+__device__ __forceinline__ void detect_segment(const LocalArgs& a, int row, int z, int y, int x0, const SegQ& L,
+                                               int32_t* sbuf, int* sn)
+{
+    const int lane = threadIdx.x & 31;
+    const int nx = a.nx;
+    const int rbase = row * nx;
+    const bool row_inner = y >= 1 && y <= a.ny - 2 && (RANK == 2 || (z >= 1 && z <= a.nz - 2));
+    const int *c = L.c, *yl = L.yl, *yr = L.yr, *zl = L.zl, *zr = L.zr;
     int xm = __shfl_up_sync(kFull, c[3], 1);
     int xp = __shfl_down_sync(kFull, c[0], 1);
-    if (lane == 0) xm = x0 > 0 ? __ldg(a.q + rbase + x0 - 1) : 0;
-    if (lane == 31) xp = x0 + 4 < nx ? __ldg(a.q + rbase + x0 + 4) : 0;
+    if (lane == 0) xm = L.edge;
+    if (lane == 31) xp = L.edge;
     unsigned em = 0x3F3F3F3Fu;  // all equal: off the interior nothing is on B1
     unsigned codes = 0;         // 2-bit sign code of S_B per point (B1 points only)
     if (row_inner) {            // warp-uniform
-        load4_i32(a.q + rbase - nx, x0, nx, VEC, yl);
-        load4_i32(a.q + rbase + nx, x0, nx, VEC, yr);
-        if (RANK == 3) {
-            load4_i32(a.q + rbase - plane, x0, nx, VEC, zl);
-            load4_i32(a.q + rbase + plane, x0, nx, VEC, zr);
-        }
         // 32-bit sums are exact while every |q| < 2^27; OR of the raw values
         // is below 2^27 exactly when all are in [0, 2^27), the common case
         unsigned acc = (unsigned)xm | (unsigned)xp;
@@ -235,18 +259,24 @@ __device__ __forceinline__ void detect_segment(const LocalArgs& a, int row, int 
 template <int RANK, bool VEC>
 __global__ void __launch_bounds__(256, QAI_DETECT_MINB) k_detect(LocalArgs a)
 {
+    wait_prior_grid();
     __shared__ int32_t sbuf[kSignedCta];
     __shared__ int sn, sbase;
     if (threadIdx.x == 0) sn = 0;
     __syncthreads();
     const int rows = a.nz * a.ny;
     const int wstride = gridDim.x * (blockDim.x >> 5);
+    const int lx = 4 * (int)(threadIdx.x & 31);
     for (int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += wstride) {
         const int z = RANK == 3 ? row / a.ny : 0;
         const int y = row - z * a.ny;
-        for (int x0 = 4 * (threadIdx.x & 31); x0 - 4 * (int)(threadIdx.x & 31) < a.nx; x0 += 128)
-            detect_segment<RANK, VEC>(a, row, z, y, x0, sbuf, &sn);
+        for (int x0 = lx; x0 - lx < a.nx; x0 += 128) {
+            SegQ b;
+            load_segment<RANK, VEC>(a, row, z, y, x0, b);
+            detect_segment<RANK, VEC>(a, row, z, y, x0, b, sbuf, &sn);
+        }
     }
+
     __syncthreads();
     const int n = sn;
     if (threadIdx.x == 0) {
@@ -332,6 +362,7 @@ __device__ __forceinline__ uint32_t site_bytes(uint32_t w)
 template <int RANK, int WPL>
 __global__ void __launch_bounds__(256, QAI_NEAR_MINB) k_near(LocalArgs a)
 {
+    wait_prior_grid();
     constexpr int PPL = 4 * WPL;   // points per lane and step
     constexpr int STEP = 32 * PPL; // points per warp and step
     __shared__ Query qbuf[kQueryCta];
@@ -483,8 +514,7 @@ int one_wave(K kern, int waves = 1)
 cudaError_t launch_local_detect(const LocalArgs& a, cudaStream_t st)
 {
     auto run = [&](auto kern) {
-        kern<<<one_wave(kern, QAI_DETECT_WAVES), 256, 0, st>>>(a);
-        return cudaGetLastError();
+        return launch_chained(kern, dim3(one_wave(kern, QAI_DETECT_WAVES)), dim3(256), 0, st, a);
     };
     if (a.rank == 3) return a.vec ? run(k_detect<3, true>) : run(k_detect<3, false>);
     return a.vec ? run(k_detect<2, true>) : run(k_detect<2, false>);
@@ -495,8 +525,7 @@ cudaError_t launch_local_near(const LocalArgs& a, cudaStream_t st)
     auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
     const bool wide = (a.nx % 16 == 0) && al(a.eqm) && al(a.s);  // 16-byte rows
     auto run = [&](auto kern) {
-        kern<<<one_wave(kern), 256, 0, st>>>(a);
-        return cudaGetLastError();
+        return launch_chained(kern, dim3(one_wave(kern)), dim3(256), 0, st, a);
     };
     if (a.rank == 3) return wide ? run(k_near<3, 4>) : run(k_near<3, 1>);
     return wide ? run(k_near<2, 4>) : run(k_near<2, 1>);

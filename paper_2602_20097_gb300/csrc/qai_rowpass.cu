@@ -357,6 +357,7 @@ template <int PHASE, int RANK, bool FINAL, bool DEBUG, bool VEC>
 __global__ void __launch_bounds__(256) k_rowpass(RowArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
+    wait_prior_grid();
     // gated launches (signed-point route): run only when the flag is set
     if (a.gate && *static_cast<const volatile int*>(a.gate) == 0) return;
     // row pass 1 of the route starts its counters (not the local-EDT flag)
@@ -407,8 +408,7 @@ cudaError_t go(const RowArgs& a, bool debug, bool vec, dim3 grid, dim3 block, si
                 per = 1;
             g.x = std::min<unsigned>(g.x, (unsigned)(sms * per));
         }
-        kern<<<g, block, smem, st>>>(a);
-        return cudaGetLastError();
+        return launch_chained(kern, g, block, smem, st, a);
     };
     if (debug) return vec ? run(k_rowpass<PHASE, RANK, FINAL, true, true>)
                           : run(k_rowpass<PHASE, RANK, FINAL, true, false>);

@@ -154,6 +154,7 @@ constexpr int kMidBuf = 2048;  // per-CTA buffer of the first phase's leftovers
 template <int RANK>
 __global__ void __launch_bounds__(256) k_query(RouteArgs a)
 {
+    wait_prior_grid();
     volatile int* ctr = a.ctr;
     if (ctr[kCtrDense]) return;
     const int nq = ctr[kCtrQueries];
@@ -202,6 +203,7 @@ __global__ void __launch_bounds__(256) k_query(RouteArgs a)
 template <int RANK>
 __global__ void __launch_bounds__(256) k_query_mid(RouteArgs a)
 {
+    wait_prior_grid();
     volatile int* ctr = a.ctr;
     if (ctr[kCtrDense]) return;
     const int nm = min((int)ctr[kCtrMid], a.qcap);  // at most the queries
@@ -246,6 +248,7 @@ __global__ void __launch_bounds__(256) k_query_mid(RouteArgs a)
 template <int RANK>
 __global__ void __launch_bounds__(256) k_query_far(RouteArgs a)
 {
+    wait_prior_grid();
     volatile int* ctr = a.ctr;
     if (ctr[kCtrDense]) return;
     const int nf = ctr[kCtrFailed];
@@ -355,6 +358,7 @@ __device__ __forceinline__ void b2_from_field(const RouteArgs& a, const SiteBuf&
 template <int RANK>
 __global__ void __launch_bounds__(256) k_b2sites(RouteArgs a, int vec)
 {
+    wait_prior_grid();
     volatile int* ctr = a.ctr;
     if (ctr[kCtrDense] || ctr[kCtrUnresolved] == 0) return;
     __shared__ uint2 sbuf[kSiteBuf];
@@ -504,6 +508,7 @@ __device__ __forceinline__ void b2_from_field(const RouteArgs& a, const SiteBuf&
 constexpr int kBruteChunk = 1024;
 __global__ void __launch_bounds__(256) k_brute(RouteArgs a)
 {
+    wait_prior_grid();
     volatile int* ctr = a.ctr;
     if (ctr[kCtrDense] || ctr[kCtrUnresolved] == 0) return;
     const int nf = ctr[kCtrFailed];
@@ -568,38 +573,33 @@ int route_table_r2(int rank) { return rank == 2 ? kTableR2_2 : kTableR2; }
 
 cudaError_t launch_route_query(const RouteArgs& a, int blocks, cudaStream_t st)
 {
-    if (a.rank == 3) k_query<3><<<blocks, 256, 0, st>>>(a);
-    else k_query<2><<<blocks, 256, 0, st>>>(a);
-    return cudaGetLastError();
+    return a.rank == 3 ? launch_chained(k_query<3>, dim3(blocks), dim3(256), 0, st, a)
+                       : launch_chained(k_query<2>, dim3(blocks), dim3(256), 0, st, a);
 }
 
 cudaError_t launch_route_query_mid(const RouteArgs& a, int blocks, cudaStream_t st)
 {
-    if (a.rank == 3) k_query_mid<3><<<blocks, 256, 0, st>>>(a);
-    else k_query_mid<2><<<blocks, 256, 0, st>>>(a);
-    return cudaGetLastError();
+    return a.rank == 3 ? launch_chained(k_query_mid<3>, dim3(blocks), dim3(256), 0, st, a)
+                       : launch_chained(k_query_mid<2>, dim3(blocks), dim3(256), 0, st, a);
 }
 
 cudaError_t launch_route_query_far(const RouteArgs& a, int blocks, cudaStream_t st)
 {
-    if (a.rank == 3) k_query_far<3><<<blocks, 256, 0, st>>>(a);
-    else k_query_far<2><<<blocks, 256, 0, st>>>(a);
-    return cudaGetLastError();
+    return a.rank == 3 ? launch_chained(k_query_far<3>, dim3(blocks), dim3(256), 0, st, a)
+                       : launch_chained(k_query_far<2>, dim3(blocks), dim3(256), 0, st, a);
 }
 
 cudaError_t launch_route_b2sites(const RouteArgs& a, int blocks, cudaStream_t st)
 {
     auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 3) == 0; };
     const int vec = (a.nx % 4 == 0) && al(a.s) && al(a.eqm);
-    if (a.rank == 3) k_b2sites<3><<<blocks, 256, 0, st>>>(a, vec);
-    else k_b2sites<2><<<blocks, 256, 0, st>>>(a, vec);
-    return cudaGetLastError();
+    return a.rank == 3 ? launch_chained(k_b2sites<3>, dim3(blocks), dim3(256), 0, st, a, vec)
+                       : launch_chained(k_b2sites<2>, dim3(blocks), dim3(256), 0, st, a, vec);
 }
 
 cudaError_t launch_route_brute(const RouteArgs& a, int blocks, cudaStream_t st)
 {
-    k_brute<<<blocks, 256, 0, st>>>(a);
-    return cudaGetLastError();
+    return launch_chained(k_brute, dim3(blocks), dim3(256), 0, st, a);
 }
 
 }  // namespace qai
