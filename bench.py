@@ -502,6 +502,7 @@ def run_adjoint1024(args):
         _, gp = step()
         torch.cuda.synchronize()
         res[mode] = {"ms_fwd_bwd": ms, "ms_bwd": ms_b, "extra_bytes": torch.cuda.max_memory_allocated() - base,
+                     "bwd_workspace_bytes": qai.workspace_size_backward(shape, mode == "recompute"),
                      "grad_eta": float(gp[0]), "grad_p": float(gp[1]),
                      "bwd_kernels_ms": {k: v[1] / v[0] for k, v in kst.items()}}
         del saved, bws

@@ -152,25 +152,27 @@ qai_status qai_mitigate_host(const int32_t* h_q, float* h_out, int rank, const i
  * L with G = dL/dD'':
  *   dL/dD' = G,  dL/deta = sum G S w eps,
  *   dL/dp  = sum G S eta eps w (1 - w) (ln k2 - ln k1),  w = 1/(1 + (k1/k2)^p)
- * (dw/dp = 0 where k1 = 0, k2 = 0 or no B2 exists). Stored mode keeps Dist1,
- * Dist2 and S from the forward (9 bytes per point); recompute mode re-runs the
- * forward pipeline in the backward call and keeps nothing in between: for 2-D
- * and 3-D fields its last column pass sums the terms against G in place of
- * writing D'', so it needs no more device memory than the forward. */
+ * (dw/dp = 0 where k1 = 0, k2 = 0 or no B2 exists). Every term vanishes
+ * where S = 0. Stored mode keeps S, Dist1 and Dist2 from the forward (9 bytes
+ * per point; for 2-D and 3-D fields Dist1 and Dist2 only where S != 0 off B1,
+ * 0 elsewhere -- where S != 0 on B1, Dist1 = 0 and the weight is 1); recompute
+ * mode re-runs the forward in the backward call and keeps nothing in between
+ * (a plain forward for 2-D and 3-D fields, Dist2 recorded where it is
+ * computed). */
 
 /* Bytes of the saved state of the stored mode (256-byte aligned buffer). */
 qai_status qai_saved_size(int rank, const int64_t* dims, size_t* bytes);
 
 /* qai_mitigate that also fills d_saved (qai_saved_size bytes, device,
- * 256-byte aligned) with Dist1, Dist2 and S for qai_mitigate_backward. */
+ * 256-byte aligned) with the saved state of qai_mitigate_backward (above). */
 qai_status qai_mitigate_save(const int32_t* d_q, float* d_out, int rank, const int64_t* dims,
                              double eb, const qai_params* params, void* d_saved, void* d_ws,
                              size_t ws_bytes, cudaStream_t stream);
 
 /* Device workspace of qai_mitigate_backward: 32 KiB of block partial sums
- * (stored mode); with recompute != 0, 16 bytes per CTA of the last column
- * pass (at least 32 KiB) plus the forward workspace, and for 1-D fields two
- * more field-sized arrays. */
+ * (stored mode); with recompute != 0, the partial sums (at least 32 KiB) plus
+ * the forward workspace and two more 4-byte field-sized arrays (the forward's
+ * D'' and Dist2). */
 qai_status qai_workspace_size_backward(int rank, const int64_t* dims, int recompute, size_t* bytes);
 
 /* Adjoint of step E.

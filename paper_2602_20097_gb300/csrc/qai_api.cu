@@ -258,10 +258,16 @@ int final_pass_blocks(const Shape& sh)
 }
 
 // The launch sequence of Algorithm 4 on a validated shape.
+// d2rec (plain calls with the signed-point route only): Dist2 is recorded
+// there, by point, wherever S != 0 off B1 (the adjoint's forward).
+// saved (plain calls with the signed-point route only): the adjoint's saved
+// state is written there (S everywhere; Dist1 and Dist2 where S != 0 off B1,
+// 0 elsewhere); Dist2 is recorded straight into it.
 qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const qai::MethodArgs& m,
                         char* ws, const Layout& lay, cudaStream_t st, const qai_debug_out* dbg,
-                        GradSink* grad = nullptr)
+                        GradSink* grad = nullptr, int32_t* d2rec = nullptr, const qai_debug_out* saved = nullptr)
 {
+    if (saved) d2rec = saved->dist2;
     const double N = (double)sh.N;
     uint8_t* eqm = reinterpret_cast<uint8_t*>(ws + lay.eqm);
     int32_t* dist1 = reinterpret_cast<int32_t*>(ws + lay.dist1);
@@ -387,6 +393,7 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
         ra.fmin = reinterpret_cast<int32_t*>(ws + lay.fmin);
         ra.b2list = reinterpret_cast<int32_t*>(ws + lay.b2list); ra.b2cap = lay.b2cap;
         ra.max_r2 = route == Route::Brute ? -1 : qai::route_table_r2(sh.rank);
+        ra.d2rec = d2rec;
         ra.brute_budget = 1LL << 28;
         ra.m = m;
         if (route == Route::Dense) ra.qcap = -1;  // every count is over it: hand over at once
@@ -423,6 +430,7 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
         // mask bytes on B1 without clearing any other bit pattern's meaning
         c.col_count_in = local ? nullptr : cflag;
         c.b1_eqm = local ? eqm : nullptr;
+        c.d2rec = ctr ? d2rec : nullptr;
         c.route_ctr = ctr;
         c.gate = ctr ? ctr + qai::kCtrDense : nullptr;
     };
@@ -453,6 +461,12 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
         if (grad) return last_grad(cz, 4, "colpass2_z_grad");
         fuse_e(cz);
         if ((st_ = colpass(2, 4, true, cz, "colpass2_z_final", 4 + 4 + 1 + 4 + 4)) != QAI_OK) return st_;
+    }
+    if (saved && ctr) {
+        e = timed("save", N * 11.0, st, [&] {
+            return qai::launch_save_signed(sh.N, s, eqm, dist1, saved->s, saved->dist1, saved->dist2, st);
+        });
+        if (e != cudaSuccess) return cuda_fail(e, "saved state");
     }
     return QAI_OK;
 }
@@ -508,11 +522,15 @@ qai_status qai_workspace_size(int rank, const int64_t* dims, uint32_t flags, siz
     return QAI_OK;
 }
 
-qai_status qai_mitigate(const int32_t* d_q, float* d_out, int rank, const int64_t* dims, double eb,
-                        const qai_params* params, void* d_ws, size_t ws_bytes, cudaStream_t stream,
-                        const qai_debug_out* dbg)
+}  // extern "C"
+
+namespace {
+// qai_mitigate with the adjoint's saved state written on the way (saved: the
+// plain path with the signed-point route; see run_pipeline).
+qai_status mitigate_impl(const int32_t* d_q, float* d_out, int rank, const int64_t* dims, double eb,
+                         const qai_params* params, void* d_ws, size_t ws_bytes, cudaStream_t stream,
+                         const qai_debug_out* dbg, const qai_debug_out* saved)
 {
-    g_last_error.clear();
     if (!d_q || !d_out) return fail(QAI_ERR_INVALID_ARG, "d_q and d_out must be non-NULL");
     if (!(eb > 0.0) || !std::isfinite(eb)) return fail(QAI_ERR_INVALID_ARG, "eb must be finite and > 0");
     qai_params defaults;
@@ -535,9 +553,21 @@ qai_status qai_mitigate(const int32_t* d_q, float* d_out, int rank, const int64_
         if (e != cudaSuccess) return fail(QAI_ERR_OOM, "cudaMallocAsync(%zu): %s", lay.total, cudaGetErrorString(e));
         owned = true;
     }
-    s = run_pipeline(d_q, d_out, sh, method_args(p, eb), static_cast<char*>(d_ws), lay, stream, dbg);
+    s = run_pipeline(d_q, d_out, sh, method_args(p, eb), static_cast<char*>(d_ws), lay, stream, dbg, nullptr,
+                     nullptr, saved);
     if (owned) cudaFreeAsync(d_ws, stream);
     return s;
+}
+}  // namespace
+
+extern "C" {
+
+qai_status qai_mitigate(const int32_t* d_q, float* d_out, int rank, const int64_t* dims, double eb,
+                        const qai_params* params, void* d_ws, size_t ws_bytes, cudaStream_t stream,
+                        const qai_debug_out* dbg)
+{
+    g_last_error.clear();
+    return mitigate_impl(d_q, d_out, rank, dims, eb, params, d_ws, ws_bytes, stream, dbg, nullptr);
 }
 
 qai_status qai_route_counts(const void* d_ws, int rank, const int64_t* dims, int32_t* counts,
@@ -632,7 +662,12 @@ qai_status qai_mitigate_save(const int32_t* d_q, float* d_out, int rank, const i
     qai_status s = make_shape(rank, dims, &sh);
     if (s != QAI_OK) return s;
     const qai_debug_out d = saved_views(d_saved, sh.N);
-    return qai_mitigate(d_q, d_out, rank, dims, eb, params, d_ws, ws_bytes, stream, &d);
+    // rank 2 and 3: the plain path writes the saved state (Dist1 and Dist2
+    // where S != 0 off B1, the only points whose terms are not zero); rank 1
+    // (and the dense-only test route): the per-step maps of a debug call
+    if (sh.rank >= 2 && signed_route() != Route::Off)
+        return mitigate_impl(d_q, d_out, rank, dims, eb, params, d_ws, ws_bytes, stream, nullptr, &d);
+    return mitigate_impl(d_q, d_out, rank, dims, eb, params, d_ws, ws_bytes, stream, &d, nullptr);
 }
 
 }  // extern "C"
@@ -647,10 +682,10 @@ size_t backward_partials_bytes(const Shape& sh, bool recompute)
     return align256(2 * sizeof(double) * (size_t)n);
 }
 
-// Recompute mode: the forward workspace; rank 1 also holds Dist2 and D''.
+// Recompute mode: the forward workspace plus room for D'' and Dist2.
 size_t recompute_bytes(const Shape& sh)
 {
-    return layout_for(sh, 0).total + (sh.rank == 1 ? 2 * align256((size_t)sh.N * 4) : 0);
+    return layout_for(sh, 0).total + 2 * align256((size_t)sh.N * 4);
 }
 }  // namespace
 
@@ -703,9 +738,24 @@ qai_status qai_mitigate_backward(const int32_t* d_q, const float* d_grad_out, fl
         b.dist1 = v.dist1;
         b.dist2 = v.dist2;
         b.s = v.s;
+    } else if (sh.rank >= 2 && signed_route() != Route::Off) {
+        // recompute with the plain path: S everywhere, Dist1 and (recorded)
+        // Dist2 wherever S != 0 off B1 -- the only points whose terms are not
+        // zero; B1 points (Dist1 = 0) come from the mask bytes
+        const Layout lay = layout_for(sh, 0);
+        char* ws = static_cast<char*>(d_ws) + partials;
+        float* scratch_out = reinterpret_cast<float*>(ws + lay.total);
+        int32_t* d2rec = reinterpret_cast<int32_t*>(ws + lay.total + align256((size_t)sh.N * 4));
+        s = run_pipeline(d_q, scratch_out, sh, method_args(p, eb), ws, lay, stream, nullptr, nullptr, d2rec);
+        if (s != QAI_OK) return s;
+        b.s = reinterpret_cast<int8_t*>(ws + lay.s);
+        b.dist1 = reinterpret_cast<int32_t*>(ws + lay.dist1);
+        b.dist2 = d2rec;
+        b.b1_eqm = reinterpret_cast<uint8_t*>(ws + lay.eqm);
     } else if (sh.rank >= 2) {
-        // recompute Dist1, S and the EDT2 words with the forward pipeline; its
-        // last column pass sums the adjoint terms in place of writing D''
+        // the dense-only route: recompute Dist1, S and the EDT2 words with
+        // the dense pipeline; its last column pass sums the adjoint terms in
+        // place of writing D''
         const Layout lay = layout_for(sh, 0);
         GradSink g{d_grad_out, b.partials, 0};
         s = run_pipeline(d_q, nullptr, sh, method_args(p, eb), static_cast<char*>(d_ws) + partials, lay,

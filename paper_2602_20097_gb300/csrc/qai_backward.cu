@@ -29,14 +29,25 @@ __global__ void __launch_bounds__(256) k_backward(BackArgs a, int vec)
     GradAcc acc;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // Terms vanish where S = 0: Dist1, Dist2 (and G, unless dL/dD' is
+    // wanted) are read only for groups of points with some S != 0.
     if (vec) {
         const int64_t n4 = a.N >> 2;
         for (int64_t i = t0; i < n4; i += stride) {
-            const float4 g = __ldg(reinterpret_cast<const float4*>(a.grad_out) + i);
-            const int4 d1 = __ldg(reinterpret_cast<const int4*>(a.dist1) + i);
-            const int4 d2 = __ldg(reinterpret_cast<const int4*>(a.dist2) + i);
             const uint32_t sw = __ldg(reinterpret_cast<const uint32_t*>(a.s) + i);
+            float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (sw || a.grad_dprime) g = __ldg(reinterpret_cast<const float4*>(a.grad_out) + i);
             if (a.grad_dprime) reinterpret_cast<float4*>(a.grad_dprime)[i] = g;
+            if (!sw) continue;
+            int4 d1 = __ldg(reinterpret_cast<const int4*>(a.dist1) + i);
+            const int4 d2 = __ldg(reinterpret_cast<const int4*>(a.dist2) + i);
+            if (a.b1_eqm) {  // Dist1 = 0 on B1 (a clear equal-q bit)
+                const uint32_t ew = __ldg(reinterpret_cast<const uint32_t*>(a.b1_eqm) + i);
+                if ((ew & 0x3Fu) != 0x3Fu) d1.x = 0;
+                if (((ew >> 8) & 0x3Fu) != 0x3Fu) d1.y = 0;
+                if (((ew >> 16) & 0x3Fu) != 0x3Fu) d1.z = 0;
+                if (((ew >> 24) & 0x3Fu) != 0x3Fu) d1.w = 0;
+            }
             float te, tp;
             grad_terms(g.x, (int8_t)(sw & 0xFF), d1.x, d2.x, a.p, te, tp);
             acc.add(te, tp);
@@ -49,10 +60,14 @@ __global__ void __launch_bounds__(256) k_backward(BackArgs a, int vec)
         }
     } else {
         for (int64_t i = t0; i < a.N; i += stride) {
-            const float g = __ldg(a.grad_out + i);
+            const int sv = __ldg(a.s + i);
+            const float g = (sv || a.grad_dprime) ? __ldg(a.grad_out + i) : 0.f;
             if (a.grad_dprime) a.grad_dprime[i] = g;
+            if (!sv) continue;
+            int32_t d1 = __ldg(a.dist1 + i);
+            if (a.b1_eqm && (__ldg(a.b1_eqm + i) & 0x3Fu) != 0x3Fu) d1 = 0;
             float te, tp;
-            grad_terms(g, __ldg(a.s + i), __ldg(a.dist1 + i), __ldg(a.dist2 + i), a.p, te, tp);
+            grad_terms(g, sv, d1, __ldg(a.dist2 + i), a.p, te, tp);
             acc.add(te, tp);
         }
     }
@@ -101,7 +116,57 @@ __global__ void __launch_bounds__(256) k_backward_final(BackArgs a, int nblocks)
     a.grad_params[1] = tp * a.eta * a.eb;
 }
 
+// The adjoint's saved state: S; Dist1 and Dist2 where S != 0 off B1, 0
+// elsewhere (Dist2 was recorded into d2 at exactly those points). Four
+// points per thread where N and the arrays allow.
+__global__ void __launch_bounds__(256) k_save_signed(int64_t N, const int8_t* s, const uint8_t* eqm,
+                                                      const int32_t* dist1, int8_t* s_out, int32_t* d1_out,
+                                                      int32_t* d2, int vec)
+{
+    wait_prior_grid();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (vec) {
+        for (int64_t i = t0; i < (N >> 2); i += stride) {
+            const uint32_t sw = __ldg(reinterpret_cast<const uint32_t*>(s) + i);
+            const uint32_t ew = __ldg(reinterpret_cast<const uint32_t*>(eqm) + i);
+            reinterpret_cast<uint32_t*>(s_out)[i] = sw;
+            unsigned keep = 0;  // bit j: S != 0 off B1
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (((sw >> (8 * j)) & 0xFFu) && ((ew >> (8 * j)) & 0x3Fu) == 0x3Fu) keep |= 1u << j;
+            int4 o1 = make_int4(0, 0, 0, 0), o2 = make_int4(0, 0, 0, 0);
+            if (keep) {
+                const int4 a1 = __ldg(reinterpret_cast<const int4*>(dist1) + i);
+                const int4 a2 = reinterpret_cast<const int4*>(d2)[i];
+                o1 = make_int4(keep & 1u ? a1.x : 0, keep & 2u ? a1.y : 0, keep & 4u ? a1.z : 0, keep & 8u ? a1.w : 0);
+                o2 = make_int4(keep & 1u ? a2.x : 0, keep & 2u ? a2.y : 0, keep & 4u ? a2.z : 0, keep & 8u ? a2.w : 0);
+            }
+            reinterpret_cast<int4*>(d1_out)[i] = o1;
+            reinterpret_cast<int4*>(d2)[i] = o2;
+        }
+    } else {
+        for (int64_t i = t0; i < N; i += stride) {
+            const int sv = __ldg(s + i);
+            s_out[i] = (int8_t)sv;
+            const bool keep = sv && (__ldg(eqm + i) & 0x3Fu) == 0x3Fu;
+            d1_out[i] = keep ? __ldg(dist1 + i) : 0;
+            d2[i] = keep ? d2[i] : 0;
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_save_signed(int64_t N, const int8_t* s, const uint8_t* eqm, const int32_t* dist1,
+                               int8_t* s_out, int32_t* d1_out, int32_t* d2, cudaStream_t st)
+{
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    auto al = [](const void* p, int b) { return reinterpret_cast<uintptr_t>(p) % b == 0; };
+    const int vec = N % 4 == 0 && al(s, 4) && al(eqm, 4) && al(s_out, 4) && al(dist1, 16) && al(d1_out, 16) && al(d2, 16);
+    return launch_chained(k_save_signed, dim3(sms * 8), dim3(256), 0, st, N, s, eqm, dist1, s_out, d1_out, d2, vec);
+}
 
 cudaError_t launch_partials_sum(const double* partials, int nblocks, double eb, double eta,
                                 double* grad_params, cudaStream_t st)

@@ -153,8 +153,10 @@ __device__ __forceinline__ void emit_point(const ColArgs& a, int idx, int src, i
         } else {
             const int sv = __ldg(a.s_in + idx);
             // signed-point route: row pass 1 wrote every point with S = 0
-            if (!a.route_ctr || sv != 0)
+            if (!a.route_ctr || sv != 0) {
                 a.out[idx] = compensate(__ldg(a.q + idx), dist1_at(a, idx), d, sv, a.m);
+                if (a.d2rec) a.d2rec[idx] = d;
+            }
             if (DEBUG && a.dbg_dist2) a.dbg_dist2[idx] = d;
         }
     }
@@ -597,7 +599,10 @@ __device__ __forceinline__ void colpass_tile(const ColArgs& a, const int blk)
                 grad_terms(pg, ps, pd1, val, a.m.idw_power, te, tp);
                 acc.add(te, tp);
             } else {
-                if (!a.route_ctr || ps != 0) a.out[idx] = compensate(pq, pd1, val, ps, a.m);
+                if (!a.route_ctr || ps != 0) {
+                    a.out[idx] = compensate(pq, pd1, val, ps, a.m);
+                    if (a.d2rec) a.d2rec[idx] = val;
+                }
                 if (DEBUG && a.dbg_dist2) a.dbg_dist2[idx] = val;
             }
             pq = nq;

@@ -141,6 +141,7 @@ struct ColArgs {
     // a point is on B1 where its equal-q mask byte has a clear bit, and its
     // Dist1 is 0 there.
     const uint8_t* b1_eqm;
+    int32_t* d2rec;          // phase 2 final in the route: NULL, or Dist2 recorded at S != 0
     Query* qlist;
     int qcap;
     int32_t* slist;          // B1 points with S != 0 (linear indices), at most scap
@@ -166,6 +167,7 @@ struct RouteArgs {
     int fcap;
     int32_t* b2list;         // B2 sites as (x | y << 16, z) pairs
     int b2cap;
+    int32_t* d2rec;          // NULL, or Dist2 recorded here (by point) at every query
     int max_r2;              // local search radius^2 (<= the offset table's)
     long long brute_budget;  // largest failed x sites product searched by brute force
     MethodArgs m;
@@ -245,8 +247,9 @@ struct BackArgs {
     int64_t N;
     const float* grad_out;   // dL/dD''
     const int8_t* s;         // S
-    const int32_t* dist1;    // Dist1
-    const int32_t* dist2;    // Dist2
+    const int32_t* dist1;    // Dist1 (read only where S != 0)
+    const int32_t* dist2;    // Dist2 (idem)
+    const uint8_t* b1_eqm;   // NULL, or equal-q mask bytes: Dist1 = 0 where a bit is clear (B1)
     float* grad_dprime;      // dL/dD' (= dL/dD''), NULL to skip
     double* grad_params;     // [2]: dL/deta, dL/dp
     double* partials;        // [2 * kBackwardMaxBlocks] block totals (workspace)
@@ -324,9 +327,10 @@ __device__ __forceinline__ void grad_terms(float g, int s, int32_t d1, int32_t d
     w = d2 == 0 ? 0.0f : w;
     w = d1 == 0 ? 1.0f : w;
     dw = pinned ? 0.0f : dw;
-    const float gs = s > 0 ? g : (s < 0 ? -g : 0.0f);
-    te = gs * w;
-    tp = gs * dw;
+    // S = 0: no term, whatever d1 and d2 hold (they need not be written there)
+    const float gs = s > 0 ? g : -g;
+    te = s ? gs * w : 0.0f;
+    tp = s ? gs * dw : 0.0f;
 }
 
 }  // namespace qai

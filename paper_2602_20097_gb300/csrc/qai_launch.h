@@ -76,6 +76,11 @@ cudaError_t launch_local_near(const LocalArgs& a, cudaStream_t st);
 
 // Adjoint reduction of step E (qai_backward.cu).
 cudaError_t launch_backward(const BackArgs& a, cudaStream_t st);
+// The adjoint's saved state from a plain call's workspace: S; Dist1 and Dist2
+// where S != 0 off B1 (Dist1 from dist1, Dist2 already recorded in d2), 0
+// elsewhere.
+cudaError_t launch_save_signed(int64_t N, const int8_t* s, const uint8_t* eqm, const int32_t* dist1,
+                               int8_t* s_out, int32_t* d1_out, int32_t* d2, cudaStream_t st);
 // Adds the per-CTA partial sums of the fused adjoint pass in a fixed order.
 cudaError_t launch_partials_sum(const double* partials, int nblocks, double eb, double eta,
                                 double* grad_params, cudaStream_t st);

@@ -115,6 +115,13 @@ __device__ __forceinline__ float query_output(const RouteArgs& a, const Query& e
     return compensate(__ldg(a.q + e.idx), e.d1code >> 2, d2, sign_of_code(e.d1code & 3), a.m);
 }
 
+// The output of a query with its Dist2 (recorded too when asked).
+__device__ __forceinline__ void emit_query(const RouteArgs& a, const Query& e, int32_t d2)
+{
+    a.out[e.idx] = query_output(a, e, d2);
+    if (a.d2rec) a.d2rec[e.idx] = d2;
+}
+
 // Offset k of the table at query (x, y, z): a B2 site? r2 = its squared
 // length (r2 > max_r2, or k past the table: no).
 template <int RANK>
@@ -180,7 +187,7 @@ __global__ void __launch_bounds__(256) k_query(RouteArgs a)
         for (int k = n0 - 1; k >= 0; --k)
             if (hit[k]) found = r2[k];
         if (found >= 0) {
-            a.out[e.idx] = query_output(a, e, found);
+            emit_query(a, e, found);
         } else {
             const int k = atomicAdd(&mn, 1);
             if (k < kMidBuf) {
@@ -229,7 +236,7 @@ __global__ void __launch_bounds__(256) k_query_mid(RouteArgs a)
         }
         if (lane == 0) {
             if (found >= 0) {
-                a.out[e.idx] = query_output(a, e, found);
+                emit_query(a, e, found);
             } else {
                 const int k = atomicAdd(a.ctr + kCtrFailed, 1);
                 if (k < a.fcap) {
@@ -275,7 +282,7 @@ __global__ void __launch_bounds__(256) k_query_far(RouteArgs a)
             for (int w = 1; w < (int)(blockDim.x >> 5); ++w) best = min(best, sbest[w]);
             if (best != 0x7FFFFFFF) {
                 const int* tab = RANK == 3 ? c_off.off3 : c_off.off2;
-                a.out[e.idx] = query_output(a, e, (int)((unsigned)tab[best] >> 24));
+                emit_query(a, e, (int)((unsigned)tab[best] >> 24));
                 a.fmin[f] = -1;
             } else {
                 atomicAdd(a.ctr + kCtrUnresolved, 1);
@@ -562,7 +569,7 @@ __global__ void __launch_bounds__(256) k_brute(RouteArgs a)
             const int32_t d2 = *static_cast<volatile int32_t*>(a.fmin + f);
             if (d2 < 0) continue;  // the second shell search found it
             const Query e = a.flist[f];
-            a.out[e.idx] = query_output(a, e, d2);
+            emit_query(a, e, d2);
         }
     }
 }
