@@ -173,19 +173,19 @@ __device__ __forceinline__ void detect_segment(const LocalArgs& a, int row, int 
                 const int q0 = c[j];
                 const int l = j == 0 ? xm : c[j - 1];
                 const int r = j == 3 ? xp : c[j + 1];
-                unsigned mk = (l == q0 ? 0x10u : 0u) | (r == q0 ? 0x20u : 0u);
+                // differing-neighbour bits: min(n ^ q0, 1) is 1 exactly where
+                // n != q0; the mask byte keeps the complement (equal bits)
+                unsigned ne = umin((unsigned)(l ^ q0), 1u) * 0x10u + umin((unsigned)(r ^ q0), 1u) * 0x20u;
                 bool fast = (unsigned)(r - l + thm1) > lim;
-                mk |= (yl[j] == q0 ? 0x4u : 0u) | (yr[j] == q0 ? 0x8u : 0u);
+                ne += umin((unsigned)(yl[j] ^ q0), 1u) * 0x4u + umin((unsigned)(yr[j] ^ q0), 1u) * 0x8u;
                 fast |= (unsigned)(yr[j] - yl[j] + thm1) > lim;
                 if (RANK == 3) {
-                    mk |= (zl[j] == q0 ? 0x1u : 0u) | (zr[j] == q0 ? 0x2u : 0u);
+                    ne += umin((unsigned)(zl[j] ^ q0), 1u) + umin((unsigned)(zr[j] ^ q0), 1u) * 0x2u;
                     fast |= (unsigned)(zr[j] - zl[j] + thm1) > lim;
-                } else {
-                    mk |= 0x3u;
                 }
                 const bool inner = (inner_bits >> j) & 1u;
-                keep |= (inner && mk != 0x3Fu && !fast) ? 1u << j : 0u;
-                em |= (inner ? mk : 0x3Fu) << (8 * j);
+                keep |= (inner && ne != 0u && !fast) ? 1u << j : 0u;
+                em |= (0x3Fu ^ (inner ? ne : 0u)) << (8 * j);
             }
             if (__any_sync(kFull, keep != 0)) {
 #pragma unroll
