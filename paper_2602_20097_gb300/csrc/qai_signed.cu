@@ -156,7 +156,58 @@ __device__ __forceinline__ void coords(const RouteArgs& a, int idx, int& x, int&
 // kPhase1, one CTA per query over the rest of the table. The first hit in
 // table order has the smallest squared distance (the table is sorted by it).
 constexpr int kPhase1 = 160;
+static_assert(7 + 32 <= kPhase1, "the first round of the second phase lies inside it");
 constexpr int kMidBuf = 2048;  // per-CTA buffer of the first phase's leftovers
+
+// The first phase for a query p at least two steps inside every kept axis:
+// 0 if p is a B2 site, else 1 if one of its axis neighbours is, else -1 --
+// the offsets of squared length 0 and 1 in table order, read off the 25 S
+// values (13 in 2-D) around p, each loaded once, and the seven mask bytes.
+template <int RANK>
+__device__ __forceinline__ int near_b2(const RouteArgs& a, int64_t p)
+{
+    const int64_t X = 1, Y = a.nx, Z = (int64_t)a.ny * a.nx;
+    const int64_t st[6] = {-Z, Z, -Y, Y, -X, X};  // mask bit order z-, z+, y-, y+, x-, x+
+    const bool literal = a.m.b2_rule == 1;
+    auto has = [](int k) { return RANK == 3 || k >= 2; };
+    const int sc = __ldg(a.s + p);
+    int sn[6];
+    unsigned en[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        sn[k] = has(k) ? (int)__ldg(a.s + p + st[k]) : sc;
+        en[k] = has(k) && !literal ? (unsigned)__ldg(a.eqm + p + st[k]) : 0x3Fu;
+    }
+    const unsigned ec = literal ? 0x3Fu : (unsigned)__ldg(a.eqm + p);
+    // S two steps away along an axis, and one step along each of two axes
+    int s2[6], sd[6][6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        s2[k] = has(k) ? (int)__ldg(a.s + p + 2 * st[k]) : 0;
+#pragma unroll
+        for (int j = 0; j < 6; ++j)
+            sd[k][j] = has(k) && has(j) && (j >> 1) != (k >> 1) && j > k ? (int)__ldg(a.s + p + st[k] + st[j]) : 0;
+    }
+    unsigned d0 = 0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) d0 |= (unsigned)(sn[k] != sc) << k;
+    if (d0 & ec) return 0;
+    bool hit1 = false;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        if (!has(k)) continue;
+        // the neighbours of p + st[k]: p + 2 st[k], p itself, p + st[k] + st[j]
+        unsigned dk = 0;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            if (!has(j)) continue;
+            const int v = j == k ? s2[k] : (j == (k ^ 1) ? sc : (j > k ? sd[k][j] : sd[j][k]));
+            dk |= (unsigned)(v != sn[k]) << j;
+        }
+        hit1 |= (dk & en[k]) != 0;
+    }
+    return hit1 ? 1 : -1;
+}
 
 template <int RANK>
 __global__ void __launch_bounds__(256) k_query(RouteArgs a)
@@ -178,14 +229,20 @@ __global__ void __launch_bounds__(256) k_query(RouteArgs a)
         const Query e = a.qlist[i];
         int x, y, z;
         coords(a, e.idx, x, y, z);
-        bool hit[n0];
-        int r2[n0];
-#pragma unroll
-        for (int k = 0; k < n0; ++k) hit[k] = probe<RANK>(a, x, y, z, k, r2[k]);
         int found = -1;
+        const bool deep = a.max_r2 >= 1 && x >= 2 && x <= a.nx - 3 && y >= 2 && y <= a.ny - 3 &&
+                          (RANK == 2 || (z >= 2 && z <= a.nz - 3));
+        if (deep) {
+            found = near_b2<RANK>(a, e.idx);
+        } else {
+            bool hit[n0];
+            int r2[n0];
 #pragma unroll
-        for (int k = n0 - 1; k >= 0; --k)
-            if (hit[k]) found = r2[k];
+            for (int k = 0; k < n0; ++k) hit[k] = probe<RANK>(a, x, y, z, k, r2[k]);
+#pragma unroll
+            for (int k = n0 - 1; k >= 0; --k)
+                if (hit[k]) found = r2[k];
+        }
         if (found >= 0) {
             emit_query(a, e, found);
         } else {
@@ -205,8 +262,9 @@ __global__ void __launch_bounds__(256) k_query(RouteArgs a)
     for (int j = threadIdx.x; j < n && mbase + j < a.qcap; j += blockDim.x) a.mlist[mbase + j] = mbuf[j];
 }
 
-// Second phase: one warp per query, table offsets n0 .. kPhase1 (five per
-// lane, their loads in flight together).
+// Second phase: one warp per query, table offsets n0 .. kPhase1: first the
+// 32 nearest (where most of these queries end), then the other four per lane
+// with their loads in flight together.
 template <int RANK>
 __global__ void __launch_bounds__(256) k_query_mid(RouteArgs a)
 {
@@ -224,15 +282,21 @@ __global__ void __launch_bounds__(256) k_query_mid(RouteArgs a)
         int found = -1;
         int r2[5];
         bool hit[5];
+        hit[0] = probe<RANK>(a, x, y, z, n0 + lane, r2[0]);  // n0 + 31 < kPhase1
+        const unsigned h0 = __ballot_sync(kFull, hit[0]);
+        if (h0) {
+            found = __shfl_sync(kFull, r2[0], __ffs(h0) - 1);
+        } else {
 #pragma unroll
-        for (int u = 0; u < 5; ++u) {
-            const int k = n0 + 32 * u + lane;
-            hit[u] = k < kPhase1 && probe<RANK>(a, x, y, z, k, r2[u]);
-        }
+            for (int u = 1; u < 5; ++u) {
+                const int k = n0 + 32 * u + lane;
+                hit[u] = k < kPhase1 && probe<RANK>(a, x, y, z, k, r2[u]);
+            }
 #pragma unroll
-        for (int u = 0; u < 5; ++u) {
-            const unsigned h = __ballot_sync(kFull, hit[u]);
-            if (h && found < 0) found = __shfl_sync(kFull, r2[u], __ffs(h) - 1);
+            for (int u = 1; u < 5; ++u) {
+                const unsigned h = __ballot_sync(kFull, hit[u]);
+                if (h && found < 0) found = __shfl_sync(kFull, r2[u], __ffs(h) - 1);
+            }
         }
         if (lane == 0) {
             if (found >= 0) {
