@@ -52,23 +52,25 @@ def hbm_peak():
     return (float(p), "measured") if p else (6800.0, "fallback")
 
 
-def csrc_hash():
+def src_hash(files):
+    """Hash of the given repository files (paths relative to the root)."""
     h = hashlib.sha256()
-    d = os.path.join(ROOT, "paper_2602_20097_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        h.update(open(os.path.join(d, f), "rb").read())
+    for f in files:
+        h.update(f.encode() + b"\0")
+        h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, or
-    None when the kernels changed since it was captured."""
+    None when a source file that builds the captured kernels (listed in the
+    record) changed since it was captured."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         rec = json.load(open(path))
-    except OSError:
-        return None
-    if rec.get("csrc_hash") != csrc_hash():
+        if rec.get("src_hash") != src_hash(rec["sources"]):
+            return None
+    except (OSError, KeyError, ValueError):
         return None
     k = rec.get("kernels", {}).get(kernel)
     return None if k is None else k.get("dram_bytes_per_launch")
