@@ -356,17 +356,6 @@ __global__ void __launch_bounds__(256) k_query_far(RouteArgs a)
     }
 }
 
-__device__ __forceinline__ uint32_t load4_u8(const void* base, int64_t off, int x0, int nx, bool vec)
-{
-    const uint8_t* p = static_cast<const uint8_t*>(base) + off;
-    if (vec) return x0 < nx ? __ldg(reinterpret_cast<const uint32_t*>(p + x0)) : 0u;
-    uint32_t w = 0;
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-        if (x0 + j < nx) w |= (uint32_t)__ldg(p + x0 + j) << (8 * j);
-    return w;
-}
-
 // B2 sites found by one CTA, flushed to the global list with one atomic.
 constexpr int kSiteBuf = 1024;
 struct SiteBuf {
