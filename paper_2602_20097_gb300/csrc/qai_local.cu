@@ -353,18 +353,100 @@ __device__ __forceinline__ uint32_t site_bytes(uint32_t w)
     return r;
 }
 
-// S at every point, Dist1 where S != 0 off B1, and the queries. One warp per
-// row; a lane holds WPL words of four points (WPL = 4: one 128-bit load per
-// row when the rows are 16-byte multiples). The six neighbours at squared
-// distance 1 are tested for four points at once, byte-wise, in the tie order
-// z-, y-, x-, x+, y+, z+ (increasing linear index); the rare point with none
-// of them on B1 scans the rest of the table alone.
-template <int RANK, int WPL>
+// S bytes of the four points xk .. xk + 3 of row `row`, with Dist1 and the
+// query-list entries of those that are queries (S != 0 off B1). cw holds
+// their mask bytes, pw and nw the words either side (for the x - 1 and x + 1
+// neighbours), ylw .. zrw the words of the four neighbour rows (0x3F: no
+// point). The six neighbours at squared distance 1 are tested for the four
+// points at once, byte-wise, in the tie order z-, y-, x-, x+, y+, z+
+// (increasing linear index); a point with none of them on B1 scans the rest
+// of the table alone.
+template <int RANK>
+__device__ __forceinline__ uint32_t near_word(const LocalArgs& a, int row, int z, int y, int xk, uint32_t cw,
+                                              uint32_t pw, uint32_t nw, uint32_t ylw, uint32_t yrw, uint32_t zlw,
+                                              uint32_t zrw, Query* qbuf, int* qn, bool& fail)
+{
+    const uint32_t own = site_bytes(cw), pm = site_bytes(pw), nm = site_bytes(nw);
+    const uint32_t xlw = __byte_perm(pw, cw, 0x6543), xlm = __byte_perm(pm, own, 0x6543);  // x - 1
+    const uint32_t xrw = __byte_perm(cw, nw, 0x4321), xrm = __byte_perm(own, nm, 0x4321);  // x + 1
+    // the first B1 neighbour in tie order: select from the last to the first
+    uint32_t found = 0, pick = 0x3F3F3F3Fu;
+    auto take = [&](uint32_t w, uint32_t m) {
+        pick = (w & m) | (pick & ~m);
+        found |= m;
+    };
+    take(zrw, site_bytes(zrw));
+    take(yrw, site_bytes(yrw));
+    take(xrw, xrm);
+    take(xlw, xlm);
+    take(ylw, site_bytes(ylw));
+    take(zlw, site_bytes(zlw));
+    // codes: own on B1, else the neighbour's; Dist1 = 1 where resolved off
+    // B1 (bytes past the row end, and x - 1 of x = 0, read 0x3F)
+    const int nvalid = min(4, a.nx - xk);
+    const uint32_t valid = nvalid >= 4 ? 0xFFFFFFFFu : (nvalid <= 0 ? 0u : (1u << (8 * nvalid)) - 1u);
+    uint32_t cw2 = ((own & cw) | (~own & pick)) >> 6 & 0x03030303u;
+    const uint32_t need = ~own & ~found & valid;  // no site within r2 = 1: scan the table
+    uint32_t d1w = ~own & 0x01010101u;
+    if (need) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (!((need >> (8 * j)) & 0xFFu)) continue;
+            int r2;
+            unsigned code;
+            nearest_site<RANK>(a, row * a.nx + xk + j, z, y, xk + j, RANK == 3 ? 6 : 4, r2, code);
+            if (r2 < 0) {
+                fail = true;
+                r2 = 0;
+                code = 0;
+            }
+            cw2 = (cw2 & ~(0xFFu << (8 * j))) | code << (8 * j);
+            d1w = (d1w & ~(0xFFu << (8 * j))) | (uint32_t)r2 << (8 * j);
+        }
+    }
+    // S bytes: code 1 -> +1, code 2 -> -1
+    const uint32_t pos = cw2 & 0x01010101u, neg = (cw2 >> 1) & 0x01010101u;
+    // queries: S != 0 off B1
+    const uint32_t qmask = (pos | neg) & ~own & valid;
+    if (qmask) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (!((qmask >> (8 * j)) & 1u)) continue;
+            const int p = row * a.nx + xk + j;
+            const int r2 = (int)((d1w >> (8 * j)) & 0xFFu);
+            const unsigned code = (cw2 >> (8 * j)) & 3u;
+            a.dist1[p] = r2;
+            const Query qe{p, (r2 << 2) | (int)code};
+            const int kq = atomicAdd(qn, 1);
+            if (kq < kQueryCta) {
+                qbuf[kq] = qe;
+            } else {
+                const int g = atomicAdd(a.ctr + kCtrQueries, 1);
+                if (g < a.qcap) a.qlist[g] = qe;
+            }
+        }
+    }
+    return pos | (neg * 0xFFu);
+}
+
+// The CTA's queries to the global list (one atomic), and the flag of a point
+// with no B1 point within reach.
+__device__ __forceinline__ void near_flush(const LocalArgs& a, const Query* qbuf, const int* qn, int* qbase, bool fail)
+{
+    if (__any_sync(kFull, fail) && (threadIdx.x & 31) == 0) *static_cast<volatile int*>(a.ctr + kCtrLocalFail) = 1;
+    __syncthreads();
+    const int n = min(*qn, kQueryCta);
+    if (threadIdx.x == 0) *qbase = n > 0 ? atomicAdd(a.ctr + kCtrQueries, n) : 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n && *qbase + i < a.qcap; i += blockDim.x) a.qlist[*qbase + i] = qbuf[i];
+}
+
+// S at every point, Dist1 where S != 0 off B1, and the queries, for rows of
+// any length: one warp per row, four points per lane and step.
+template <int RANK>
 __global__ void __launch_bounds__(256, QAI_NEAR_MINB) k_near(LocalArgs a)
 {
     wait_prior_grid();
-    constexpr int PPL = 4 * WPL;   // points per lane and step
-    constexpr int STEP = 32 * PPL; // points per warp and step
     __shared__ Query qbuf[kQueryCta];
     __shared__ int qn, qbase;
     if (threadIdx.x == 0) qn = 0;
@@ -374,127 +456,112 @@ __global__ void __launch_bounds__(256, QAI_NEAR_MINB) k_near(LocalArgs a)
     const int plane = a.ny * a.nx;
     const int wstride = gridDim.x * (blockDim.x >> 5);
     bool fail = false;
-    // WPL words of a row at x0 (0x3F: no point)
-    auto load_row = [&](const uint8_t* row, int x0) -> uint4 {
-        if (WPL == 4)
-            return x0 < a.nx ? __ldg(reinterpret_cast<const uint4*>(row + x0))
-                             : make_uint4(0x3F3F3F3Fu, 0x3F3F3F3Fu, 0x3F3F3F3Fu, 0x3F3F3F3Fu);
-        return make_uint4(load4_em(row, x0, a.nx, false), 0u, 0u, 0u);
-    };
-    auto word = [](const uint4& v, int k) -> uint32_t { return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w)); };
-    const uint4 none = make_uint4(0x3F3F3F3Fu, 0x3F3F3F3Fu, 0x3F3F3F3Fu, 0x3F3F3F3Fu);
+    const uint32_t none = 0x3F3F3F3Fu;
     for (int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += wstride) {
         const int z = RANK == 3 ? row / a.ny : 0;
         const int y = row - z * a.ny;
         const uint8_t* er = a.eqm + (int64_t)row * a.nx;
         int8_t* sr = a.s + (int64_t)row * a.nx;
-        uint32_t carry = 0x3F3F3F3Fu;  // last word of the previous step (its byte 3 is x - 1 of byte 0)
-        for (int xs = 0; xs < a.nx; xs += STEP) {
-            const int x0 = xs + PPL * lane;
-            // words of the row and of its four neighbour rows (absent: no B1 point)
-            const uint4 c = load_row(er, x0);
-            const uint4 yl = y > 0 ? load_row(er - a.nx, x0) : none;
-            const uint4 yr = y < a.ny - 1 ? load_row(er + a.nx, x0) : none;
-            const uint4 zl = RANK == 3 && z > 0 ? load_row(er - plane, x0) : none;
-            const uint4 zr = RANK == 3 && z < a.nz - 1 ? load_row(er + plane, x0) : none;
-            uint32_t prev = __shfl_up_sync(kFull, word(c, WPL - 1), 1);
-            uint32_t next = __shfl_down_sync(kFull, c.x, 1);
-            const uint32_t last = __shfl_sync(kFull, word(c, WPL - 1), 31);
+        uint32_t carry = none;  // the word of the previous step (its byte 3 is x - 1 of byte 0)
+        for (int xs = 0; xs < a.nx; xs += 128) {
+            const int x0 = xs + 4 * lane;
+            const uint32_t cw = load4_em(er, x0, a.nx, false);
+            const uint32_t ylw = y > 0 ? load4_em(er - a.nx, x0, a.nx, false) : none;
+            const uint32_t yrw = y < a.ny - 1 ? load4_em(er + a.nx, x0, a.nx, false) : none;
+            const uint32_t zlw = RANK == 3 && z > 0 ? load4_em(er - plane, x0, a.nx, false) : none;
+            const uint32_t zrw = RANK == 3 && z < a.nz - 1 ? load4_em(er + plane, x0, a.nx, false) : none;
+            uint32_t prev = __shfl_up_sync(kFull, cw, 1);
+            uint32_t next = __shfl_down_sync(kFull, cw, 1);
+            const uint32_t last = __shfl_sync(kFull, cw, 31);
             if (lane == 0) prev = carry;
-            if (lane == 31) next = x0 + PPL < a.nx ? (uint32_t)__ldg(er + x0 + PPL) : 0x3Fu;
+            if (lane == 31) next = x0 + 4 < a.nx ? (uint32_t)__ldg(er + x0 + 4) : 0x3Fu;
             carry = last;
-            // site masks of the row's words (and of the words either side);
-            // those of the x - 1 and x + 1 neighbours are byte shifts of them
-            const uint32_t mprev = site_bytes(prev), mnext = site_bytes(next);
-            uint32_t mown[4];
+            const uint32_t sw = near_word<RANK>(a, row, z, y, x0, cw, prev, next, ylw, yrw, zlw, zrw, qbuf, &qn, fail);
 #pragma unroll
-            for (int k = 0; k < WPL; ++k) mown[k] = site_bytes(word(c, k));
-            uint32_t sw[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-            for (int k = 0; k < WPL; ++k) {
-                const int xk = x0 + 4 * k;
-                const uint32_t cw = word(c, k);
-                const uint32_t pw = k == 0 ? prev : word(c, k - 1), nw = k == WPL - 1 ? next : word(c, k + 1);
-                const uint32_t pm = k == 0 ? mprev : mown[k > 0 ? k - 1 : 0];
-                const uint32_t nm = k == WPL - 1 ? mnext : mown[k + 1 < WPL ? k + 1 : 0];
-                const uint32_t xlw = __byte_perm(pw, cw, 0x6543), xlm = __byte_perm(pm, mown[k], 0x6543);  // x - 1
-                const uint32_t xrw = __byte_perm(cw, nw, 0x4321), xrm = __byte_perm(mown[k], nm, 0x4321);  // x + 1
-                // the first B1 neighbour in tie order: select from the last to the first
-                const uint32_t own = mown[k];
-                uint32_t found = 0, pick = 0x3F3F3F3Fu;
-                auto take = [&](uint32_t w, uint32_t m) {
-                    pick = (w & m) | (pick & ~m);
-                    found |= m;
-                };
-                take(word(zr, k), site_bytes(word(zr, k)));
-                take(word(yr, k), site_bytes(word(yr, k)));
-                take(xrw, xrm);
-                take(xlw, xlm);
-                take(word(yl, k), site_bytes(word(yl, k)));
-                take(word(zl, k), site_bytes(word(zl, k)));
-                // codes: own on B1, else the neighbour's; Dist1 = 1 where resolved
-                // off B1 (bytes past the row end, and x - 1 of x = 0, read 0x3F)
-                const int nvalid = min(4, a.nx - xk);
-                const uint32_t valid = nvalid >= 4 ? 0xFFFFFFFFu : (nvalid <= 0 ? 0u : (1u << (8 * nvalid)) - 1u);
-                uint32_t cw2 = ((own & cw) | (~own & pick)) >> 6 & 0x03030303u;
-                const uint32_t need = ~own & ~found & valid;  // no site within r2 = 1: scan the table
-                uint32_t d1w = ~own & 0x01010101u;
-                if (need) {
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        if (!((need >> (8 * j)) & 0xFFu)) continue;
-                        int r2;
-                        unsigned code;
-                        nearest_site<RANK>(a, row * a.nx + xk + j, z, y, xk + j, RANK == 3 ? 6 : 4, r2, code);
-                        if (r2 < 0) {
-                            fail = true;
-                            r2 = 0;
-                            code = 0;
-                        }
-                        cw2 = (cw2 & ~(0xFFu << (8 * j))) | code << (8 * j);
-                        d1w = (d1w & ~(0xFFu << (8 * j))) | (uint32_t)r2 << (8 * j);
-                    }
-                }
-                // S bytes: code 1 -> +1, code 2 -> -1
-                const uint32_t pos = cw2 & 0x01010101u, neg = (cw2 >> 1) & 0x01010101u;
-                sw[k] = pos | (neg * 0xFFu);
-                // queries: S != 0 off B1
-                const uint32_t qmask = (pos | neg) & ~own & valid;
-                if (qmask) {
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        if (!((qmask >> (8 * j)) & 1u)) continue;
-                        const int p = row * a.nx + xk + j;
-                        const int r2 = (int)((d1w >> (8 * j)) & 0xFFu);
-                        const unsigned code = (cw2 >> (8 * j)) & 3u;
-                        a.dist1[p] = r2;
-                        const Query qe{p, (r2 << 2) | (int)code};
-                        const int kq = atomicAdd(&qn, 1);
-                        if (kq < kQueryCta) {
-                            qbuf[kq] = qe;
-                        } else {
-                            const int g = atomicAdd(a.ctr + kCtrQueries, 1);
-                            if (g < a.qcap) a.qlist[g] = qe;
-                        }
-                    }
-                }
-            }
-            if (WPL == 4) {
-                if (x0 < a.nx)
-                    *reinterpret_cast<uint4*>(sr + x0) = make_uint4(sw[0], sw[1], sw[2], sw[3]);
-            } else {
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (x0 + j < a.nx) sr[x0 + j] = (int8_t)(sw[0] >> (8 * j));
-            }
+            for (int j = 0; j < 4; ++j)
+                if (x0 + j < a.nx) sr[x0 + j] = (int8_t)(sw >> (8 * j));
         }
     }
-    if (__any_sync(kFull, fail) && lane == 0) *static_cast<volatile int*>(a.ctr + kCtrLocalFail) = 1;
+    near_flush(a, qbuf, &qn, &qbase, fail);
+}
+
+// The same for rows of 16-byte multiples, sparse in the points off B1 (most
+// points of a field with a dense B1 are on it and keep their own sign). A
+// lane reads 16 mask bytes of the row per step (one 128-bit load) and writes
+// the S of its B1 points; the words holding a point off B1 are gathered
+// across the warp (a ballot per word position) and dealt one per lane to
+// near_word, which reads the neighbour words it needs. The S words meet in
+// shared memory before the lane's 128-bit store.
+template <int RANK>
+__global__ void __launch_bounds__(256, QAI_NEAR_MINB) k_near_sparse(LocalArgs a)
+{
+    wait_prior_grid();
+    __shared__ Query qbuf[kQueryCta];
+    __shared__ uint32_t swb[8][4 * 32];
+    __shared__ int qn, qbase;
+    if (threadIdx.x == 0) qn = 0;
     __syncthreads();
-    const int n = min(qn, kQueryCta);
-    if (threadIdx.x == 0) qbase = n > 0 ? atomicAdd(a.ctr + kCtrQueries, n) : 0;
-    __syncthreads();
-    for (int i = threadIdx.x; i < n && qbase + i < a.qcap; i += blockDim.x) a.qlist[qbase + i] = qbuf[i];
+    const int lane = threadIdx.x & 31;
+    uint32_t* sw = swb[threadIdx.x >> 5];  // word k of lane l at [32 k + l]
+    const int rows = a.nz * a.ny;
+    const int plane = a.ny * a.nx;
+    const int wstride = gridDim.x * (blockDim.x >> 5);
+    bool fail = false;
+    const uint32_t none = 0x3F3F3F3Fu;
+    for (int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += wstride) {
+        const int z = RANK == 3 ? row / a.ny : 0;
+        const int y = row - z * a.ny;
+        const uint8_t* er = a.eqm + (int64_t)row * a.nx;
+        int8_t* sr = a.s + (int64_t)row * a.nx;
+        for (int xs = 0; xs < a.nx; xs += 512) {
+            const int x0 = xs + 16 * lane;
+            const bool in = x0 < a.nx;  // rows are 16-byte multiples: four words or none
+            const uint4 c = in ? __ldg(reinterpret_cast<const uint4*>(er + x0)) : make_uint4(none, none, none, none);
+            unsigned off[4];  // word position k: the lanes whose word k holds a point off B1
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t cw = k == 0 ? c.x : (k == 1 ? c.y : (k == 2 ? c.z : c.w));
+                const uint32_t own = site_bytes(cw);
+                const uint32_t cw2 = (own & cw) >> 6 & 0x03030303u;  // B1 points: their own code
+                const uint32_t pos = cw2 & 0x01010101u, neg = (cw2 >> 1) & 0x01010101u;
+                sw[32 * k + lane] = pos | (neg * 0xFFu);
+                off[k] = __ballot_sync(kFull, in && own != 0xFFFFFFFFu);
+            }
+            const int n0 = __popc(off[0]), n1 = __popc(off[1]), n2 = __popc(off[2]), n3 = __popc(off[3]);
+            const int total = n0 + n1 + n2 + n3;
+            __syncwarp();
+            for (int e = lane; e - lane < total; e += 32) {
+                if (e >= total) continue;
+                int k, r;
+                if (e < n0) {
+                    k = 0; r = e;
+                } else if (e < n0 + n1) {
+                    k = 1; r = e - n0;
+                } else if (e < n0 + n1 + n2) {
+                    k = 2; r = e - n0 - n1;
+                } else {
+                    k = 3; r = e - n0 - n1 - n2;
+                }
+                const unsigned bk = k == 0 ? off[0] : (k == 1 ? off[1] : (k == 2 ? off[2] : off[3]));
+                const int src = (int)__fns(bk, 0, r + 1);  // the lane that holds the word
+                const int xk = xs + 16 * src + 4 * k;
+                auto w32 = [&](const uint8_t* rp) { return __ldg(reinterpret_cast<const uint32_t*>(rp + xk)); };
+                const uint32_t cw = w32(er);
+                const uint32_t pw = xk >= 4 ? w32(er - 4) : none;
+                const uint32_t nw = xk + 4 < a.nx ? w32(er + 4) : none;
+                const uint32_t ylw = y > 0 ? w32(er - a.nx) : none;
+                const uint32_t yrw = y < a.ny - 1 ? w32(er + a.nx) : none;
+                const uint32_t zlw = RANK == 3 && z > 0 ? w32(er - plane) : none;
+                const uint32_t zrw = RANK == 3 && z < a.nz - 1 ? w32(er + plane) : none;
+                sw[32 * k + src] = near_word<RANK>(a, row, z, y, xk, cw, pw, nw, ylw, yrw, zlw, zrw, qbuf, &qn, fail);
+            }
+            __syncwarp();
+            if (in)
+                *reinterpret_cast<uint4*>(sr + x0) = make_uint4(sw[lane], sw[32 + lane], sw[64 + lane], sw[96 + lane]);
+            __syncwarp();
+        }
+    }
+    near_flush(a, qbuf, &qn, &qbase, fail);
 }
 
 }  // namespace
@@ -527,8 +594,8 @@ cudaError_t launch_local_near(const LocalArgs& a, cudaStream_t st)
     auto run = [&](auto kern) {
         return launch_chained(kern, dim3(one_wave(kern)), dim3(256), 0, st, a);
     };
-    if (a.rank == 3) return wide ? run(k_near<3, 4>) : run(k_near<3, 1>);
-    return wide ? run(k_near<2, 4>) : run(k_near<2, 1>);
+    if (a.rank == 3) return wide ? run(k_near_sparse<3>) : run(k_near<3>);
+    return wide ? run(k_near_sparse<2>) : run(k_near<2>);
 }
 
 }  // namespace qai
