@@ -21,7 +21,10 @@
 //             -- and takes the first B1 point it meets: Dist1 and I1 exactly,
 //             since any point outside that ball is at squared distance >= 9.
 //             It writes S everywhere, Dist1 where S != 0, and lists the
-//             queries of the second EDT (S != 0 off B1).
+//             queries of the second EDT (S != 0 off B1). k_near_sparse does
+//             the same for rows of 16-byte multiples, with the search run
+//             only on the 4-point words that hold a point off B1, gathered
+//             across the warp.
 //
 // A point with no B1 point within that ball sets kCtrLocalFail; the separable
 // first EDT (row pass 1, column passes 1) then runs and rewrites all of it.
