@@ -158,7 +158,7 @@ def quality_gain(x, q, eb, out):
     D'' against x, from the library's GPU quality kernels (untimed)."""
     from paper_2602_20097_gb300 import qai
     xf = x.float().contiguous()
-    dp = (q.double() * (2 * eb)).float()
+    dp = qai.dequantize(q, eb)
     a = qai.quality(xf, dp)
     b = qai.quality(xf, out.contiguous())
     return {"psnr_dprime_db": a["psnr"], "psnr_mitigated_db": b["psnr"], "psnr_gain_db": b["psnr"] - a["psnr"],
@@ -216,8 +216,7 @@ def run_reference(args):
 def run_e2e(q, eb, dev, stream, steps, barrier, world, ws):
     """Same metric through qai_mitigate_host: H2D of q and D2H of D'' timed."""
     import torch
-    import torch.distributed as dist
-    from paper_2602_20097_gb300 import qai
+    from paper_2602_20097_gb300 import qai, replicas
     qh = q.cpu().pin_memory()
     oh = torch.empty(tuple(q.shape), dtype=torch.float32).pin_memory()
     del ws
@@ -231,16 +230,14 @@ def run_e2e(q, eb, dev, stream, steps, barrier, world, ws):
         qai.mitigate_host(qh, eb, out_host=oh, workspace=wsh)
     e1.record(stream)
     barrier()
-    t = torch.tensor([e0.elapsed_time(e1) / steps], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return q.numel() * 4 * world / (float(t.item()) * 1e-3) / 1e9
+    ms_max = replicas.max_over_ranks(e0.elapsed_time(e1) / steps, device=dev)
+    return replicas.whole_job_gbs(q.numel() * 4, world, ms_max)
 
 
 def run_qai(args):
     import torch
     import torch.distributed as dist
-    from paper_2602_20097_gb300 import qai
+    from paper_2602_20097_gb300 import qai, replicas
 
     world, rank, local = dist_env()
     if world > 1:
@@ -299,11 +296,8 @@ def run_qai(args):
     qai.profile_enable(False)
     qai.profile_select(None)
     ms = ev0.elapsed_time(ev1) / args.steps
-    t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = N * 4 * world / (ms_max * 1e-3) / 1e9
+    ms_max = replicas.max_over_ranks(ms, device=dev)
+    value = replicas.whole_job_gbs(N * 4, world, ms_max)
 
     route = qai.route_counts(ws, tuple(q.shape))  # how the second EDT went (signed-point route)
 
@@ -354,9 +348,19 @@ def run_qai(args):
         qs = q[:min(SAMPLE_Z, q.shape[0])].cpu().numpy()
         import oracle
         runs, el = time_oracle(qs, eb)
-        cpu = {"value": qs.size * 4 * runs / el / 1e9, "unit": "GB/s", "cores": oracle.threads(),
+        cores = oracle.threads()
+        cpu = {"value": qs.size * 4 * runs / el / 1e9, "unit": "GB/s", "cores": cores,
                "kind": "oracle",
                "sample": f"first {SAMPLE_Z} z-planes of the bench field ({SAMPLE_Z}x512x512), {runs} runs, {el:.1f} s"}
+        # the same oracle on one thread, on a quarter of that slab
+        q1 = qs[:max(1, qs.shape[0] // 4)]
+        oracle.set_threads(1)
+        try:
+            r1, el1 = time_oracle(q1, eb, min_s=2.0, max_s=15.0)
+        finally:
+            oracle.set_threads(cores)
+        cpu["single_thread"] = {"value": q1.size * 4 * r1 / el1 / 1e9, "unit": "GB/s", "cores": 1,
+                                "sample": f"first {q1.shape[0]} z-planes of the bench field, {r1} runs, {el1:.1f} s"}
 
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,

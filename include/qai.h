@@ -62,10 +62,28 @@ typedef struct {
     int32_t b2_rule;         /* Algorithm 3 GetBoundary(S): 0 = a neighbour with
                                 the same q and a different S (default);
                                 1 = any neighbour with a different S               */
-    uint32_t flags;          /* 0, or QAI_FLAG_OUTPUT_C                            */
+    uint32_t flags;          /* 0, or QAI_FLAG_OUTPUT_C, optionally with one route
+                                selection bit below                                */
 } qai_params;
 
 #define QAI_FLAG_OUTPUT_C 1u  /* write the compensation C (step E) instead of D''  */
+
+/* Route selection for rank-2 and rank-3 plain calls. These bits exist for
+ * testing and measurement: every route computes the same Dist1, I1, S and
+ * Dist2 where they reach the output, so the output bits do not depend on them
+ * (qai_route_counts reports which route ran). At most one QAI_FLAG_EDT2_* bit.
+ *  QAI_FLAG_EDT2_DENSE       the dense second EDT over the whole field (the
+ *                            separable passes of Algorithm 1), no route
+ *  QAI_FLAG_EDT2_HANDOVER    the route's kernels run and hand every field
+ *                            over to the dense second EDT
+ *  QAI_FLAG_EDT2_LIST        no shell search: every point that needs Dist2
+ *                            takes the search over the listed B2 sites
+ *  QAI_FLAG_EDT1_SEPARABLE   the first EDT by the separable passes alone,
+ *                            without the bounded nearest-site search first */
+#define QAI_FLAG_EDT2_DENSE 0x10u
+#define QAI_FLAG_EDT2_HANDOVER 0x20u
+#define QAI_FLAG_EDT2_LIST 0x40u
+#define QAI_FLAG_EDT1_SEPARABLE 0x80u
 
 /* Optional per-step outputs of Algorithm 4 (debug and parity checking).
  * Each pointer is a device array of N elements, or NULL to skip it.
@@ -168,6 +186,21 @@ qai_status qai_saved_size(int rank, const int64_t* dims, size_t* bytes);
 qai_status qai_mitigate_save(const int32_t* d_q, float* d_out, int rank, const int64_t* dims,
                              double eb, const qai_params* params, void* d_saved, void* d_ws,
                              size_t ws_bytes, cudaStream_t stream);
+
+/* D' = 2 q eps (Eq. 1, the dequantized field) in fp32, computed as every
+ * kernel of the library computes it: float(q) * float(2 eps), rounded once.
+ *  d_q   int32[n] indices, device;  d_out  float[n], device;  n >= 0. */
+qai_status qai_dequantize(const int32_t* d_q, float* d_out, int64_t n, double eb, cudaStream_t stream);
+
+/* Algorithm 4 with the dequantized field given: d_out = d_dprime + C, C the
+ * compensation of step E computed from d_q (the differentiable form, where
+ * D' is an independent input: dL/dD' = dL/dD''). d_dprime is float[N],
+ * device; with d_dprime = 2 q eps the result equals qai_mitigate's to one
+ * fp32 rounding. d_saved: NULL, or the stored-mode saved state to fill, as
+ * qai_mitigate_save. Other arguments as qai_mitigate_save. */
+qai_status qai_mitigate_add(const int32_t* d_q, const float* d_dprime, float* d_out, int rank,
+                            const int64_t* dims, double eb, const qai_params* params, void* d_saved,
+                            void* d_ws, size_t ws_bytes, cudaStream_t stream);
 
 /* Device workspace of qai_mitigate_backward: 32 KiB of block partial sums
  * (stored mode); with recompute != 0, the partial sums (at least 32 KiB) plus
@@ -287,20 +320,26 @@ qai_status qai_quality(const float* d_x, const float* d_y, int rank, const int64
  *
  * Instead of a workspace it uses one scratch array compiled into the library
  * (a 256-byte aligned __device__ array of 13.5 * QAI_STATIC_MAX_POINTS +
- * 1 MiB bytes, about 28 MiB). Every GPU that loads the library holds that array
- * until the process exits. The call itself allocates nothing: no cudaMalloc,
- * no cudaFree, no library routine that allocates.
+ * 1 MiB bytes, about 28 MiB). Every GPU on which the library's code is loaded
+ * holds that array until the process exits.
+ *
+ * First call on a device: it looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current. Under CUDA's lazy module
+ * loading (the default) that lookup loads the array's module on the device,
+ * which commits the array's memory there; if that fails (out of memory, for
+ * one) the call returns QAI_ERR_CUDA. So make the first call on each device
+ * outside any region that must not allocate, and before any stream capture.
+ * Later calls allocate nothing: no cudaMalloc, no cudaFree, no library
+ * routine that allocates.
  *  d_q, d_out, rank, dims, eb, params, stream: as for qai_mitigate (the
  *          caller still passes the input and the output buffers).
  * Fields larger than QAI_STATIC_MAX_POINTS points return QAI_ERR_SHAPE before
- * any CUDA call. The first call on each device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture. Every call shares the array, which keeps
- * the last call's contents; the call's first kernel clears the few counters
- * that must start at zero, and every other slice is written before it is
- * read. Calls whose work overlaps on the GPU (two streams, or two host threads)
- * race on the array and corrupt each other's results: serialise them, for
- * example on one stream. No per-step (debug) outputs. */
+ * any CUDA call. Every call shares the array, which keeps the last call's
+ * contents; the call's first kernel clears the few counters that must start
+ * at zero, and every other slice is written before it is read. Calls whose
+ * work overlaps on the GPU (two streams, or two host threads) race on the
+ * array and corrupt each other's results: serialise them, for example on one
+ * stream. No per-step (debug) outputs. */
 qai_status qai_mitigate_static(const int32_t* d_q, float* d_out, int rank, const int64_t* dims,
                                double eb, const qai_params* params, cudaStream_t stream);
 

@@ -72,6 +72,8 @@ def _load():
                                                      ctypes.POINTER(_Params), P, P]
         lib.qai_oracle_boundary_and_sign.restype = None
         lib.qai_oracle_threads.restype = ctypes.c_int
+        lib.qai_oracle_set_threads.argtypes = [ctypes.c_int]
+        lib.qai_oracle_set_threads.restype = None
         lib.qai_oracle_grad_params.argtypes = [P, ctypes.c_int, P, ctypes.c_double,
                                                ctypes.POINTER(_Params), P, P]
         lib.qai_oracle_grad_params.restype = ctypes.c_int
@@ -82,6 +84,12 @@ def _load():
 def threads() -> int:
     """OpenMP threads the oracle uses (``OMP_NUM_THREADS`` or all cores)."""
     return int(_load().qai_oracle_threads())
+
+
+def set_threads(n: int) -> None:
+    """Use ``n`` OpenMP threads from now on (timing only; results do not
+    depend on it)."""
+    _load().qai_oracle_set_threads(int(n))
 
 
 def _params(eta, idw_power, grad_threshold, sign_rule, b2_rule):

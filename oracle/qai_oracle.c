@@ -92,6 +92,17 @@ int qai_oracle_threads(void)
 #endif
 }
 
+/* Threads of the parallel loops from now on (n >= 1; timing only: the
+ * results do not depend on it). */
+void qai_oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 static int interior(const shape3* s, int64_t i)
 {
     int64_t c[3] = { i / s->st[0], (i / s->st[1]) % s->n[1], i % s->n[2] };

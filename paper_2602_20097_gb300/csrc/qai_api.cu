@@ -182,7 +182,11 @@ qai_status check_params(const qai_params* p)
     if (p->grad_threshold < 1) return fail(QAI_ERR_INVALID_ARG, "grad_threshold must be >= 1");
     if (p->sign_rule != 0 && p->sign_rule != 1) return fail(QAI_ERR_INVALID_ARG, "sign_rule must be 0 or 1");
     if (p->b2_rule != 0 && p->b2_rule != 1) return fail(QAI_ERR_INVALID_ARG, "b2_rule must be 0 or 1");
-    if (p->flags & ~QAI_FLAG_OUTPUT_C) return fail(QAI_ERR_INVALID_ARG, "unknown bits in flags");
+    const uint32_t known = QAI_FLAG_OUTPUT_C | QAI_FLAG_EDT2_DENSE | QAI_FLAG_EDT2_HANDOVER | QAI_FLAG_EDT2_LIST |
+                           QAI_FLAG_EDT1_SEPARABLE;
+    if (p->flags & ~known) return fail(QAI_ERR_INVALID_ARG, "unknown bits in flags");
+    const uint32_t e2 = p->flags & (QAI_FLAG_EDT2_DENSE | QAI_FLAG_EDT2_HANDOVER | QAI_FLAG_EDT2_LIST);
+    if (e2 & (e2 - 1)) return fail(QAI_ERR_INVALID_ARG, "more than one QAI_FLAG_EDT2_* bit in flags");
     return QAI_OK;
 }
 
@@ -197,6 +201,7 @@ qai::MethodArgs method_args(const qai_params* p, double eb)
     m.sign_rule = p->sign_rule;
     m.b2_rule = p->b2_rule;
     m.output_c = (p->flags & QAI_FLAG_OUTPUT_C) ? 1 : 0;
+    m.flags = p->flags;
     return m;
 }
 
@@ -219,30 +224,24 @@ struct GradSink {
     int nblocks;       // set by run_pipeline
 };
 
-// Route of the second EDT for plain calls: QAI_SIGNED_ROUTE = "off" (the
-// dense second EDT alone, no signed-point route), "dense" (the route's
-// kernels run but hand every field to the dense second EDT), "brute" (no
-// shell search: every query goes to the brute-force search); anything else
-// is the default. Read on every call; all routes give the same bits.
+// Route of the second EDT for plain calls, from the route selection bits of
+// qai_params.flags (testing and measurement only; all routes give the same
+// bits): Off = the dense second EDT alone, Dense = the route's kernels run
+// but hand every field to the dense second EDT, Brute = no shell search
+// (every query goes to the brute-force search), Auto = the default.
 enum class Route { Auto, Off, Dense, Brute };
-Route signed_route()
+Route signed_route(uint32_t flags)
 {
-    const char* v = getenv("QAI_SIGNED_ROUTE");
-    if (!v) return Route::Auto;
-    if (!strcmp(v, "off")) return Route::Off;
-    if (!strcmp(v, "dense")) return Route::Dense;
-    if (!strcmp(v, "brute")) return Route::Brute;
+    if (flags & QAI_FLAG_EDT2_DENSE) return Route::Off;
+    if (flags & QAI_FLAG_EDT2_HANDOVER) return Route::Dense;
+    if (flags & QAI_FLAG_EDT2_LIST) return Route::Brute;
     return Route::Auto;
 }
 
 // First EDT of plain calls with the signed-point route: the local search with
-// the separable passes behind it (default), or QAI_FIRST_EDT = "separable"
-// (the separable passes alone). Read on every call; both give the same bits.
-bool local_first_edt()
-{
-    const char* v = getenv("QAI_FIRST_EDT");
-    return !(v && !strcmp(v, "separable"));
-}
+// the separable passes behind it (default), or the separable passes alone
+// (QAI_FLAG_EDT1_SEPARABLE). Both give the same bits.
+bool local_first_edt(uint32_t flags) { return !(flags & QAI_FLAG_EDT1_SEPARABLE); }
 
 // CTAs of the last EDT2 pass (the sums it leaves in the partials array).
 int final_pass_blocks(const Shape& sh)
@@ -283,10 +282,10 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
     cudaError_t e;
     // The signed-point route: plain calls on rank 2 and 3 fields (the debug
     // maps and the adjoint need the dense second EDT everywhere).
-    const Route route = signed_route();
+    const Route route = signed_route(m.flags);
     const bool signed_route_on = !debug && !grad && sh.rank >= 2 && route != Route::Off;
     int* ctr = signed_route_on ? reinterpret_cast<int*>(ws + lay.ctr) : nullptr;
-    const bool local = ctr && local_first_edt();
+    const bool local = ctr && local_first_edt(m.flags);
     const int* local_fail = local ? ctr + qai::kCtrLocalFail : nullptr;  // gate of the separable first EDT
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -490,15 +489,6 @@ qai_status run_plain(const int32_t* d_q, float* d_out, const Shape& sh, const Me
 
 void qai::set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
 
-bool qai::chained_launches()
-{
-    static const bool on = [] {
-        const char* v = getenv("QAI_PDL");
-        return !(v && !strcmp(v, "0"));
-    }();
-    return on;
-}
-
 extern "C" {
 
 void qai_default_params(qai_params* p)
@@ -665,9 +655,42 @@ qai_status qai_mitigate_save(const int32_t* d_q, float* d_out, int rank, const i
     // rank 2 and 3: the plain path writes the saved state (Dist1 and Dist2
     // where S != 0 off B1, the only points whose terms are not zero); rank 1
     // (and the dense-only test route): the per-step maps of a debug call
-    if (sh.rank >= 2 && signed_route() != Route::Off)
+    if (sh.rank >= 2 && signed_route(params ? params->flags : 0u) != Route::Off)
         return mitigate_impl(d_q, d_out, rank, dims, eb, params, d_ws, ws_bytes, stream, nullptr, &d);
     return mitigate_impl(d_q, d_out, rank, dims, eb, params, d_ws, ws_bytes, stream, &d, nullptr);
+}
+
+qai_status qai_dequantize(const int32_t* d_q, float* d_out, int64_t n, double eb, cudaStream_t stream)
+{
+    g_last_error.clear();
+    if (!d_q || !d_out) return fail(QAI_ERR_INVALID_ARG, "d_q and d_out must be non-NULL");
+    if (n < 0) return fail(QAI_ERR_INVALID_ARG, "n must be >= 0");
+    if (!(eb > 0.0) || !std::isfinite(eb)) return fail(QAI_ERR_INVALID_ARG, "eb must be finite and > 0");
+    if (n == 0) return QAI_OK;
+    cudaError_t e = timed("dequantize", (double)n * 8, stream,
+                          [&] { return qai::launch_dequantize(d_q, d_out, n, (float)(2.0 * eb), stream); });
+    return e == cudaSuccess ? QAI_OK : cuda_fail(e, "dequantize");
+}
+
+qai_status qai_mitigate_add(const int32_t* d_q, const float* d_dprime, float* d_out, int rank, const int64_t* dims,
+                            double eb, const qai_params* params, void* d_saved, void* d_ws, size_t ws_bytes,
+                            cudaStream_t stream)
+{
+    g_last_error.clear();
+    if (!d_dprime) return fail(QAI_ERR_INVALID_ARG, "d_dprime must be non-NULL");
+    qai_params p;
+    if (params) p = *params;
+    else qai_default_params(&p);
+    p.flags |= QAI_FLAG_OUTPUT_C;
+    Shape sh;
+    qai_status s = make_shape(rank, dims, &sh);
+    if (s != QAI_OK) return s;
+    s = d_saved ? qai_mitigate_save(d_q, d_out, rank, dims, eb, &p, d_saved, d_ws, ws_bytes, stream)
+                : qai_mitigate(d_q, d_out, rank, dims, eb, &p, d_ws, ws_bytes, stream, nullptr);
+    if (s != QAI_OK) return s;
+    cudaError_t e = timed("add_dprime", (double)sh.N * 12, stream,
+                          [&] { return qai::launch_add_dprime(d_dprime, d_out, sh.N, stream); });
+    return e == cudaSuccess ? QAI_OK : cuda_fail(e, "D' + C");
 }
 
 }  // extern "C"
@@ -738,7 +761,7 @@ qai_status qai_mitigate_backward(const int32_t* d_q, const float* d_grad_out, fl
         b.dist1 = v.dist1;
         b.dist2 = v.dist2;
         b.s = v.s;
-    } else if (sh.rank >= 2 && signed_route() != Route::Off) {
+    } else if (sh.rank >= 2 && signed_route(p->flags) != Route::Off) {
         // recompute with the plain path: S everywhere, Dist1 and (recorded)
         // Dist2 wherever S != 0 off B1 -- the only points whose terms are not
         // zero; B1 points (Dist1 = 0) come from the mask bytes

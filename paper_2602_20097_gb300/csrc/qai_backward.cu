@@ -10,6 +10,8 @@
 // compensation and takes the sums to FP64 at the end; each block writes its
 // two FP64 totals to a partials array, and a one-block kernel adds the
 // partials in a fixed order, so the result is the same on every run.
+#include <algorithm>
+
 #include "qai_device.cuh"
 #include "qai_launch.h"
 
@@ -156,7 +158,45 @@ __global__ void __launch_bounds__(256) k_save_signed(int64_t N, const int8_t* s,
     }
 }
 
+// D' = 2 q eps (Eq. 1) in fp32: float(q) * float(2 eps), rounded once, the
+// expression every output of the library starts from.
+__global__ void __launch_bounds__(256) k_dequantize(const int32_t* q, float* out, int64_t n, float two_eb)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        out[i] = (float)__ldg(q + i) * two_eb;
+}
+
+// out = dprime + out: the last step of D'' = D' + C for a given D' (out
+// holds C).
+__global__ void __launch_bounds__(256) k_add_dprime(const float* dprime, float* out, int64_t n)
+{
+    wait_prior_grid();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        out[i] = __ldg(dprime + i) + out[i];
+}
+
+int grid_for(int64_t n)
+{
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t blocks = (n + 255) / 256;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)sms * 8));
+}
+
 }  // namespace
+
+cudaError_t launch_dequantize(const int32_t* q, float* out, int64_t n, float two_eb, cudaStream_t st)
+{
+    k_dequantize<<<grid_for(n), 256, 0, st>>>(q, out, n, two_eb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add_dprime(const float* dprime, float* out, int64_t n, cudaStream_t st)
+{
+    return launch_chained(k_add_dprime, dim3(grid_for(n)), dim3(256), 0, st, dprime, out, n);
+}
 
 cudaError_t launch_save_signed(int64_t N, const int8_t* s, const uint8_t* eqm, const int32_t* dist1,
                                int8_t* s_out, int32_t* d1_out, int32_t* d2, cudaStream_t st)

@@ -711,23 +711,13 @@ cudaError_t go(ColArgs& a, bool debug, bool narrow, dim3 grid, dim3 block, size_
 
 }  // namespace
 
-// Rows per band and the largest column count per CTA; QAI_COL_ROWS_PER_BAND
-// and QAI_COL_MAX_W override them (tuning experiments).
-static int env_int(const char* name, int dflt)
-{
-    const char* v = getenv(name);
-    return v && *v ? atoi(v) : dflt;
-}
-
 bool choose_colpass(int L, int in_bytes, ColConfig* cfg, bool first_edt_last_pass)
 {
     // 32 columns per tile suit the last pass of the first EDT (dense sites,
     // the scan fast path, wider output rows); 16 suit the envelope-heavy
-    // passes (measured on a 512^3 field). Both knobs can be overridden.
-    static const int rows_per_band = env_int("QAI_COL_ROWS_PER_BAND", 32);
-    static const int max_w = env_int("QAI_COL_MAX_W", 0);
-    const int w = max_w > 0 ? max_w : (first_edt_last_pass && in_bytes == 4 ? 32 : 16);
-    return choose_colpass_with(L, in_bytes, rows_per_band, w, cfg);
+    // passes (measured on a 512^3 field); 32 rows per band.
+    const int w = first_edt_last_pass && in_bytes == 4 ? 32 : 16;
+    return choose_colpass_with(L, in_bytes, 32, w, cfg);
 }
 
 bool choose_colpass_with(int L, int in_bytes, int rows_per_band, int max_w, ColConfig* cfg)

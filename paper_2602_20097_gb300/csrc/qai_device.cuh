@@ -39,6 +39,7 @@ struct MethodArgs {
     int sign_rule;       // 0 SUM, 1 FIRST
     int b2_rule;         // 0 SAME_Q, 1 LITERAL
     int output_c;        // write the compensation C instead of D''
+    unsigned flags;      // qai_params.flags (route selection bits)
 };
 
 // Programmatic dependent launch: a kernel launched by launch_chained (see

@@ -10,8 +10,7 @@ namespace qai {
 
 // Launches of the plain path's kernels with programmatic stream
 // serialization: the next kernel is scheduled while the previous one drains
-// (every such kernel starts with wait_prior_grid()). QAI_PDL=0 turns it off.
-bool chained_launches();
+// (every such kernel starts with wait_prior_grid()).
 template <class... P, class... A>
 cudaError_t launch_chained(void (*kern)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A&&... args)
 {
@@ -22,7 +21,7 @@ cudaError_t launch_chained(void (*kern)(P...), dim3 grid, dim3 block, size_t sme
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = chained_launches() ? 1 : 0;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kern, static_cast<A&&>(args)...);
@@ -81,6 +80,9 @@ cudaError_t launch_backward(const BackArgs& a, cudaStream_t st);
 // elsewhere.
 cudaError_t launch_save_signed(int64_t N, const int8_t* s, const uint8_t* eqm, const int32_t* dist1,
                                int8_t* s_out, int32_t* d1_out, int32_t* d2, cudaStream_t st);
+// D' = 2 q eps in fp32 (n points), and out = dprime + out (D'' for a given D').
+cudaError_t launch_dequantize(const int32_t* q, float* out, int64_t n, float two_eb, cudaStream_t st);
+cudaError_t launch_add_dprime(const float* dprime, float* out, int64_t n, cudaStream_t st);
 // Adds the per-CTA partial sums of the fused adjoint pass in a fixed order.
 cudaError_t launch_partials_sum(const double* partials, int nblocks, double eb, double eta,
                                 double* grad_params, cudaStream_t st);

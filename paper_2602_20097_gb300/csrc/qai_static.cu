@@ -31,7 +31,10 @@ std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of g_scratch on the current device. In host code the name
-// g_scratch is a host-side stand-in, never a device address.
+// g_scratch is a host-side stand-in, never a device address. The first lookup
+// on a device loads this file's module there (lazy module loading), which
+// commits the array's memory on that device; a failure to load or to commit
+// it is reported here, as QAI_ERR_CUDA.
 qai_status scratch_address(void** out)
 {
     int dev = -1;
@@ -66,16 +69,26 @@ extern "C" qai_status qai_mitigate_static(const int32_t* d_q, float* d_out, int 
                                           const int64_t* dims, double eb, const qai_params* params,
                                           cudaStream_t stream)
 {
+    qai::set_last_error("");
     size_t need = 0;
     qai_status s = qai_workspace_size(rank, dims, 0, &need);  // validates rank and dims
     if (s != QAI_OK) return s;
     int64_t n = 1;
     for (int a = 0; a < rank; ++a) n *= dims[a];
-    if (n > kMaxPoints || need > kScratchBytes) {
+    if (n > kMaxPoints) {
         char msg[200];
         snprintf(msg, sizeof msg,
                  "qai_mitigate_static: %lld points exceed the static scratch limit of %lld points",
                  (long long)n, (long long)kMaxPoints);
+        qai::set_last_error(msg);
+        return QAI_ERR_SHAPE;
+    }
+    if (need > kScratchBytes) {
+        char msg[200];
+        snprintf(msg, sizeof msg,
+                 "qai_mitigate_static: this shape needs %zu bytes of workspace, more than the %zu bytes "
+                 "of the static scratch array",
+                 need, kScratchBytes);
         qai::set_last_error(msg);
         return QAI_ERR_SHAPE;
     }

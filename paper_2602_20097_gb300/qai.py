@@ -32,6 +32,13 @@ SIGN_SUM, SIGN_FIRST = 0, 1
 B2_SAME_Q, B2_LITERAL = 0, 1
 WS_INDEX = 1
 FLAG_OUTPUT_C = 1
+# route selection bits of qai_params.flags (testing and measurement only: every
+# route gives the same output bits)
+FLAG_EDT2_DENSE = 0x10
+FLAG_EDT2_HANDOVER = 0x20
+FLAG_EDT2_LIST = 0x40
+FLAG_EDT1_SEPARABLE = 0x80
+ROUTE_FLAGS = {"auto": 0, "off": FLAG_EDT2_DENSE, "dense": FLAG_EDT2_HANDOVER, "brute": FLAG_EDT2_LIST}
 INF32 = 2 ** 31 - 1
 
 
@@ -71,6 +78,9 @@ SIGNATURES = {
                                          P, ctypes.c_size_t, P]),
     "qai_mitigate_static": (ctypes.c_int, [P, P, ctypes.c_int, P, ctypes.c_double,
                                            ctypes.POINTER(Params), P]),
+    "qai_dequantize": (ctypes.c_int, [P, P, ctypes.c_int64, ctypes.c_double, P]),
+    "qai_mitigate_add": (ctypes.c_int, [P, P, P, ctypes.c_int, P, ctypes.c_double, ctypes.POINTER(Params),
+                                        P, P, ctypes.c_size_t, P]),
     "qai_saved_size": (ctypes.c_int, [ctypes.c_int, P, ctypes.POINTER(ctypes.c_size_t)]),
     "qai_mitigate_save": (ctypes.c_int, [P, P, ctypes.c_int, P, ctypes.c_double, ctypes.POINTER(Params),
                                          P, P, ctypes.c_size_t, P]),
@@ -166,21 +176,34 @@ def alloc_workspace(nbytes: int, device=None) -> torch.Tensor:
     return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device or "cuda")
 
 
-def _params(eta, idw_power, grad_threshold, sign_rule, b2_rule, output_c=False):
+def route_flags(route: str = "auto", first_edt: str = "local") -> int:
+    """qai_params.flags bits of a route choice: ``route`` = "auto" (default),
+    "off" (dense second EDT alone), "dense" (the route hands over to the dense
+    second EDT), "brute" (no shell search); ``first_edt`` = "local" (default)
+    or "separable". Every choice gives the same output bits."""
+    if route not in ROUTE_FLAGS or first_edt not in ("local", "separable"):
+        raise QAIError(f"unknown route {route!r} / first_edt {first_edt!r}")
+    return ROUTE_FLAGS[route] | (FLAG_EDT1_SEPARABLE if first_edt == "separable" else 0)
+
+
+def _params(eta, idw_power, grad_threshold, sign_rule, b2_rule, output_c=False, route="auto",
+            first_edt="local"):
     return default_params(eta=eta, idw_power=idw_power, grad_threshold=grad_threshold,
                           sign_rule=sign_rule, b2_rule=b2_rule,
-                          flags=FLAG_OUTPUT_C if output_c else 0)
+                          flags=(FLAG_OUTPUT_C if output_c else 0) | route_flags(route, first_edt))
 
 
 def mitigate(q: torch.Tensor, eb: float, eta: float = 0.9, idw_power: float = 1.0,
              grad_threshold: int = 2, sign_rule: int = SIGN_SUM, b2_rule: int = B2_SAME_Q,
              out: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
-             debug: bool = False, stream=None, output_c: bool = False):
+             debug: bool = False, stream=None, output_c: bool = False, route: str = "auto",
+             first_edt: str = "local"):
     """Algorithm 4 on a contiguous CUDA int32 tensor ``q`` (rank 1-3).
 
     Returns D'' as a float32 tensor of ``q``'s shape (the compensation C alone
     with ``output_c``), or ``(D'', maps)`` when ``debug`` with ``maps`` = dict
-    of the per-step outputs (device tensors).
+    of the per-step outputs (device tensors). ``route`` and ``first_edt``
+    select how the EDTs are computed (see :func:`route_flags`; testing only).
     """
     lib = load()
     if not (q.is_cuda and q.dtype == torch.int32 and q.is_contiguous()):
@@ -196,14 +219,23 @@ def mitigate(q: torch.Tensor, eb: float, eta: float = 0.9, idw_power: float = 1.
                  ("idx1", torch.int32), ("s", torch.int8), ("b2", torch.uint8),
                  ("dist2", torch.int32))}
         dbg = DebugOut(**{k: v.data_ptr() for k, v in maps.items()})
+    _check_out(out, shape, q.device)
     if workspace is None:
         workspace = alloc_workspace(workspace_size(shape, with_index=debug), q.device)
-    p = _params(eta, idw_power, grad_threshold, sign_rule, b2_rule, output_c)
-    rc = lib.qai_mitigate(q.data_ptr(), out.data_ptr(), len(shape), _dims(shape), float(eb),
-                          ctypes.byref(p), workspace.data_ptr(), workspace.numel(), _stream(stream),
-                          ctypes.byref(dbg) if dbg is not None else None)
+    p = _params(eta, idw_power, grad_threshold, sign_rule, b2_rule, output_c, route, first_edt)
+    with torch.cuda.device(q.device):
+        rc = lib.qai_mitigate(q.data_ptr(), out.data_ptr(), len(shape), _dims(shape), float(eb),
+                              ctypes.byref(p), workspace.data_ptr(), workspace.numel(), _stream(stream),
+                              ctypes.byref(dbg) if dbg is not None else None)
     _check(rc)
     return (out, maps) if debug else out
+
+
+def _check_out(out, shape, device):
+    """``out`` must be a contiguous float32 tensor of ``shape`` on ``device``."""
+    if not (out.dtype == torch.float32 and out.is_contiguous() and tuple(out.shape) == tuple(shape)
+            and out.device == device):
+        raise QAIError(f"out must be a contiguous float32 tensor of shape {tuple(shape)} on {device}")
 
 
 def route_counts(workspace: torch.Tensor, shape, stream=None) -> dict:
@@ -301,6 +333,40 @@ def mitigate_backward(q: torch.Tensor, eb: float, grad_out: torch.Tensor, saved=
     return gd, gp
 
 
+def dequantize(q: torch.Tensor, eb: float, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """D' = 2 q eps (Eq. 1) in float32, computed by the library's kernel."""
+    if not (q.is_cuda and q.dtype == torch.int32 and q.is_contiguous()):
+        raise QAIError("q must be a contiguous CUDA int32 tensor")
+    if out is None:
+        out = torch.empty(q.shape, dtype=torch.float32, device=q.device)
+    _check_out(out, q.shape, q.device)
+    _check(load().qai_dequantize(q.data_ptr(), out.data_ptr(), q.numel(), float(eb), _stream(stream)))
+    return out
+
+
+def mitigate_add(q: torch.Tensor, dprime: torch.Tensor, eb: float, eta: float = 0.9, idw_power: float = 1.0,
+                 saved: torch.Tensor | None = None, workspace: torch.Tensor | None = None, stream=None,
+                 out: torch.Tensor | None = None):
+    """D'' = D' + C with the dequantized field ``dprime`` given (float32, q's
+    shape): C from ``q`` by Algorithm 4 and the add, both in the library.
+    ``saved`` (from :func:`saved_size`) also receives the stored-mode state."""
+    lib = load()
+    shape = tuple(q.shape)
+    if not (dprime.is_cuda and dprime.dtype == torch.float32 and dprime.is_contiguous()
+            and tuple(dprime.shape) == shape and dprime.device == q.device):
+        raise QAIError("dprime must be a contiguous float32 CUDA tensor of q's shape")
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float32, device=q.device)
+    _check_out(out, shape, q.device)
+    if workspace is None:
+        workspace = alloc_workspace(workspace_size(shape), q.device)
+    p = _params(eta, idw_power, 2, SIGN_SUM, B2_SAME_Q)
+    _check(lib.qai_mitigate_add(q.data_ptr(), dprime.data_ptr(), out.data_ptr(), len(shape), _dims(shape),
+                                float(eb), ctypes.byref(p), saved.data_ptr() if saved is not None else None,
+                                workspace.data_ptr(), workspace.numel(), _stream(stream)))
+    return out
+
+
 class QAIFunction(torch.autograd.Function):
     """D'' = D' + C(q; eta, p), differentiable in D', eta and p with the EDT
     assignment held fixed (the adjoint of step E, run by the CUDA library).
@@ -309,18 +375,17 @@ class QAIFunction(torch.autograd.Function):
     field on the device, ``eta`` and ``p`` 0-dim float64 tensors, ``q`` the
     int32 indices, ``stored`` True keeps Dist1/Dist2/S from the forward,
     False recomputes them in the backward (no memory held between the two).
+    The forward's D'' (C and the add) comes from the library.
     """
 
     @staticmethod
     def forward(ctx, dprime, eta, p, q, eb, stored=True):
         e, pw = float(eta), float(p)
-        if stored:
-            comp, saved = mitigate_save(q, eb, eta=e, idw_power=pw, output_c=True)
-        else:
-            comp, saved = mitigate(q, eb, eta=e, idw_power=pw, output_c=True), None
+        saved = alloc_workspace(saved_size(tuple(q.shape)), q.device) if stored else None
+        out = mitigate_add(q, dprime.contiguous().to(torch.float32), eb, eta=e, idw_power=pw, saved=saved)
         ctx.save_for_backward(q)
         ctx.saved_state, ctx.eb, ctx.e, ctx.pw = saved, eb, e, pw
-        return dprime + comp
+        return out
 
     @staticmethod
     def backward(ctx, grad):
@@ -334,7 +399,7 @@ def tune(q: torch.Tensor, eb: float, x: torch.Tensor, eta: float = 0.9, p: float
          steps: int = 20, lr: float = 0.05, stored: bool = True):
     """Gradient descent on (eta, p) minimising mean((D'' - x)^2) against the
     original field ``x``; returns the list of (eta, p, loss) per step."""
-    dprime = (q.to(torch.float64) * (2.0 * eb)).to(torch.float32)
+    dprime = dequantize(q, eb)
     e = torch.tensor(eta, dtype=torch.float64, device=q.device, requires_grad=True)
     pw = torch.tensor(p, dtype=torch.float64, device=q.device, requires_grad=True)
     xs = x.to(torch.float32)
@@ -456,18 +521,22 @@ def quality(x: torch.Tensor, y: torch.Tensor, window: int = 7, stride: int = 2, 
 def mitigate_static(q: torch.Tensor, eb: float, out: torch.Tensor | None = None, stream=None, **kw):
     """Algorithm 4 without any device allocation by the library: for callers
     that cannot allocate device memory. Uses the scratch array compiled into
-    libqai (fields up to STATIC_MAX_POINTS points); calls that overlap on the
-    GPU race on that array, so keep them on one stream."""
+    libqai (fields up to STATIC_MAX_POINTS points); the first call on a device
+    loads that array there, so make it before any region that must not
+    allocate. Calls that overlap on the GPU race on that array, so keep them
+    on one stream."""
     lib = load()
     if not (q.is_cuda and q.dtype == torch.int32 and q.is_contiguous()):
         raise QAIError("q must be a contiguous CUDA int32 tensor")
     shape = tuple(q.shape)
     if out is None:
         out = torch.empty(shape, dtype=torch.float32, device=q.device)
+    _check_out(out, shape, q.device)
     p = _params(kw.get("eta", 0.9), kw.get("idw_power", 1.0), kw.get("grad_threshold", 2),
                 kw.get("sign_rule", SIGN_SUM), kw.get("b2_rule", B2_SAME_Q))
-    _check(lib.qai_mitigate_static(q.data_ptr(), out.data_ptr(), len(shape), _dims(shape),
-                                   float(eb), ctypes.byref(p), _stream(stream)))
+    with torch.cuda.device(q.device):
+        _check(lib.qai_mitigate_static(q.data_ptr(), out.data_ptr(), len(shape), _dims(shape),
+                                       float(eb), ctypes.byref(p), _stream(stream)))
     return out
 
 

@@ -85,6 +85,13 @@ def test_output_c_is_the_compensation():
     torch.cuda.synchronize()
     assert float(torch.max(torch.abs(dprime + comp - full))) <= 2e-7 * float(torch.max(torch.abs(full))) + 1e-9
     assert float(torch.max(torch.abs(comp))) <= 0.9 * eb * (1 + 1e-6)
+    # the library's D' is float(q) * float(2 eps), and D' + C from the library
+    # is that D' plus the compensation, one fp32 add
+    dq = qai.dequantize(q, eb)
+    assert torch.equal(dq, q.float() * torch.tensor(2 * eb, dtype=torch.float32, device="cuda"))
+    added = qai.mitigate_add(q, dq, eb)
+    assert torch.equal(added, dq + comp)
+    assert float(torch.max(torch.abs(added - full))) <= 2e-7 * float(torch.max(torch.abs(full))) + 1e-9
 
 
 def test_autograd_function_and_tuning():
