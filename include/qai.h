@@ -319,9 +319,9 @@ qai_status qai_quality(const float* d_x, const float* d_y, int rank, const int64
  * no counterpart; it is a deployment convenience of this library.
  *
  * Instead of a workspace it uses one scratch array compiled into the library
- * (a 256-byte aligned __device__ array of 13.5 * QAI_STATIC_MAX_POINTS +
- * 1 MiB bytes, about 28 MiB). Every GPU on which the library's code is loaded
- * holds that array until the process exits.
+ * (a 256-byte aligned __device__ array of 14 * QAI_STATIC_MAX_POINTS + 1 MiB
+ * bytes, about 29 MiB). Every GPU on which the library's code is loaded holds
+ * that array until the process exits.
  *
  * First call on a device: it looks up the array's device address
  * (cudaGetSymbolAddress) with that device current. Under CUDA's lazy module
@@ -334,7 +334,9 @@ qai_status qai_quality(const float* d_x, const float* d_y, int rank, const int64
  *  d_q, d_out, rank, dims, eb, params, stream: as for qai_mitigate (the
  *          caller still passes the input and the output buffers).
  * Fields larger than QAI_STATIC_MAX_POINTS points return QAI_ERR_SHAPE before
- * any CUDA call. Every call shares the array, which keeps the last call's
+ * any CUDA call, and so do fields whose workspace (qai_workspace_size) is
+ * larger than the array; every field of at most QAI_STATIC_MAX_POINTS points
+ * with an x extent (after squeezing) of 16 or more fits. Every call shares the array, which keeps the last call's
  * contents; the call's first kernel clears the few counters that must start
  * at zero, and every other slice is written before it is read. Calls whose
  * work overlaps on the GPU (two streams, or two host threads) race on the

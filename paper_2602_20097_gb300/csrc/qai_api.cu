@@ -158,6 +158,12 @@ Layout layout_for(const Shape& s, uint32_t flags)
     // a uint16 count per column of the last column pass (z: ny * nx, y: nx)
     l.cflag = s.rank == 3 ? take((size_t)s.ny * s.nx * 2) : s.rank == 2 ? take((size_t)s.nx * 2) : 0;
     if (s.rank >= 2) {
+        const size_t rows = (size_t)s.nz * s.ny;
+        l.wpr = (s.nx + 15) / 16;
+        l.bwpr = (s.nx + 31) / 32;
+        l.codes = take(rows * l.wpr * 4);
+        l.spk = take(rows * l.wpr * 4);
+        l.b2bits = take(rows * l.bwpr * 4);
         l.qcap = (int)(N / 128 + 1024);
         l.scap = (int)(N / 256 + 1024);
         l.fcap = std::min(l.qcap, 1 << 16);
@@ -293,20 +299,24 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
         if ((e = cudaMemsetAsync(ctr, 0, qai::kCtrWords * sizeof(int), st)) != cudaSuccess)
             return cuda_fail(e, "route counters");
     }
+    qai::LocalArgs la{};
+    if (ctr) {
+        la.rank = sh.rank; la.nz = sh.nz; la.ny = sh.ny; la.nx = sh.nx; la.wpr = lay.wpr;
+        la.q = d_q; la.out = d_out; la.ctr = ctr; la.dist1 = dist1;
+        la.codes = reinterpret_cast<uint32_t*>(ws + lay.codes);
+        la.spk = reinterpret_cast<uint32_t*>(ws + lay.spk);
+        la.qlist = reinterpret_cast<qai::Query*>(ws + lay.qlist); la.qcap = lay.qcap;
+        la.eqm = eqm; la.s = s;
+        la.m = m;
+        auto al = [](const void* p, int b) { return (reinterpret_cast<uintptr_t>(p) % b) == 0; };
+        la.vec = (sh.nx % 4 == 0) && al(d_q, 16) && al(d_out, 16);
+    }
     if (local) {
         // Steps A-C by the bounded nearest-site search; the separable passes
         // below run only if some point has no B1 point within reach.
-        qai::LocalArgs la{};
-        la.rank = sh.rank; la.nz = sh.nz; la.ny = sh.ny; la.nx = sh.nx;
-        la.q = d_q; la.eqm = eqm; la.s = s; la.dist1 = dist1; la.out = d_out; la.ctr = ctr;
-        la.qlist = reinterpret_cast<qai::Query*>(ws + lay.qlist); la.qcap = lay.qcap;
-        la.slist = reinterpret_cast<int32_t*>(ws + lay.slist); la.scap = lay.scap;
-        la.m = m;
-        auto al = [](const void* p, int b) { return (reinterpret_cast<uintptr_t>(p) % b) == 0; };
-        la.vec = (sh.nx % 4 == 0) && al(d_q, 16) && al(d_out, 16) && al(eqm, 4);
-        e = timed("detect", N * 9.0, st, [&] { return qai::launch_local_detect(la, st); });
+        e = timed("detect", N * 8.25, st, [&] { return qai::launch_local_detect(la, st); });
         if (e != cudaSuccess) return cuda_fail(e, "step A");
-        e = timed("near", N * 2.0, st, [&] { return qai::launch_local_near(la, st); });
+        e = timed("near", N * 0.5, st, [&] { return qai::launch_local_near(la, st); });
         if (e != cudaSuccess) return cuda_fail(e, "nearest-site search");
     }
 
@@ -374,6 +384,10 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
         if (d.idx1) { cz.dbg_idx_in = idx_tmp; cz.dbg_idx_out = d.idx1; }
         if ((st_ = colpass(1, 4, true, cz, "colpass1_z_final", 4 + 4 + 1)) != QAI_OK) return st_;
     }
+    if (ctr) {  // the packed S of the route, from the separable first EDT's S map when it ran
+        e = timed("pack_s", N * 1.25, st, [&] { return qai::launch_local_pack_s(la, local, st); });
+        if (e != cudaSuccess) return cuda_fail(e, "packed S");
+    }
     if (d.dist1 && (e = cudaMemcpyAsync(d.dist1, dist1, (size_t)sh.N * 4, cudaMemcpyDeviceToDevice, st)))
         return cuda_fail(e, "copy dist1");
     if (d.s && (e = cudaMemcpyAsync(d.s, s, (size_t)sh.N, cudaMemcpyDeviceToDevice, st)))
@@ -384,28 +398,36 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
     if (ctr) {
         qai::RouteArgs ra{};
         ra.rank = sh.rank; ra.nz = sh.nz; ra.ny = sh.ny; ra.nx = sh.nx;
-        ra.q = d_q; ra.eqm = eqm; ra.s = s; ra.out = d_out; ra.ctr = ctr;
+        ra.wpr = lay.wpr; ra.bwpr = lay.bwpr;
+        ra.q = d_q; ra.spk = la.spk; ra.out = d_out; ra.ctr = ctr;
+        ra.b2bits = reinterpret_cast<uint32_t*>(ws + lay.b2bits);
         ra.qlist = qlist; ra.qcap = lay.qcap;
-        ra.slist = reinterpret_cast<const int32_t*>(ws + lay.slist); ra.scap = lay.scap;
         ra.mlist = reinterpret_cast<qai::Query*>(ws + lay.mlist);
         ra.flist = reinterpret_cast<qai::Query*>(ws + lay.flist); ra.fcap = lay.fcap;
         ra.fmin = reinterpret_cast<int32_t*>(ws + lay.fmin);
         ra.b2list = reinterpret_cast<int32_t*>(ws + lay.b2list); ra.b2cap = lay.b2cap;
-        ra.max_r2 = route == Route::Brute ? -1 : qai::route_table_r2(sh.rank);
+        ra.shell = route == Route::Brute ? 0 : 1;
         ra.d2rec = d2rec;
         ra.brute_budget = 1LL << 28;
         ra.m = m;
         if (route == Route::Dense) ra.qcap = -1;  // every count is over it: hand over at once
+        e = timed("b2map", N * 0.375, st, [&] { return qai::launch_route_b2map(ra, st); });
+        if (e != cudaSuccess) return cuda_fail(e, "B2 bitmap");
         e = timed("signed_query", 0.0, st, [&] { return qai::launch_route_query(ra, 4 * sms, st); });
         if (e != cudaSuccess) return cuda_fail(e, "signed-point shell search");
         e = timed("signed_query_mid", 0.0, st, [&] { return qai::launch_route_query_mid(ra, 4 * sms, st); });
         if (e != cudaSuccess) return cuda_fail(e, "signed-point shell search, second phase");
-        e = timed("signed_query_far", 0.0, st, [&] { return qai::launch_route_query_far(ra, 4 * sms, st); });
-        if (e != cudaSuccess) return cuda_fail(e, "signed-point shell search, third phase");
-        e = timed("signed_b2sites", 0.0, st, [&] { return qai::launch_route_b2sites(ra, 8 * sms, st); });
+        e = timed("b2list", 0.0, st, [&] { return qai::launch_route_b2list(ra, st); });
         if (e != cudaSuccess) return cuda_fail(e, "B2 site list");
         e = timed("signed_brute", 0.0, st, [&] { return qai::launch_route_brute(ra, 2 * sms, st); });
         if (e != cudaSuccess) return cuda_fail(e, "brute-force search");
+        // the byte maps of the separable passes: for the dense second EDT
+        // when it takes over, and always for the adjoint's forward
+        const int mode = (d2rec || saved) ? 2 : 1;
+        if (local) {
+            e = timed("expand", N * (mode == 2 ? 6.25 : 0.0), st, [&] { return qai::launch_local_expand(la, mode, st); });
+            if (e != cudaSuccess) return cuda_fail(e, "byte maps");
+        }
     }
 
     // B2 = GetBoundary(S) + EDT-x of B2 (rank 1: also step E).

@@ -55,14 +55,13 @@ __device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol
 // "queries": points with S != 0 off B1. The route counters live in the
 // workspace; row pass 1 zeroes them.
 enum RouteCtr : int {
-    kCtrQueries = 0,   // queries appended by the last pass of the first EDT
-    kCtrFailed = 1,    // queries whose local search found no B2 site
-    kCtrB2 = 2,        // B2 sites listed for the brute-force search
+    kCtrQueries = 0,   // queries appended (by near, or the last separable EDT1 pass)
+    kCtrUnresolved = 1,// queries the shell search left to the search over the B2 sites
+    kCtrB2 = 2,        // B2 sites listed for that search
     kCtrDense = 3,     // != 0: the dense second EDT must run
-    kCtrSigned = 4,    // B1 points with S != 0 appended (the rest of the signed set)
-    kCtrSignedOver = 5,// != 0: a tile had more of them than it could buffer
+    kCtrSigned = 4,    // B1 points with S != 0
+    kCtrSignedOver = 5,// != 0: a tile of the separable pass had more of them than it could buffer
     kCtrBruteDone = 6, // CTAs of the brute-force search that finished
-    kCtrUnresolved = 7,// queries left to the brute-force search by both shell searches
     kCtrMid = 8,       // queries the first (per-thread) shell search left
     kCtrLocalFail = 15,// != 0: the local first EDT left a point without its site;
                        // the separable first EDT runs (and zeroes the words before)
@@ -153,15 +152,14 @@ struct ColArgs {
 // The kernels of the signed-point route.
 struct RouteArgs {
     int rank, nz, ny, nx;
+    int wpr, bwpr;           // packed words per row: S (16 points), B2 bitmap (32)
     const int32_t* q;
-    const uint8_t* eqm;      // equal-q neighbour mask of row pass 1
-    const int8_t* s;         // S
+    const uint32_t* spk;     // packed S
+    uint32_t* b2bits;        // B2 bitmap (written by k_b2map)
     float* out;
     int* ctr;                // RouteCtr words
     const Query* qlist;
     int qcap;
-    const int32_t* slist;    // B1 points with S != 0
-    int scap;
     Query* mlist;            // queries left by the first shell search (qcap entries)
     Query* flist;            // queries left to the brute-force search
     int32_t* fmin;           // their Dist2, min-reduced by the brute-force CTAs
@@ -169,26 +167,40 @@ struct RouteArgs {
     int32_t* b2list;         // B2 sites as (x | y << 16, z) pairs
     int b2cap;
     int32_t* d2rec;          // NULL, or Dist2 recorded here (by point) at every query
-    int max_r2;              // local search radius^2 (<= the offset table's)
-    long long brute_budget;  // largest failed x sites product searched by brute force
+    int shell;               // 0: no shell search (every query to the site list)
+    long long brute_budget;  // largest leftover queries x sites product searched by brute force
     MethodArgs m;
 };
 
 // The local first EDT (qai_local.cu): step A, then the nearest B1 site of
 // every point by a bounded exact search, S and the signed-point lists.
+//
+// Packed per-point maps (2 bits a point, 16 points a 32-bit word; each row
+// of x starts a new word, so a row takes wpr = ceil(nx / 16) words and the
+// fields past nx are 0): point (row, x) is field x & 15 of word
+// row * wpr + (x >> 4), at bits 2 (x & 15) and up.
+//   codes  step A: 0 off B1, 1 + sign code of S_B on B1 (1: S_B = 0,
+//          2: S_B = +1, 3: S_B = -1)
+//   spk    S (Algorithm 3) as a sign code: 0, 1 (+1), 2 (-1)
+// The B2 bitmap of the route is 1 bit a point, 32 points a word, a row
+// taking bwpr = ceil(nx / 32) words (bits past nx are 0).
 struct LocalArgs {
     int rank, nz, ny, nx;
+    int wpr;                 // packed words per row
     const int32_t* q;
-    uint8_t* eqm;            // equal-q mask (bits 0-5) and sign code of S_B (bits 6-7)
-    int8_t* s;               // S
-    int32_t* dist1;          // Dist1 where S != 0
+    uint32_t* codes;         // packed step-A codes (written by detect)
+    uint32_t* spk;           // packed S (written by near)
+    int32_t* dist1;          // Dist1 at the queries (S != 0 off B1)
     float* out;              // D' + S_B eta eps on B1, D' elsewhere
     int* ctr;                // RouteCtr words
     Query* qlist;
     int qcap;
-    int32_t* slist;
-    int scap;
     int vec;                 // 128-bit loads of q usable
+    // the byte maps of the separable passes, for the fallbacks: eqm (equal-q
+    // mask, bits 0-5, and the sign code of S_B, bits 6-7; 0x3F off the
+    // interior) and s (S as int8)
+    uint8_t* eqm;
+    int8_t* s;
     MethodArgs m;
 };
 

@@ -58,20 +58,25 @@ cudaError_t launch_colpass_grad(int in_bytes, ColArgs& a, const ColConfig& cfg, 
 cudaError_t launch_colpass(int phase, int in_bytes, bool final_pass, ColArgs& a,
                            const ColConfig& cfg, bool debug, int64_t max_g, cudaStream_t st);
 
-// Signed-point route of the second EDT (qai_signed.cu): the shell search at
-// the queries, the list of B2 sites and the brute-force search; each kernel
-// reads the route counters and does nothing when it is not needed.
-int route_table_r2(int rank);
+// Signed-point route of the second EDT (qai_signed.cu): the B2 bitmap, the
+// two shell phases at the queries, the list of B2 sites and the brute-force
+// search; each kernel reads the route counters and does nothing when it is
+// not needed.
+cudaError_t launch_route_b2map(const RouteArgs& a, cudaStream_t st);
 cudaError_t launch_route_query(const RouteArgs& a, int blocks, cudaStream_t st);
 cudaError_t launch_route_query_mid(const RouteArgs& a, int blocks, cudaStream_t st);
-cudaError_t launch_route_query_far(const RouteArgs& a, int blocks, cudaStream_t st);
-cudaError_t launch_route_b2sites(const RouteArgs& a, int blocks, cudaStream_t st);
+cudaError_t launch_route_b2list(const RouteArgs& a, cudaStream_t st);
 cudaError_t launch_route_brute(const RouteArgs& a, int blocks, cudaStream_t st);
 
-// The local first EDT (qai_local.cu): step A with the pre-written output,
-// then S, Dist1 and the signed-point lists by a bounded nearest-site search.
+// The local first EDT (qai_local.cu): step A with the pre-written output and
+// the packed codes, then S (packed), Dist1 and the queries by a bounded
+// nearest-site search; the byte maps of the separable passes (mode 1: when
+// the dense second EDT runs, 2: always) and the packed S from the separable
+// first EDT's int8 S map (gated: when that EDT ran as the fallback).
 cudaError_t launch_local_detect(const LocalArgs& a, cudaStream_t st);
 cudaError_t launch_local_near(const LocalArgs& a, cudaStream_t st);
+cudaError_t launch_local_expand(const LocalArgs& a, int mode, cudaStream_t st);
+cudaError_t launch_local_pack_s(const LocalArgs& a, bool gated, cudaStream_t st);
 
 // Adjoint reduction of step E (qai_backward.cu).
 cudaError_t launch_backward(const BackArgs& a, cudaStream_t st);

@@ -8,26 +8,28 @@
 // where almost every point differs from a neighbour -- the nearest site is a
 // few cells away, and a bounded search finds it exactly:
 //
-//   k_detect  step A (Algorithm 2) at every point: the equal-q mask with the
-//             sign code of S_B packed in (a point is on B1 iff it is interior
-//             and some neighbour differs; points off the interior get the
-//             all-equal mask), the output wherever Dist2 does not matter
-//             (D' + S_B eta eps on B1, D' elsewhere), and the list of B1
-//             points with S != 0. Dist1 = 0 on B1 is not stored: readers take
-//             B1 from the mask byte.
-//   k_near    every point off B1 scans the lattice offsets of squared length
-//             <= 8 in order of (squared length, dz, dy, dx) -- for points
-//             inside the field that is the order of (distance, linear index)
-//             -- and takes the first B1 point it meets: Dist1 and I1 exactly,
-//             since any point outside that ball is at squared distance >= 9.
-//             It writes S everywhere, Dist1 where S != 0, and lists the
-//             queries of the second EDT (S != 0 off B1). k_near_sparse does
-//             the same for rows of 16-byte multiples, with the search run
-//             only on the 4-point words that hold a point off B1, gathered
-//             across the warp.
+//   k_detect  step A (Algorithm 2) at every point: whether the point is on B1
+//             (interior, some axis neighbour differs) and the sign code of
+//             S_B, as a 2-bit code per point in the packed `codes` map; the
+//             output wherever Dist2 does not matter (D' + S_B eta eps on B1,
+//             D' elsewhere); the count of B1 points with S != 0. It reads q
+//             once and writes 4.25 bytes per point.
+//   k_near    S at every point into the packed `spk` map. A point on B1
+//             keeps S_B. A point off B1 takes the first B1 point among the
+//             lattice offsets of squared length <= 8 in order of (squared
+//             length, dz, dy, dx) -- for points inside the field that is the
+//             order of (distance, linear index) -- which gives Dist1 and I1
+//             exactly, since any point outside that ball is at squared
+//             distance >= 9. The search runs on 16 points at once, on the
+//             2-bit fields of one word: for each offset the neighbour word is
+//             shifted into place and the still-unresolved fields with a site
+//             there take its code. Queries of the second EDT (S != 0 off B1)
+//             go to the query list with Dist1.
 //
 // A point with no B1 point within that ball sets kCtrLocalFail; the separable
-// first EDT (row pass 1, column passes 1) then runs and rewrites all of it.
+// first EDT (row pass 1, column passes 1) then runs and rewrites all of it,
+// and k_pack_s packs its S map for the route. k_expand writes the byte maps
+// (equal-q mask, S) that the separable second EDT and the adjoint read.
 #include "qai_detect.cuh"
 #include "qai_device.cuh"
 #include "qai_launch.h"
@@ -77,21 +79,40 @@ constexpr int count_near(bool three)
 static_assert(count_near(true) == kNearN3 && count_near(false) == kNearN2, "nearest-site table size");
 __constant__ NearTable c_near = make_near();
 
+// First table entry of squared length r2 (1..9: one past the table for 9),
+// 3-D or 2-D table.
+constexpr int group_begin(bool three, int r2)
+{
+    int k = 0;
+    for (int dz = three ? -2 : 0; dz <= (three ? 2 : 0); ++dz)
+        for (int dy = -2; dy <= 2; ++dy)
+            for (int dx = -2; dx <= 2; ++dx) {
+                const int d = dz * dz + dy * dy + dx * dx;
+                if (d >= 1 && d <= kNearR2 && d < r2) ++k;
+            }
+    return k;
+}
+static_assert(group_begin(true, 2) == 6 && group_begin(false, 2) == 4 && group_begin(true, 9) == kNearN3 &&
+                  group_begin(false, 9) == kNearN2,
+              "nearest-site table groups");
+
 // Minimum resident CTAs per SM the kernels are compiled for (register cap).
 #ifndef QAI_DETECT_MINB
 #define QAI_DETECT_MINB 5
 #endif
 #ifndef QAI_NEAR_MINB
-#define QAI_NEAR_MINB 5
+#define QAI_NEAR_MINB 4
 #endif
 // Grid of the step-A kernel in resident waves.
 #ifndef QAI_DETECT_WAVES
 #define QAI_DETECT_WAVES 2
 #endif
 
-// Per-CTA collection of list entries before one global atomic per CTA.
-constexpr int kSignedCta = 1024;
+// Per-CTA collection of query-list entries before one global atomic per CTA.
 constexpr int kQueryCta = 2048;
+
+// The low bit of every nonzero 2-bit field of v.
+__device__ __forceinline__ uint32_t field_lsb(uint32_t v) { return (v | (v >> 1)) & 0x55555555u; }
 
 // Step A on one warp-segment of 128 points (4 per lane) of row `row`.
 // The q values one lane needs for its four points of a segment: the row and
@@ -107,8 +128,8 @@ __device__ __forceinline__ void load_segment(const LocalArgs& a, int row, int z,
 {
     const int lane = threadIdx.x & 31;
     const int nx = a.nx;
-    const int rbase = row * nx;
-    const int plane = a.ny * nx;
+    const int64_t rbase = (int64_t)row * nx;
+    const int64_t plane = (int64_t)a.ny * nx;
     const bool row_inner = y >= 1 && y <= a.ny - 2 && (RANK == 2 || (z >= 1 && z <= a.nz - 2));
     load4_i32(a.q + rbase, x0, nx, VEC, L.c);
 #pragma unroll
@@ -126,310 +147,183 @@ __device__ __forceinline__ void load_segment(const LocalArgs& a, int row, int z,
     if (lane == 31 && x0 + 4 < nx) L.edge = __ldg(a.q + rbase + x0 + 4);
 }
 
-template <int RANK, bool VEC>
-__device__ __forceinline__ void detect_segment(const LocalArgs& a, int row, int z, int y, int x0, const SegQ& L,
-                                               int32_t* sbuf, int* sn)
+// Step A for the lane's four points: b1 (bit j: point j on B1), sg (2-bit
+// sign code of S_B per point, 0 off B1) and, when MASK, the equal-q mask
+// byte per point (the byte map of the separable passes: bits z-, z+, y-, y+,
+// x-, x+, 0x3F off the interior).
+template <int RANK, bool MASK>
+__device__ __forceinline__ void step_a(const LocalArgs& a, int z, int y, int x0, const SegQ& L, unsigned& b1,
+                                       unsigned& sg, uint32_t& em)
 {
     const int lane = threadIdx.x & 31;
     const int nx = a.nx;
-    const int rbase = row * nx;
     const bool row_inner = y >= 1 && y <= a.ny - 2 && (RANK == 2 || (z >= 1 && z <= a.nz - 2));
     const int *c = L.c, *yl = L.yl, *yr = L.yr, *zl = L.zl, *zr = L.zr;
     int xm = __shfl_up_sync(kFull, c[3], 1);
     int xp = __shfl_down_sync(kFull, c[0], 1);
     if (lane == 0) xm = L.edge;
     if (lane == 31) xp = L.edge;
-    unsigned em = 0x3F3F3F3Fu;  // all equal: off the interior nothing is on B1
-    unsigned codes = 0;         // 2-bit sign code of S_B per point (B1 points only)
-    if (row_inner) {            // warp-uniform
-        // 32-bit sums are exact while every |q| < 2^27; OR of the raw values
-        // is below 2^27 exactly when all are in [0, 2^27), the common case
-        unsigned acc = (unsigned)xm | (unsigned)xp;
+    b1 = 0;
+    sg = 0;
+    em = 0x3F3F3F3Fu;
+    if (!row_inner) return;  // warp-uniform: off the interior nothing is on B1
+    // 32-bit sums are exact while every |q| < 2^27; the OR of the raw values
+    // is below 2^27 exactly when all are in [0, 2^27), the common case
+    unsigned acc = (unsigned)xm | (unsigned)xp;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc |= (unsigned)c[j] | (unsigned)yl[j] | (unsigned)yr[j] | (unsigned)zl[j] | (unsigned)zr[j];
-        bool narrow = acc < (1u << 27);
-        if (!__all_sync(kFull, narrow)) {
-            acc = (unsigned)(xm ^ (xm >> 31)) | (unsigned)(xp ^ (xp >> 31));
+    for (int j = 0; j < 4; ++j) acc |= (unsigned)c[j] | (unsigned)yl[j] | (unsigned)yr[j] | (unsigned)zl[j] | (unsigned)zr[j];
+    bool narrow = acc < (1u << 27);
+    if (!__all_sync(kFull, narrow)) {
+        acc = (unsigned)(xm ^ (xm >> 31)) | (unsigned)(xp ^ (xp >> 31));
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-                acc |= (unsigned)(c[j] ^ (c[j] >> 31)) | (unsigned)(yl[j] ^ (yl[j] >> 31)) |
-                       (unsigned)(yr[j] ^ (yr[j] >> 31)) | (unsigned)(zl[j] ^ (zl[j] >> 31)) |
-                       (unsigned)(zr[j] ^ (zr[j] >> 31));
-            narrow = acc < (1u << 27);
-        }
-        const bool wide = __any_sync(kFull, !narrow);
-        // interior along x: only the first and the last lanes of a row have
-        // points off it
-        const unsigned inner_bits = (x0 >= 1 && x0 + 4 <= nx - 1)
-                                        ? 0xFu
-                                        : ((x0 >= 1 && x0 <= nx - 2) ? 1u : 0u) | ((x0 + 1 >= 1 && x0 + 1 <= nx - 2) ? 2u : 0u) |
-                                              ((x0 + 2 <= nx - 2) ? 4u : 0u) | ((x0 + 3 <= nx - 2) ? 8u : 0u);
-        em = 0;
-        if (!wide && a.m.sign_rule == 0) {
-            // the common case in two steps: masks and the fast-varying test
-            // at every point, the sign only where a boundary keeps it
-            const int thm1 = a.m.grad_threshold - 1;
-            const unsigned lim = 2u * (unsigned)thm1;
-            unsigned keep = 0;  // bit j: point j is on B1 and not fast-varying
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int q0 = c[j];
-                const int l = j == 0 ? xm : c[j - 1];
-                const int r = j == 3 ? xp : c[j + 1];
-                // differing-neighbour bits: min(n ^ q0, 1) is 1 exactly where
-                // n != q0; the mask byte keeps the complement (equal bits)
-                unsigned ne = umin((unsigned)(l ^ q0), 1u) * 0x10u + umin((unsigned)(r ^ q0), 1u) * 0x20u;
-                bool fast = (unsigned)(r - l + thm1) > lim;
-                ne += umin((unsigned)(yl[j] ^ q0), 1u) * 0x4u + umin((unsigned)(yr[j] ^ q0), 1u) * 0x8u;
-                fast |= (unsigned)(yr[j] - yl[j] + thm1) > lim;
-                if (RANK == 3) {
-                    ne += umin((unsigned)(zl[j] ^ q0), 1u) + umin((unsigned)(zr[j] ^ q0), 1u) * 0x2u;
-                    fast |= (unsigned)(zr[j] - zl[j] + thm1) > lim;
-                }
-                const bool inner = (inner_bits >> j) & 1u;
-                keep |= (inner && ne != 0u && !fast) ? 1u << j : 0u;
-                em |= (0x3Fu ^ (inner ? ne : 0u)) << (8 * j);
-            }
-            if (__any_sync(kFull, keep != 0)) {
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    if (!((keep >> j) & 1u)) continue;
-                    const int l = j == 0 ? xm : c[j - 1];
-                    const int r = j == 3 ? xp : c[j + 1];
-                    int sum = l + r + yl[j] + yr[j] - 2 * RANK * c[j];
-                    if (RANK == 3) sum += zl[j] + zr[j];
-                    const unsigned cd = sum > 0 ? 1u : (sum < 0 ? 2u : 0u);
-                    em |= cd << (8 * j + 6);
-                    codes |= cd << (2 * j);
-                }
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const bool inner = (inner_bits >> j) & 1u;
-                const int l = j == 0 ? xm : c[j - 1];
-                const int r = j == 3 ? xp : c[j + 1];
-                unsigned mk;
-                bool site;
-                int code;
-                if (!wide) detect_point<RANK, false>(c[j], zl[j], zr[j], yl[j], yr[j], l, r, inner, a.m, mk, site, code);
-                else detect_point<RANK, true>(c[j], zl[j], zr[j], yl[j], yr[j], l, r, inner, a.m, mk, site, code);
-                const unsigned cd = (unsigned)code;  // 0 off the interior
-                em |= ((inner ? mk : 0x3Fu) | cd << 6) << (8 * j);
-                codes |= cd << (2 * j);
-            }
-        }
+        for (int j = 0; j < 4; ++j)
+            acc |= (unsigned)(c[j] ^ (c[j] >> 31)) | (unsigned)(yl[j] ^ (yl[j] >> 31)) |
+                   (unsigned)(yr[j] ^ (yr[j] >> 31)) | (unsigned)(zl[j] ^ (zl[j] >> 31)) |
+                   (unsigned)(zr[j] ^ (zr[j] >> 31));
+        narrow = acc < (1u << 27);
     }
+    const bool wide = __any_sync(kFull, !narrow);
+    // interior along x: only the first and the last lanes of a row have
+    // points off it
+    const unsigned inner_bits = (x0 >= 1 && x0 + 4 <= nx - 1)
+                                    ? 0xFu
+                                    : ((x0 >= 1 && x0 <= nx - 2) ? 1u : 0u) | ((x0 + 1 >= 1 && x0 + 1 <= nx - 2) ? 2u : 0u) |
+                                          ((x0 + 2 <= nx - 2) ? 4u : 0u) | ((x0 + 3 <= nx - 2) ? 8u : 0u);
+    if (!MASK && !wide && a.m.sign_rule == 0) {
+        // the common case in two steps: B1 and the fast-varying test at
+        // every point, the sign only where a boundary keeps it
+        const int thm1 = a.m.grad_threshold - 1;
+        const unsigned lim = 2u * (unsigned)thm1;
+        unsigned keep = 0;  // bit j: point j is on B1 and not fast-varying
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int q0 = c[j];
+            const int l = j == 0 ? xm : c[j - 1];
+            const int r = j == 3 ? xp : c[j + 1];
+            unsigned d = ((unsigned)l ^ (unsigned)q0) | ((unsigned)r ^ (unsigned)q0) |
+                         ((unsigned)yl[j] ^ (unsigned)q0) | ((unsigned)yr[j] ^ (unsigned)q0);
+            bool fast = (unsigned)(r - l + thm1) > lim || (unsigned)(yr[j] - yl[j] + thm1) > lim;
+            if (RANK == 3) {
+                d |= ((unsigned)zl[j] ^ (unsigned)q0) | ((unsigned)zr[j] ^ (unsigned)q0);
+                fast = fast || (unsigned)(zr[j] - zl[j] + thm1) > lim;
+            }
+            const bool site = ((inner_bits >> j) & 1u) && d != 0u;
+            b1 |= site ? 1u << j : 0u;
+            keep |= (site && !fast) ? 1u << j : 0u;
+        }
+        if (__any_sync(kFull, keep != 0)) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (!((keep >> j) & 1u)) continue;
+                const int l = j == 0 ? xm : c[j - 1];
+                const int r = j == 3 ? xp : c[j + 1];
+                int sum = l + r + yl[j] + yr[j] - 2 * RANK * c[j];
+                if (RANK == 3) sum += zl[j] + zr[j];
+                sg |= (sum > 0 ? 1u : (sum < 0 ? 2u : 0u)) << (2 * j);
+            }
+        }
+        return;
+    }
+    em = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const bool inner = (inner_bits >> j) & 1u;
+        const int l = j == 0 ? xm : c[j - 1];
+        const int r = j == 3 ? xp : c[j + 1];
+        unsigned mk;
+        bool site;
+        int code;
+        if (!wide) detect_point<RANK, false>(c[j], zl[j], zr[j], yl[j], yr[j], l, r, inner, a.m, mk, site, code);
+        else detect_point<RANK, true>(c[j], zl[j], zr[j], yl[j], yr[j], l, r, inner, a.m, mk, site, code);
+        b1 |= site ? 1u << j : 0u;
+        sg |= (unsigned)code << (2 * j);  // 0 off the interior
+        em |= ((inner ? mk : 0x3Fu) | (unsigned)code << 6) << (8 * j);
+    }
+}
+
+// Bits 0, 1, 2, 3 of b to bits 0, 2, 4, 6.
+__device__ __forceinline__ unsigned spread4(unsigned b)
+{
+    return (b & 1u) | ((b & 2u) << 1) | ((b & 4u) << 2) | ((b & 8u) << 3);
+}
+
+template <int RANK, bool VEC>
+__device__ __forceinline__ void detect_segment(const LocalArgs& a, int row, int z, int y, int x0, const SegQ& L,
+                                               unsigned& nsigned)
+{
+    const int nx = a.nx;
+    const int64_t rbase = (int64_t)row * nx;
+    unsigned b1, sg;
+    uint32_t em;
+    step_a<RANK, false>(a, z, y, x0, L, b1, sg, em);
     // outputs where Dist2 does not matter: the expressions of compensate()
     // (with C = +0 the fma is the product)
     float o[4];
-    if (__any_sync(kFull, codes != 0)) {
+    if (__any_sync(kFull, sg != 0)) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const unsigned cd = (codes >> (2 * j)) & 3u;
+            const unsigned cd = (sg >> (2 * j)) & 3u;
             const float cc = (cd == 1u ? 1.0f : (cd == 2u ? -1.0f : 0.0f)) * a.m.eta_eb;
-            o[j] = a.m.output_c ? cc : fmaf((float)c[j], a.m.two_eb, cc);
+            o[j] = a.m.output_c ? cc : fmaf((float)L.c[j], a.m.two_eb, cc);
         }
+        nsigned += __popc(field_lsb(sg));
     } else {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) o[j] = a.m.output_c ? 0.0f : (float)c[j] * a.m.two_eb;
+        for (int j = 0; j < 4; ++j) o[j] = a.m.output_c ? 0.0f : (float)L.c[j] * a.m.two_eb;
     }
     if (VEC) {
-        if (x0 < nx) {
-            *reinterpret_cast<uint32_t*>(a.eqm + rbase + x0) = em;
-            *reinterpret_cast<float4*>(a.out + rbase + x0) = make_float4(o[0], o[1], o[2], o[3]);
-        }
+        if (x0 < nx) *reinterpret_cast<float4*>(a.out + rbase + x0) = make_float4(o[0], o[1], o[2], o[3]);
     } else {
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-            if (x0 + j < nx) {
-                a.eqm[rbase + x0 + j] = (uint8_t)(em >> (8 * j));
-                a.out[rbase + x0 + j] = o[j];
-            }
+            if (x0 + j < nx) a.out[rbase + x0 + j] = o[j];
     }
-    // B1 points with S != 0: the signed set lists them (Dist1 = 0 there is
-    // not stored; the mask byte tells B1), until the CTA's buffer is full
-    if (codes && *static_cast<volatile int*>(sn) <= kSignedCta) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if (((codes >> (2 * j)) & 3u) == 0u) continue;
-            const int k = atomicAdd(sn, 1);
-            if (k < kSignedCta) sbuf[k] = rbase + x0 + j;
-        }
-    }
+    // the code byte of the four points (0 past nx, up to the row's last word)
+    if (x0 < 16 * a.wpr)
+        reinterpret_cast<uint8_t*>(a.codes)[(int64_t)row * 4 * a.wpr + (x0 >> 2)] = (uint8_t)(spread4(b1) + sg);
 }
 
 template <int RANK, bool VEC>
 __global__ void __launch_bounds__(256, QAI_DETECT_MINB) k_detect(LocalArgs a)
 {
     wait_prior_grid();
-    __shared__ int32_t sbuf[kSignedCta];
-    __shared__ int sn, sbase;
-    if (threadIdx.x == 0) sn = 0;
-    __syncthreads();
     const int rows = a.nz * a.ny;
     const int wstride = gridDim.x * (blockDim.x >> 5);
     const int lx = 4 * (int)(threadIdx.x & 31);
+    unsigned nsigned = 0;
     for (int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += wstride) {
         const int z = RANK == 3 ? row / a.ny : 0;
         const int y = row - z * a.ny;
         for (int x0 = lx; x0 - lx < a.nx; x0 += 128) {
             SegQ b;
             load_segment<RANK, VEC>(a, row, z, y, x0, b);
-            detect_segment<RANK, VEC>(a, row, z, y, x0, b, sbuf, &sn);
+            detect_segment<RANK, VEC>(a, row, z, y, x0, b, nsigned);
         }
     }
-
-    __syncthreads();
-    const int n = sn;
-    if (threadIdx.x == 0) {
-        sbase = -1;
-        if (n > kSignedCta) *static_cast<volatile int*>(a.ctr + kCtrSignedOver) = 1;
-        else if (n > 0) sbase = atomicAdd(a.ctr + kCtrSigned, n);
-    }
-    __syncthreads();
-    if (sbase >= 0)
-        for (int i = threadIdx.x; i < n && sbase + i < a.scap; i += blockDim.x) a.slist[sbase + i] = sbuf[i];
+    // B1 points with S != 0: one atomic per warp that has any
+    nsigned = __reduce_add_sync(kFull, nsigned);
+    if ((threadIdx.x & 31) == 0 && nsigned) atomicAdd(a.ctr + kCtrSigned, (int)nsigned);
 }
 
-// The nearest B1 point of p (off B1): its squared distance and the sign code
-// it carries, or r2 = -1 when none lies within squared distance 8.
-// The nearest B1 point of p (off B1) among table entries k0.. (the first 6,
-// or 4 in 2-D, are the squared distance 1): its squared distance and the sign
-// code it carries, or r2 = -1 when none lies within squared distance 8. The table is scanned in chunks of eight entries whose
-// loads are issued together; the first B1 point in table order is the answer.
-template <int RANK>
-__device__ __forceinline__ void nearest_site(const LocalArgs& a, int p, int z, int y, int x, int k0, int& r2,
-                                             unsigned& code)
+// Word k of packed row `prow` (0 past the row, or where ok is false).
+__device__ __forceinline__ uint32_t pword(const uint32_t* m, int64_t prow, int k, int wpr, bool ok)
 {
-    const int plane = a.ny * a.nx;
-    const int* tab = RANK == 3 ? c_near.off3 : c_near.off2;
-    constexpr int ntab = RANK == 3 ? kNearN3 : kNearN2;
-    r2 = -1;
-    code = 0;
-    for (; k0 < ntab; k0 += 8) {
-        unsigned e[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            e[u] = 0x3Fu;
-            const int k = k0 + u;
-            if (k >= ntab) continue;
-            const int o = tab[k];
-            const int dx = (int)(int8_t)(o & 0xFF), dy = (int)(int8_t)((o >> 8) & 0xFF);
-            const int dz = (int)(int8_t)((o >> 16) & 0xFF);
-            const bool in = (unsigned)(x + dx) < (unsigned)a.nx && (unsigned)(y + dy) < (unsigned)a.ny &&
-                            (RANK == 2 || (unsigned)(z + dz) < (unsigned)a.nz);
-            if (in) e[u] = __ldg(a.eqm + p + dz * plane + dy * a.nx + dx);
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            if (k0 + u < ntab && (e[u] & 0x3Fu) != 0x3Fu) {
-                r2 = (int)((unsigned)tab[k0 + u] >> 24);
-                code = e[u] >> 6;
-                return;
-            }
-        }
-    }
+    return ok && k >= 0 && k < wpr ? __ldg(m + prow * wpr + k) : 0u;
 }
 
-// Four bytes of a row at x0.. (0x3F, "not on B1", past the row end).
-__device__ __forceinline__ uint32_t load4_em(const uint8_t* row, int x0, int nx, bool vec)
+// The word of row `prow` shifted by dx points, from the lane's word w at k
+// (the neighbour words come from the adjacent lanes, or are loaded by the
+// first and the last lane). Every lane of the warp must take part.
+__device__ __forceinline__ uint32_t pshift(const uint32_t* m, int64_t prow, int k, int wpr, bool ok, uint32_t w,
+                                           int dx)
 {
-    if (vec) return x0 < nx ? __ldg(reinterpret_cast<const uint32_t*>(row + x0)) : 0x3F3F3F3Fu;
-    uint32_t w = 0x3F3F3F3Fu;
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-        if (x0 + j < nx) w = (w & ~(0xFFu << (8 * j))) | (uint32_t)__ldg(row + x0 + j) << (8 * j);
+    const int lane = threadIdx.x & 31;
+    uint32_t wl = __shfl_up_sync(kFull, w, 1), wr = __shfl_down_sync(kFull, w, 1);
+    if (lane == 0) wl = pword(m, prow, k - 1, wpr, ok);
+    if (lane == 31) wr = pword(m, prow, k + 1, wpr, ok);
+    if (dx > 0) return __funnelshift_r(w, wr, 2 * dx);
+    if (dx < 0) return __funnelshift_l(wl, w, -2 * dx);
     return w;
-}
-
-// Byte k = 0xFF where byte k of the mask word marks a B1 point (some of its
-// six equal-q bits clear): t = the clear bits, at most 0x3F per byte, so
-// t + 0x7F sets bit 7 of a byte exactly when t is not zero, with no carry;
-// the byte permute with selector nibbles 8..B copies each byte's bit 7 over
-// the byte.
-__device__ __forceinline__ uint32_t site_bytes(uint32_t w)
-{
-    const uint32_t t = (~w & 0x3F3F3F3Fu) + 0x7F7F7F7Fu;
-    uint32_t r;
-    asm("prmt.b32 %0, %1, 0, 0xBA98;" : "=r"(r) : "r"(t));  // sign-replicating byte permute
-    return r;
-}
-
-// S bytes of the four points xk .. xk + 3 of row `row`, with Dist1 and the
-// query-list entries of those that are queries (S != 0 off B1). cw holds
-// their mask bytes, pw and nw the words either side (for the x - 1 and x + 1
-// neighbours), ylw .. zrw the words of the four neighbour rows (0x3F: no
-// point). The six neighbours at squared distance 1 are tested for the four
-// points at once, byte-wise, in the tie order z-, y-, x-, x+, y+, z+
-// (increasing linear index); a point with none of them on B1 scans the rest
-// of the table alone.
-template <int RANK>
-__device__ __forceinline__ uint32_t near_word(const LocalArgs& a, int row, int z, int y, int xk, uint32_t cw,
-                                              uint32_t pw, uint32_t nw, uint32_t ylw, uint32_t yrw, uint32_t zlw,
-                                              uint32_t zrw, Query* qbuf, int* qn, bool& fail)
-{
-    const uint32_t own = site_bytes(cw), pm = site_bytes(pw), nm = site_bytes(nw);
-    const uint32_t xlw = __byte_perm(pw, cw, 0x6543), xlm = __byte_perm(pm, own, 0x6543);  // x - 1
-    const uint32_t xrw = __byte_perm(cw, nw, 0x4321), xrm = __byte_perm(own, nm, 0x4321);  // x + 1
-    // the first B1 neighbour in tie order: select from the last to the first
-    uint32_t found = 0, pick = 0x3F3F3F3Fu;
-    auto take = [&](uint32_t w, uint32_t m) {
-        pick = (w & m) | (pick & ~m);
-        found |= m;
-    };
-    take(zrw, site_bytes(zrw));
-    take(yrw, site_bytes(yrw));
-    take(xrw, xrm);
-    take(xlw, xlm);
-    take(ylw, site_bytes(ylw));
-    take(zlw, site_bytes(zlw));
-    // codes: own on B1, else the neighbour's; Dist1 = 1 where resolved off
-    // B1 (bytes past the row end, and x - 1 of x = 0, read 0x3F)
-    const int nvalid = min(4, a.nx - xk);
-    const uint32_t valid = nvalid >= 4 ? 0xFFFFFFFFu : (nvalid <= 0 ? 0u : (1u << (8 * nvalid)) - 1u);
-    uint32_t cw2 = ((own & cw) | (~own & pick)) >> 6 & 0x03030303u;
-    const uint32_t need = ~own & ~found & valid;  // no site within r2 = 1: scan the table
-    uint32_t d1w = ~own & 0x01010101u;
-    if (need) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if (!((need >> (8 * j)) & 0xFFu)) continue;
-            int r2;
-            unsigned code;
-            nearest_site<RANK>(a, row * a.nx + xk + j, z, y, xk + j, RANK == 3 ? 6 : 4, r2, code);
-            if (r2 < 0) {
-                fail = true;
-                r2 = 0;
-                code = 0;
-            }
-            cw2 = (cw2 & ~(0xFFu << (8 * j))) | code << (8 * j);
-            d1w = (d1w & ~(0xFFu << (8 * j))) | (uint32_t)r2 << (8 * j);
-        }
-    }
-    // S bytes: code 1 -> +1, code 2 -> -1
-    const uint32_t pos = cw2 & 0x01010101u, neg = (cw2 >> 1) & 0x01010101u;
-    // queries: S != 0 off B1
-    const uint32_t qmask = (pos | neg) & ~own & valid;
-    if (qmask) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if (!((qmask >> (8 * j)) & 1u)) continue;
-            const int p = row * a.nx + xk + j;
-            const int r2 = (int)((d1w >> (8 * j)) & 0xFFu);
-            const unsigned code = (cw2 >> (8 * j)) & 3u;
-            a.dist1[p] = r2;
-            const Query qe{p, (r2 << 2) | (int)code};
-            const int kq = atomicAdd(qn, 1);
-            if (kq < kQueryCta) {
-                qbuf[kq] = qe;
-            } else {
-                const int g = atomicAdd(a.ctr + kCtrQueries, 1);
-                if (g < a.qcap) a.qlist[g] = qe;
-            }
-        }
-    }
-    return pos | (neg * 0xFFu);
 }
 
 // The CTA's queries to the global list (one atomic), and the flag of a point
@@ -444,8 +338,8 @@ __device__ __forceinline__ void near_flush(const LocalArgs& a, const Query* qbuf
     for (int i = threadIdx.x; i < n && *qbase + i < a.qcap; i += blockDim.x) a.qlist[*qbase + i] = qbuf[i];
 }
 
-// S at every point, Dist1 where S != 0 off B1, and the queries, for rows of
-// any length: one warp per row, four points per lane and step.
+// S at every point, Dist1 where S != 0 off B1, and the queries: one warp per
+// row, one packed word (16 points) per lane and step.
 template <int RANK>
 __global__ void __launch_bounds__(256, QAI_NEAR_MINB) k_near(LocalArgs a)
 {
@@ -456,115 +350,156 @@ __global__ void __launch_bounds__(256, QAI_NEAR_MINB) k_near(LocalArgs a)
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int rows = a.nz * a.ny;
-    const int plane = a.ny * a.nx;
+    const int wpr = a.wpr;
+    const uint32_t* cm = a.codes;
     const int wstride = gridDim.x * (blockDim.x >> 5);
+    const int* tab = RANK == 3 ? c_near.off3 : c_near.off2;
     bool fail = false;
-    const uint32_t none = 0x3F3F3F3Fu;
     for (int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += wstride) {
         const int z = RANK == 3 ? row / a.ny : 0;
         const int y = row - z * a.ny;
-        const uint8_t* er = a.eqm + (int64_t)row * a.nx;
-        int8_t* sr = a.s + (int64_t)row * a.nx;
-        uint32_t carry = none;  // the word of the previous step (its byte 3 is x - 1 of byte 0)
-        for (int xs = 0; xs < a.nx; xs += 128) {
-            const int x0 = xs + 4 * lane;
-            const uint32_t cw = load4_em(er, x0, a.nx, false);
-            const uint32_t ylw = y > 0 ? load4_em(er - a.nx, x0, a.nx, false) : none;
-            const uint32_t yrw = y < a.ny - 1 ? load4_em(er + a.nx, x0, a.nx, false) : none;
-            const uint32_t zlw = RANK == 3 && z > 0 ? load4_em(er - plane, x0, a.nx, false) : none;
-            const uint32_t zrw = RANK == 3 && z < a.nz - 1 ? load4_em(er + plane, x0, a.nx, false) : none;
-            uint32_t prev = __shfl_up_sync(kFull, cw, 1);
-            uint32_t next = __shfl_down_sync(kFull, cw, 1);
-            const uint32_t last = __shfl_sync(kFull, cw, 31);
-            if (lane == 0) prev = carry;
-            if (lane == 31) next = x0 + 4 < a.nx ? (uint32_t)__ldg(er + x0 + 4) : 0x3Fu;
-            carry = last;
-            const uint32_t sw = near_word<RANK>(a, row, z, y, x0, cw, prev, next, ylw, yrw, zlw, zrw, qbuf, &qn, fail);
+        for (int ks = 0; ks < wpr; ks += 32) {
+            const int k = ks + lane;
+            const bool in = k < wpr;
+            const uint32_t w = pword(cm, row, k, wpr, true);
+            const int nv = a.nx - 16 * k;  // fields of this word inside the row
+            const uint32_t valid = !in ? 0u : (nv >= 16 ? 0xFFFFFFFFu : (1u << (2 * nv)) - 1u);
+            const uint32_t site = field_lsb(w);
+            uint32_t need = ~site & 0x55555555u & valid;  // points off B1
+            uint32_t s = w - site;                        // B1: the code less one is S_B
+            if (__any_sync(kFull, need != 0)) {
+                uint32_t res = 0;     // the code of the site each resolved point took
+                uint32_t grp[kNearR2 + 1];  // points resolved at squared distance r2
+                const uint32_t need0 = need;
+                // squared distance 1, in tie order z-, y-, x-, x+, y+, z+
+                auto take = [&](uint32_t v) {
+                    const uint32_t t = field_lsb(v) & need;
+                    res |= v & (t * 3u);
+                    need &= ~t;
+                };
+                const bool zm = RANK == 3 && z > 0, zp = RANK == 3 && z < a.nz - 1;
+                const uint32_t wzm = pword(cm, row - a.ny, k, wpr, zm);
+                const uint32_t wym = pword(cm, row - 1, k, wpr, y > 0);
+                const uint32_t wyp = pword(cm, row + 1, k, wpr, y < a.ny - 1);
+                const uint32_t wzp = pword(cm, row + a.ny, k, wpr, zp);
+                const uint32_t wxm = pshift(cm, row, k, wpr, true, w, -1);
+                const uint32_t wxp = pshift(cm, row, k, wpr, true, w, 1);
+                if (RANK == 3) take(wzm);
+                take(wym);
+                take(wxm);
+                take(wxp);
+                take(wyp);
+                if (RANK == 3) take(wzp);
+                grp[1] = need0 & ~need;
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (x0 + j < a.nx) sr[x0 + j] = (int8_t)(sw >> (8 * j));
+                for (int r = 2; r <= kNearR2; ++r) grp[r] = 0;
+                if (__any_sync(kFull, need != 0)) {
+                    // squared distances 2..8: the rest of the table in order
+#pragma unroll
+                    for (int r = 2; r <= kNearR2; ++r) {
+                        const uint32_t before = need;
+                        const int e0 = group_begin(RANK == 3, r), e1 = group_begin(RANK == 3, r + 1);
+                        for (int e = e0; e < e1; ++e) {
+                            const int o = tab[e];
+                            const int dx = (int)(int8_t)(o & 0xFF), dy = (int)(int8_t)((o >> 8) & 0xFF);
+                            const int dz = (int)(int8_t)((o >> 16) & 0xFF);
+                            const bool ok = (unsigned)(y + dy) < (unsigned)a.ny &&
+                                            (RANK == 2 || (unsigned)(z + dz) < (unsigned)a.nz);
+                            const int64_t prow = (int64_t)row + (int64_t)dz * a.ny + dy;
+                            const uint32_t wr = pword(cm, prow, k, wpr, ok);
+                            take(pshift(cm, prow, k, wpr, ok, wr, dx));
+                        }
+                        grp[r] = before & ~need;
+                    }
+                    fail |= need != 0;
+                }
+                const uint32_t resolved = need0 & ~need;
+                const uint32_t soff = res - resolved;  // the site's code less one: S
+                s |= soff;
+                uint32_t qm = field_lsb(soff);         // queries: S != 0 off B1
+                while (qm) {
+                    const int f = __ffs(qm) - 1;
+                    qm &= qm - 1;
+                    int r2 = 1;
+#pragma unroll
+                    for (int r = kNearR2; r >= 1; --r)
+                        if ((grp[r] >> f) & 1u) r2 = r;
+                    const int code = (int)((soff >> f) & 3u);
+                    const int p = row * a.nx + 16 * k + (f >> 1);
+                    a.dist1[p] = r2;
+                    const Query qe{p, (r2 << 2) | code};
+                    const int kq = atomicAdd(&qn, 1);
+                    if (kq < kQueryCta) {
+                        qbuf[kq] = qe;
+                    } else {
+                        const int g = atomicAdd(a.ctr + kCtrQueries, 1);
+                        if (g < a.qcap) a.qlist[g] = qe;
+                    }
+                }
+            }
+            if (in) a.spk[(int64_t)row * wpr + k] = s;
         }
     }
     near_flush(a, qbuf, &qn, &qbase, fail);
 }
 
-// The same for rows of 16-byte multiples, sparse in the points off B1 (most
-// points of a field with a dense B1 are on it and keep their own sign). A
-// lane reads 16 mask bytes of the row per step (one 128-bit load) and writes
-// the S of its B1 points; the words holding a point off B1 are gathered
-// across the warp (a ballot per word position) and dealt one per lane to
-// near_word, which reads the neighbour words it needs. The S words meet in
-// shared memory before the lane's 128-bit store.
-template <int RANK>
-__global__ void __launch_bounds__(256, QAI_NEAR_MINB) k_near_sparse(LocalArgs a)
+// The byte maps of the separable passes from q and the packed S: the equal-q
+// mask with the sign code of S_B (row pass 1's eqm) and S as int8, after the
+// local first EDT (when the separable one ran, its passes wrote them). mode
+// 1: only when the separable second EDT takes over (the dense flag set);
+// mode 2: always (the adjoint reads them).
+template <int RANK, bool VEC>
+__global__ void __launch_bounds__(256) k_expand(LocalArgs a, int mode)
 {
     wait_prior_grid();
-    __shared__ Query qbuf[kQueryCta];
-    __shared__ uint32_t swb[8][4 * 32];
-    __shared__ int qn, qbase;
-    if (threadIdx.x == 0) qn = 0;
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    uint32_t* sw = swb[threadIdx.x >> 5];  // word k of lane l at [32 k + l]
+    {
+        const volatile int* ctr = a.ctr;
+        if (ctr[kCtrLocalFail] != 0 || (mode == 1 && ctr[kCtrDense] == 0)) return;
+    }
     const int rows = a.nz * a.ny;
-    const int plane = a.ny * a.nx;
     const int wstride = gridDim.x * (blockDim.x >> 5);
-    bool fail = false;
-    const uint32_t none = 0x3F3F3F3Fu;
+    const int lx = 4 * (int)(threadIdx.x & 31);
     for (int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += wstride) {
         const int z = RANK == 3 ? row / a.ny : 0;
         const int y = row - z * a.ny;
-        const uint8_t* er = a.eqm + (int64_t)row * a.nx;
-        int8_t* sr = a.s + (int64_t)row * a.nx;
-        for (int xs = 0; xs < a.nx; xs += 512) {
-            const int x0 = xs + 16 * lane;
-            const bool in = x0 < a.nx;  // rows are 16-byte multiples: four words or none
-            const uint4 c = in ? __ldg(reinterpret_cast<const uint4*>(er + x0)) : make_uint4(none, none, none, none);
-            unsigned off[4];  // word position k: the lanes whose word k holds a point off B1
+        const int64_t rbase = (int64_t)row * a.nx;
+        for (int x0 = lx; x0 - lx < a.nx; x0 += 128) {
+            SegQ b;
+            load_segment<RANK, VEC>(a, row, z, y, x0, b);
+            unsigned b1, sg;
+            uint32_t em;
+            step_a<RANK, true>(a, z, y, x0, b, b1, sg, em);
+            const uint32_t sw = x0 < 16 * a.wpr ? __ldg(a.spk + (int64_t)row * a.wpr + (x0 >> 4)) >> (2 * (x0 & 15)) : 0u;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const uint32_t cw = k == 0 ? c.x : (k == 1 ? c.y : (k == 2 ? c.z : c.w));
-                const uint32_t own = site_bytes(cw);
-                const uint32_t cw2 = (own & cw) >> 6 & 0x03030303u;  // B1 points: their own code
-                const uint32_t pos = cw2 & 0x01010101u, neg = (cw2 >> 1) & 0x01010101u;
-                sw[32 * k + lane] = pos | (neg * 0xFFu);
-                off[k] = __ballot_sync(kFull, in && own != 0xFFFFFFFFu);
+            for (int j = 0; j < 4; ++j) {
+                if (x0 + j >= a.nx) continue;
+                const unsigned c = (sw >> (2 * j)) & 3u;
+                a.eqm[rbase + x0 + j] = (uint8_t)(em >> (8 * j));
+                a.s[rbase + x0 + j] = (int8_t)(c == 1u ? 1 : (c == 2u ? -1 : 0));
             }
-            const int n0 = __popc(off[0]), n1 = __popc(off[1]), n2 = __popc(off[2]), n3 = __popc(off[3]);
-            const int total = n0 + n1 + n2 + n3;
-            __syncwarp();
-            for (int e = lane; e - lane < total; e += 32) {
-                if (e >= total) continue;
-                int k, r;
-                if (e < n0) {
-                    k = 0; r = e;
-                } else if (e < n0 + n1) {
-                    k = 1; r = e - n0;
-                } else if (e < n0 + n1 + n2) {
-                    k = 2; r = e - n0 - n1;
-                } else {
-                    k = 3; r = e - n0 - n1 - n2;
-                }
-                const unsigned bk = k == 0 ? off[0] : (k == 1 ? off[1] : (k == 2 ? off[2] : off[3]));
-                const int src = (int)__fns(bk, 0, r + 1);  // the lane that holds the word
-                const int xk = xs + 16 * src + 4 * k;
-                auto w32 = [&](const uint8_t* rp) { return __ldg(reinterpret_cast<const uint32_t*>(rp + xk)); };
-                const uint32_t cw = w32(er);
-                const uint32_t pw = xk >= 4 ? w32(er - 4) : none;
-                const uint32_t nw = xk + 4 < a.nx ? w32(er + 4) : none;
-                const uint32_t ylw = y > 0 ? w32(er - a.nx) : none;
-                const uint32_t yrw = y < a.ny - 1 ? w32(er + a.nx) : none;
-                const uint32_t zlw = RANK == 3 && z > 0 ? w32(er - plane) : none;
-                const uint32_t zrw = RANK == 3 && z < a.nz - 1 ? w32(er + plane) : none;
-                sw[32 * k + src] = near_word<RANK>(a, row, z, y, xk, cw, pw, nw, ylw, yrw, zlw, zrw, qbuf, &qn, fail);
-            }
-            __syncwarp();
-            if (in)
-                *reinterpret_cast<uint4*>(sr + x0) = make_uint4(sw[lane], sw[32 + lane], sw[64 + lane], sw[96 + lane]);
-            __syncwarp();
         }
     }
-    near_flush(a, qbuf, &qn, &qbase, fail);
+}
+
+// The packed S from the int8 S map of the separable first EDT (gated: when
+// the local first EDT fell short; else always).
+__global__ void __launch_bounds__(256) k_pack_s(LocalArgs a, int gated)
+{
+    wait_prior_grid();
+    if (gated && *static_cast<const volatile int*>(a.ctr + kCtrLocalFail) == 0) return;
+    const int64_t words = (int64_t)a.nz * a.ny * a.wpr;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += stride) {
+        const int64_t row = i / a.wpr;
+        const int x0 = 16 * (int)(i - row * a.wpr);
+        const int8_t* sr = a.s + row * a.nx;
+        uint32_t w = 0;
+        for (int j = 0; j < 16 && x0 + j < a.nx; ++j) {
+            const int v = sr[x0 + j];
+            w |= (v > 0 ? 1u : (v < 0 ? 2u : 0u)) << (2 * j);
+        }
+        a.spk[i] = w;
+    }
 }
 
 }  // namespace
@@ -592,13 +527,22 @@ cudaError_t launch_local_detect(const LocalArgs& a, cudaStream_t st)
 
 cudaError_t launch_local_near(const LocalArgs& a, cudaStream_t st)
 {
-    auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
-    const bool wide = (a.nx % 16 == 0) && al(a.eqm) && al(a.s);  // 16-byte rows
+    auto run = [&](auto kern) { return launch_chained(kern, dim3(one_wave(kern)), dim3(256), 0, st, a); };
+    return a.rank == 3 ? run(k_near<3>) : run(k_near<2>);
+}
+
+cudaError_t launch_local_expand(const LocalArgs& a, int mode, cudaStream_t st)
+{
     auto run = [&](auto kern) {
-        return launch_chained(kern, dim3(one_wave(kern)), dim3(256), 0, st, a);
+        return launch_chained(kern, dim3(one_wave(kern)), dim3(256), 0, st, a, mode);
     };
-    if (a.rank == 3) return wide ? run(k_near_sparse<3>) : run(k_near<3>);
-    return wide ? run(k_near_sparse<2>) : run(k_near<2>);
+    if (a.rank == 3) return a.vec ? run(k_expand<3, true>) : run(k_expand<3, false>);
+    return a.vec ? run(k_expand<2, true>) : run(k_expand<2, false>);
+}
+
+cudaError_t launch_local_pack_s(const LocalArgs& a, bool gated, cudaStream_t st)
+{
+    return launch_chained(k_pack_s, dim3(one_wave(k_pack_s)), dim3(256), 0, st, a, gated ? 1 : 0);
 }
 
 }  // namespace qai

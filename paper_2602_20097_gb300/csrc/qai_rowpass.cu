@@ -167,6 +167,15 @@ __device__ __forceinline__ void rowpass_row(const RowArgs& a, const int row, uns
                     for (int j = 0; j < 4; ++j)
                         if (x0 + j < nx) a.eqm[rbase + x0 + j] = (uint8_t)(eq >> (8 * j));
                 }
+            } else {
+                // rows off the interior: nothing is on B1, the all-equal mask
+                if (VEC) {
+                    if (x0 < nx) *reinterpret_cast<uint32_t*>(a.eqm + rbase + x0) = 0x3F3F3F3Fu;
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (x0 + j < nx) a.eqm[rbase + x0 + j] = 0x3Fu;
+                }
             }
             if (a.out_pre) {
                 // the output wherever Dist2 does not matter: on B1 the weight

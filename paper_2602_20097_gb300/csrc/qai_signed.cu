@@ -3,22 +3,21 @@
 //
 // Step E adds C = S w eta eps (Sec. VI-E). Where S = 0 the output is D'
 // whatever Dist2 is, and on B1 (Dist1 = 0) the weight is 1 whatever Dist2 is
-// (the boundary value eta eps); row pass 1 writes both of these outputs. Dist2
-// is needed only at the queries -- points with S != 0 off B1 -- which the last
-// pass of the first EDT lists, with the B1 points that have S != 0. These
-// kernels then give the exact Dist2 of every query, Eq. 2 over the
-// sign-flipping boundary B2 of Algorithm 3:
+// (the boundary value eta eps); the step-A kernel writes both of these
+// outputs. Dist2 is needed only at the queries -- points with S != 0 off
+// B1 -- which the first EDT lists with their Dist1 and sign. These kernels
+// give the exact Dist2 of every query, Eq. 2 over the sign-flipping boundary
+// B2 of Algorithm 3:
 //
-//   k_query    a shell search around the query (one thread each, then one
-//              warp, then one CTA each for the queries the phase before
-//              left): lattice offsets in order of squared length,
-//              GetBoundary(S) evaluated at each candidate from S and the
-//              equal-q mask; the first hit is the minimum. A query with no B2
-//              site within the search radius is left to the brute-force
-//              search.
-//   k_b2sites  (only when such queries exist) lists the B2 sites from the
-//              signed points and their axis neighbours, or, when the list of
-//              signed points overflowed, from a pass over the whole field;
+//   k_b2map    GetBoundary(S) at every interior point, from the packed S map
+//              (q is read only where two neighbours' S differ, for the
+//              same-q test of the default rule): the B2 bitmap, 1 bit a point.
+//   k_query    one thread per query: the 3 x 3 x 3 block of the bitmap around
+//              it (every point within squared distance 3, and no other).
+//   k_query_mid one warp per query the first left: the bitmap rows within
+//              radius R (12 in 3-D, 31 in 2-D) of it, each row's nearest bit
+//              to x by bit scans; the minimum is exact when it is <= R^2.
+//   k_b2list   (only when queries remain) lists the B2 sites from the bitmap;
 //   k_brute    (idem) min over the site list for each remaining query.
 //
 // A count over a capacity, or a brute-force product over its budget, sets the
@@ -33,81 +32,60 @@ namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
-// Lattice offsets in order of squared length, then (dz, dy, dx):
-// (r2 << 24) | (dz & 0xFF) << 16 | (dy & 0xFF) << 8 | (dx & 0xFF), so r2 <=
-// 255. off3 spans three axes up to squared length kTableR2 (radius 6), off2
-// two axes (dz = 0) up to kTableR2_2 (radius 15.9); the search phases take
-// at most 1184 offsets (160 by a warp, 1024 by a CTA).
-constexpr int kTableR2 = 36;
-constexpr int kTableR = 6;
-constexpr int kTableR2_2 = 255;
-constexpr int kTableR_2 = 15;
-constexpr int kN3 = 925, kN2 = 793;
-struct OffsetTable {
-    int off3[kN3];
-    int off2[kN2];
-};
-constexpr int pack_offset(int r2, int dz, int dy, int dx)
-{
-    return (int)(((unsigned)r2 << 24) | ((unsigned)(dz & 0xFF) << 16) | ((unsigned)(dy & 0xFF) << 8) |
-                 (unsigned)(dx & 0xFF));
-}
-constexpr int isqrt_c(int v)
-{
-    int r = 0;
-    while ((r + 1) * (r + 1) <= v) ++r;
-    return r;
-}
-constexpr OffsetTable make_offsets()
-{
-    OffsetTable t{};
-    int n3 = 0, n2 = 0;
-    for (int r2 = 0; r2 <= kTableR2; ++r2)
-        for (int dz = -kTableR; dz <= kTableR; ++dz)
-            for (int dy = -kTableR; dy <= kTableR; ++dy)
-                for (int dx = -kTableR; dx <= kTableR; ++dx)
-                    if (dz * dz + dy * dy + dx * dx == r2) t.off3[n3++] = pack_offset(r2, dz, dy, dx);
-    for (int r2 = 0; r2 <= kTableR2_2; ++r2)
-        for (int dy = -kTableR_2; dy <= kTableR_2; ++dy) {
-            const int rest = r2 - dy * dy;
-            if (rest < 0) continue;
-            const int dx = isqrt_c(rest);
-            if (dx * dx != rest) continue;
-            t.off2[n2++] = pack_offset(r2, 0, dy, -dx);  // increasing dx
-            if (dx > 0) t.off2[n2++] = pack_offset(r2, 0, dy, dx);
-        }
-    return t;
-}
-// the tables hold exactly kN3 and kN2 offsets
-constexpr int count_offsets(int r2max, int r, bool three)
+// Radius of the second shell phase (in grid units), 3-D and 2-D. The 3-D
+// phase reads the bitmap rows (dz, dy) with dz^2 + dy^2 <= R^2; the window
+// of a row is 2R + 1 <= 63 bits.
+constexpr int kMidR3 = 12, kMidR2 = 31;
+constexpr int count_rows3(int r)
 {
     int n = 0;
-    for (int dz = three ? -r : 0; dz <= (three ? r : 0); ++dz)
+    for (int dz = -r; dz <= r; ++dz)
         for (int dy = -r; dy <= r; ++dy)
-            for (int dx = -r; dx <= r; ++dx)
-                if (dz * dz + dy * dy + dx * dx <= r2max) ++n;
+            if (dz * dz + dy * dy <= r * r) ++n;
     return n;
 }
-static_assert(count_offsets(kTableR2, kTableR, true) == kN3, "3-D offset table size");
-static_assert(count_offsets(kTableR2_2, kTableR_2, false) == kN2, "2-D offset table size");
-static_assert(kTableR2_2 <= 255 && (kTableR_2 + 1) * (kTableR_2 + 1) > kTableR2_2, "2-D table radius");
-__constant__ OffsetTable c_off = make_offsets();
-
-// GetBoundary(S) of Algorithm 3 at an interior point b: an axis neighbour
-// (with the same q, under the SAME_Q reading) has a different S.
-// Every load is issued before any test, so their latencies overlap.
-template <int RANK>
-__device__ __forceinline__ bool is_b2(const RouteArgs& a, int64_t b)
+constexpr int kRows3 = count_rows3(kMidR3);
+struct RowTable3 {
+    int8_t dz[kRows3], dy[kRows3];
+};
+constexpr RowTable3 make_rows3()
 {
-    const int64_t pl = (int64_t)a.ny * a.nx;
-    const int sb = __ldg(a.s + b);
-    const unsigned em = a.m.b2_rule == 1 ? 0x3Fu : (unsigned)__ldg(a.eqm + b);
-    const int xl = __ldg(a.s + b - 1), xr = __ldg(a.s + b + 1);
-    const int yl = __ldg(a.s + b - a.nx), yr = __ldg(a.s + b + a.nx);
-    const int zl = RANK == 3 ? __ldg(a.s + b - pl) : sb, zr = RANK == 3 ? __ldg(a.s + b + pl) : sb;
-    const unsigned diff = (unsigned)(zl != sb) | (unsigned)(zr != sb) << 1 | (unsigned)(yl != sb) << 2 |
-                          (unsigned)(yr != sb) << 3 | (unsigned)(xl != sb) << 4 | (unsigned)(xr != sb) << 5;
-    return (diff & em) != 0;
+    RowTable3 t{};
+    int n = 0;
+    for (int dz = -kMidR3; dz <= kMidR3; ++dz)
+        for (int dy = -kMidR3; dy <= kMidR3; ++dy)
+            if (dz * dz + dy * dy <= kMidR3 * kMidR3) {
+                t.dz[n] = (int8_t)dz;
+                t.dy[n] = (int8_t)dy;
+                ++n;
+            }
+    return t;
+}
+static_assert(2 * kMidR3 + 1 <= 63 && 2 * kMidR2 + 1 <= 63, "shell windows fit 64 bits");
+__constant__ RowTable3 c_rows3 = make_rows3();
+
+constexpr int kMidBuf = 2048;  // per-CTA buffer of the first phase's leftovers
+
+// The low bit of every nonzero 2-bit field of v.
+__device__ __forceinline__ uint32_t field_lsb(uint32_t v) { return (v | (v >> 1)) & 0x55555555u; }
+
+// Bits 0, 2, 4, ..., 30 of v to bits 0..15.
+__device__ __forceinline__ uint32_t even_bits(uint32_t v)
+{
+    v &= 0x55555555u;
+    v = (v | (v >> 1)) & 0x33333333u;
+    v = (v | (v >> 2)) & 0x0F0F0F0Fu;
+    v = (v | (v >> 4)) & 0x00FF00FFu;
+    return (v | (v >> 8)) & 0x0000FFFFu;
+}
+
+__device__ __forceinline__ void coords(const RouteArgs& a, int idx, int& x, int& y, int& z)
+{
+    const int plane = a.ny * a.nx;
+    z = idx / plane;
+    const int rem = idx - z * plane;
+    y = rem / a.nx;
+    x = rem - y * a.nx;
 }
 
 __device__ __forceinline__ float query_output(const RouteArgs& a, const Query& e, int32_t d2)
@@ -122,92 +100,116 @@ __device__ __forceinline__ void emit_query(const RouteArgs& a, const Query& e, i
     if (a.d2rec) a.d2rec[e.idx] = d2;
 }
 
-// Offset k of the table at query (x, y, z): a B2 site? r2 = its squared
-// length (r2 > max_r2, or k past the table: no).
-template <int RANK>
-__device__ __forceinline__ bool probe(const RouteArgs& a, int x, int y, int z, int k, int& r2)
+// Packed word k of row `prow` (0 past the row).
+__device__ __forceinline__ uint32_t sword(const RouteArgs& a, int64_t prow, int k, bool ok)
 {
-    const int* tab = RANK == 3 ? c_off.off3 : c_off.off2;
-    constexpr int ntab = RANK == 3 ? kN3 : kN2;
-    const int o = k < ntab ? tab[k] : -1;
-    r2 = (int)((unsigned)o >> 24);
-    if (k >= ntab || r2 > a.max_r2) return false;
-    const int bx = x + (int)(int8_t)(o & 0xFF);
-    const int by = y + (int)(int8_t)((o >> 8) & 0xFF);
-    const int bz = z + (int)(int8_t)((o >> 16) & 0xFF);
-    // B2 lies on interior points only (extents of kept axes are >= 2)
-    const bool inner = (unsigned)(bx - 1) < (unsigned)(a.nx - 2) && (unsigned)(by - 1) < (unsigned)(a.ny - 2) &&
-                       (RANK == 2 || (unsigned)(bz - 1) < (unsigned)(a.nz - 2));
-    return inner && is_b2<RANK>(a, (int64_t)bz * a.ny * a.nx + (int64_t)by * a.nx + bx);
+    return ok && k >= 0 && k < a.wpr ? __ldg(a.spk + prow * a.wpr + k) : 0u;
 }
 
-__device__ __forceinline__ void coords(const RouteArgs& a, int idx, int& x, int& y, int& z)
-{
-    const int plane = a.ny * a.nx;
-    z = idx / plane;
-    const int rem = idx - z * plane;
-    y = rem / a.nx;
-    x = rem - y * a.nx;
-}
-
-// The shell search runs in three phases, each on the queries the one before
-// left: one thread per query over the offsets of squared length 0 and 1
-// (most queries end there), one warp per query over the offsets up to
-// kPhase1, one CTA per query over the rest of the table. The first hit in
-// table order has the smallest squared distance (the table is sorted by it).
-constexpr int kPhase1 = 160;
-static_assert(7 + 32 <= kPhase1, "the first round of the second phase lies inside it");
-constexpr int kMidBuf = 2048;  // per-CTA buffer of the first phase's leftovers
-
-// The first phase for a query p at least two steps inside every kept axis:
-// 0 if p is a B2 site, else 1 if one of its axis neighbours is, else -1 --
-// the offsets of squared length 0 and 1 in table order, read off the 25 S
-// values (13 in 2-D) around p, each loaded once, and the seven mask bytes.
+// GetBoundary(S) (Algorithm 3) for the 16 points of packed S word k of row
+// (z, y): the low bit of each B2 point's field. Every lane of the warp takes
+// part (the x neighbours come from the adjacent lanes).
 template <int RANK>
-__device__ __forceinline__ int near_b2(const RouteArgs& a, int64_t p)
+__device__ __forceinline__ uint32_t b2_word(const RouteArgs& a, int64_t row, int z, int y, int k, bool in)
 {
-    const int64_t X = 1, Y = a.nx, Z = (int64_t)a.ny * a.nx;
-    const int64_t st[6] = {-Z, Z, -Y, Y, -X, X};  // mask bit order z-, z+, y-, y+, x-, x+
-    const bool literal = a.m.b2_rule == 1;
-    auto has = [](int k) { return RANK == 3 || k >= 2; };
-    const int sc = __ldg(a.s + p);
-    int sn[6];
-    unsigned en[6];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        sn[k] = has(k) ? (int)__ldg(a.s + p + st[k]) : sc;
-        en[k] = has(k) && !literal ? (unsigned)__ldg(a.eqm + p + st[k]) : 0x3Fu;
+    const int lane = threadIdx.x & 31;
+    const uint32_t w = sword(a, row, k, in);
+    uint32_t wl = __shfl_up_sync(kFull, w, 1), wr = __shfl_down_sync(kFull, w, 1);
+    if (lane == 0) wl = sword(a, row, k - 1, true);
+    if (lane == 31) wr = sword(a, row, k + 1, true);
+    const bool row_inner = y >= 1 && y <= a.ny - 2 && (RANK == 2 || (z >= 1 && z <= a.nz - 2));
+    if (!row_inner || !in) return 0u;
+    // interior along x: fields 16k + i in [1, nx - 2]
+    const int x0 = 16 * k;
+    uint32_t inner = 0xFFFFFFFFu;
+    if (x0 == 0) inner &= ~3u;
+    const int last = a.nx - 2 - x0;  // last inner field
+    if (last < 15) inner &= last < 0 ? 0u : (1u << (2 * (last + 1))) - 1u;
+    // differing neighbours per direction (mask bit order z-, z+, y-, y+, x-, x+)
+    uint32_t d[6];
+    d[4] = field_lsb(__funnelshift_l(wl, w, 2) ^ w);
+    d[5] = field_lsb(__funnelshift_r(w, wr, 2) ^ w);
+    d[2] = field_lsb(sword(a, row - 1, k, true) ^ w);
+    d[3] = field_lsb(sword(a, row + 1, k, true) ^ w);
+    if (RANK == 3) {
+        d[0] = field_lsb(sword(a, row - a.ny, k, true) ^ w);
+        d[1] = field_lsb(sword(a, row + a.ny, k, true) ^ w);
+    } else {
+        d[0] = d[1] = 0u;
     }
-    const unsigned ec = literal ? 0x3Fu : (unsigned)__ldg(a.eqm + p);
-    // S two steps away along an axis, and one step along each of two axes
-    int s2[6], sd[6][6];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        s2[k] = has(k) ? (int)__ldg(a.s + p + 2 * st[k]) : 0;
+    const uint32_t cand = (d[0] | d[1] | d[2] | d[3] | d[4] | d[5]) & inner;
+    if (a.m.b2_rule == 1 || cand == 0u) return cand;
+    // the default rule: the differing neighbour must have the same q
+    const int64_t plane = (int64_t)a.ny * a.nx;
+    const int64_t st[6] = {-plane, plane, -(int64_t)a.nx, (int64_t)a.nx, -1, 1};
+    uint32_t b2 = 0;
+    for (uint32_t m = cand; m; m &= m - 1) {
+        const int f = __ffs(m) - 1;
+        const int64_t p = row * a.nx + x0 + (f >> 1);
+        const int qb = __ldg(a.q + p);
+        bool hit = false;
 #pragma unroll
         for (int j = 0; j < 6; ++j)
-            sd[k][j] = has(k) && has(j) && (j >> 1) != (k >> 1) && j > k ? (int)__ldg(a.s + p + st[k] + st[j]) : 0;
+            if ((d[j] >> f) & 1u) hit = hit || __ldg(a.q + p + st[j]) == qb;
+        b2 |= hit ? 1u << f : 0u;
     }
-    unsigned d0 = 0;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) d0 |= (unsigned)(sn[k] != sc) << k;
-    if (d0 & ec) return 0;
-    bool hit1 = false;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        if (!has(k)) continue;
-        // the neighbours of p + st[k]: p + 2 st[k], p itself, p + st[k] + st[j]
-        unsigned dk = 0;
-#pragma unroll
-        for (int j = 0; j < 6; ++j) {
-            if (!has(j)) continue;
-            const int v = j == k ? s2[k] : (j == (k ^ 1) ? sc : (j > k ? sd[k][j] : sd[j][k]));
-            dk |= (unsigned)(v != sn[k]) << j;
-        }
-        hit1 |= (dk & en[k]) != 0;
-    }
-    return hit1 ? 1 : -1;
+    return b2;
 }
+
+// The B2 bitmap: one warp per row, one packed S word (16 points) per lane;
+// pairs of lanes make one bitmap word. Every word is written (the bitmap is
+// not cleared between calls). Nothing to do without queries.
+template <int RANK>
+__global__ void __launch_bounds__(256) k_b2map(RouteArgs a)
+{
+    wait_prior_grid();
+    const volatile int* ctr = a.ctr;
+    if (ctr[kCtrDense] || ctr[kCtrQueries] == 0 || ctr[kCtrQueries] > a.qcap) return;
+    const int lane = threadIdx.x & 31;
+    const int rows = a.nz * a.ny;
+    const int wstride = gridDim.x * (blockDim.x >> 5);
+    for (int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += wstride) {
+        const int z = RANK == 3 ? row / a.ny : 0;
+        const int y = row - z * a.ny;
+        for (int ks = 0; ks < a.wpr; ks += 32) {
+            const int k = ks + lane;
+            const uint32_t m16 = even_bits(b2_word<RANK>(a, row, z, y, k, k < a.wpr));
+            const uint32_t hi = __shfl_down_sync(kFull, m16, 1);
+            if (!(lane & 1) && k < a.wpr) a.b2bits[(int64_t)row * a.bwpr + (k >> 1)] = m16 | (hi << 16);
+        }
+    }
+}
+
+// Bitmap bits x0 .. x0 + 63 of row `prow` (0 outside the row).
+__device__ __forceinline__ uint64_t bwin64(const RouteArgs& a, int64_t prow, int x0)
+{
+    const int lo = x0 >> 5, sh = x0 & 31;  // arithmetic shift: lo = -1 or -2 left of the row
+    const uint32_t* r = a.b2bits + prow * a.bwpr;
+    auto w = [&](int i) { return i >= 0 && i < a.bwpr ? __ldg(r + i) : 0u; };
+    const uint32_t w0 = w(lo), w1 = w(lo + 1), w2 = w(lo + 2);
+    return (uint64_t)__funnelshift_r(w0, w1, sh) | ((uint64_t)__funnelshift_r(w1, w2, sh) << 32);
+}
+
+// Squared distance from bit R of v to its nearest set bit among bits 0..2R
+// (INT_MAX if none).
+__device__ __forceinline__ int nearest_bit2(uint64_t v, int R)
+{
+    const uint64_t left = v & ((2ull << R) - 1ull);   // bits 0..R
+    const uint64_t right = (v >> R) & ((2ull << R) - 1ull);  // bits R..2R, from R
+    int d = 0x7FFFFFFF;
+    if (left) {
+        const int hb = 63 - __clzll((long long)left);
+        d = min(d, R - hb);
+    }
+    if (right) d = min(d, __ffsll((long long)right) - 1);
+    return d == 0x7FFFFFFF ? d : d * d;
+}
+
+// Leftover of a shell phase to the next one (per-CTA buffer, one atomic).
+struct LeftBuf {
+    Query* e;
+    int* n;
+};
 
 template <int RANK>
 __global__ void __launch_bounds__(256) k_query(RouteArgs a)
@@ -220,30 +222,29 @@ __global__ void __launch_bounds__(256) k_query(RouteArgs a)
         if (blockIdx.x == 0 && threadIdx.x == 0) ctr[kCtrDense] = 1;
         return;
     }
-    constexpr int n0 = RANK == 3 ? 7 : 5;  // offsets of squared length 0 and 1
     __shared__ Query mbuf[kMidBuf];
     __shared__ int mn, mbase;
     if (threadIdx.x == 0) mn = 0;
     __syncthreads();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += gridDim.x * blockDim.x) {
         const Query e = a.qlist[i];
-        int x, y, z;
-        coords(a, e.idx, x, y, z);
-        int found = -1;
-        const bool deep = a.max_r2 >= 1 && x >= 2 && x <= a.nx - 3 && y >= 2 && y <= a.ny - 3 &&
-                          (RANK == 2 || (z >= 2 && z <= a.nz - 3));
-        if (deep) {
-            found = near_b2<RANK>(a, e.idx);
-        } else {
-            bool hit[n0];
-            int r2[n0];
+        int found = 0x7FFFFFFF;
+        if (a.shell) {
+            int x, y, z;
+            coords(a, e.idx, x, y, z);
+            const int64_t row = (int64_t)z * a.ny + y;
 #pragma unroll
-            for (int k = 0; k < n0; ++k) hit[k] = probe<RANK>(a, x, y, z, k, r2[k]);
+            for (int dz = (RANK == 3 ? -1 : 0); dz <= (RANK == 3 ? 1 : 0); ++dz)
 #pragma unroll
-            for (int k = n0 - 1; k >= 0; --k)
-                if (hit[k]) found = r2[k];
+                for (int dy = -1; dy <= 1; ++dy) {
+                    if ((unsigned)(y + dy) >= (unsigned)a.ny || (RANK == 3 && (unsigned)(z + dz) >= (unsigned)a.nz))
+                        continue;
+                    const uint32_t v = (uint32_t)bwin64(a, row + (int64_t)dz * a.ny + dy, x - 1) & 7u;
+                    const int d = nearest_bit2(v, 1);
+                    if (d != 0x7FFFFFFF) found = min(found, dz * dz + dy * dy + d);
+                }
         }
-        if (found >= 0) {
+        if (found <= 3) {  // every point within squared distance 3 is in the block
             emit_query(a, e, found);
         } else {
             const int k = atomicAdd(&mn, 1);
@@ -262,47 +263,41 @@ __global__ void __launch_bounds__(256) k_query(RouteArgs a)
     for (int j = threadIdx.x; j < n && mbase + j < a.qcap; j += blockDim.x) a.mlist[mbase + j] = mbuf[j];
 }
 
-// Second phase: one warp per query, table offsets n0 .. kPhase1: first the
-// 32 nearest (where most of these queries end), then the other four per lane
-// with their loads in flight together.
+// Second phase: one warp per query; the lanes take the bitmap rows within
+// radius R, each row's nearest bit to x in the window x - R .. x + R.
 template <int RANK>
 __global__ void __launch_bounds__(256) k_query_mid(RouteArgs a)
 {
     wait_prior_grid();
     volatile int* ctr = a.ctr;
     if (ctr[kCtrDense]) return;
-    const int nm = min((int)ctr[kCtrMid], a.qcap);  // at most the queries
-    constexpr int n0 = RANK == 3 ? 7 : 5;
+    const int nm = min((int)ctr[kCtrMid], a.qcap);
     const int lane = threadIdx.x & 31;
     const int wstride = gridDim.x * (blockDim.x >> 5);
+    constexpr int R = RANK == 3 ? kMidR3 : kMidR2;
+    constexpr int nrows = RANK == 3 ? kRows3 : 2 * kMidR2 + 1;
     for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < nm; i += wstride) {
         const Query e = a.mlist[i];
-        int x, y, z;
-        coords(a, e.idx, x, y, z);
-        int found = -1;
-        int r2[5];
-        bool hit[5];
-        hit[0] = probe<RANK>(a, x, y, z, n0 + lane, r2[0]);  // n0 + 31 < kPhase1
-        const unsigned h0 = __ballot_sync(kFull, hit[0]);
-        if (h0) {
-            found = __shfl_sync(kFull, r2[0], __ffs(h0) - 1);
-        } else {
-#pragma unroll
-            for (int u = 1; u < 5; ++u) {
-                const int k = n0 + 32 * u + lane;
-                hit[u] = k < kPhase1 && probe<RANK>(a, x, y, z, k, r2[u]);
+        int best = 0x7FFFFFFF;
+        if (a.shell) {
+            int x, y, z;
+            coords(a, e.idx, x, y, z);
+            const int64_t row = (int64_t)z * a.ny + y;
+            for (int r = lane; r < nrows; r += 32) {
+                const int dz = RANK == 3 ? c_rows3.dz[r] : 0;
+                const int dy = RANK == 3 ? c_rows3.dy[r] : r - kMidR2;
+                if ((unsigned)(y + dy) >= (unsigned)a.ny || (RANK == 3 && (unsigned)(z + dz) >= (unsigned)a.nz))
+                    continue;
+                const int d = nearest_bit2(bwin64(a, row + (int64_t)dz * a.ny + dy, x - R), R);
+                if (d != 0x7FFFFFFF) best = min(best, dz * dz + dy * dy + d);
             }
-#pragma unroll
-            for (int u = 1; u < 5; ++u) {
-                const unsigned h = __ballot_sync(kFull, hit[u]);
-                if (h && found < 0) found = __shfl_sync(kFull, r2[u], __ffs(h) - 1);
-            }
+            best = __reduce_min_sync(kFull, best);
         }
         if (lane == 0) {
-            if (found >= 0) {
-                emit_query(a, e, found);
+            if (best <= R * R) {  // exact: a nearer site would lie in a row and window read here
+                emit_query(a, e, best);
             } else {
-                const int k = atomicAdd(a.ctr + kCtrFailed, 1);
+                const int k = atomicAdd(a.ctr + kCtrUnresolved, 1);
                 if (k < a.fcap) {
                     a.flist[k] = e;
                     a.fmin[k] = kDistInf;
@@ -312,266 +307,76 @@ __global__ void __launch_bounds__(256) k_query_mid(RouteArgs a)
     }
 }
 
-// Third phase: one CTA per query the second left, over table offsets
-// kPhase1 .. (4 per thread: 1024 cover the 3-D table). A hit writes the
-// output and marks the query done (fmin = -1); a miss leaves it to the
-// brute-force search.
-template <int RANK>
-__global__ void __launch_bounds__(256) k_query_far(RouteArgs a)
-{
-    wait_prior_grid();
-    volatile int* ctr = a.ctr;
-    if (ctr[kCtrDense]) return;
-    const int nf = ctr[kCtrFailed];
-    if (nf > a.fcap) {  // the list is incomplete: the dense route takes over
-        if (blockIdx.x == 0 && threadIdx.x == 0) ctr[kCtrDense] = 1;
-        return;
-    }
-    __shared__ int sbest[8];
-    for (int f = blockIdx.x; f < nf; f += gridDim.x) {
-        const Query e = a.flist[f];
-        int x, y, z;
-        coords(a, e.idx, x, y, z);
-        int best = 0x7FFFFFFF;  // smallest table index with a hit
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int k = kPhase1 + (int)threadIdx.x + (int)blockDim.x * u;
-            int r2;
-            if (probe<RANK>(a, x, y, z, k, r2)) best = min(best, k);
-        }
-        best = __reduce_min_sync(kFull, best);
-        if ((threadIdx.x & 31) == 0) sbest[threadIdx.x >> 5] = best;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) best = min(best, sbest[w]);
-            if (best != 0x7FFFFFFF) {
-                const int* tab = RANK == 3 ? c_off.off3 : c_off.off2;
-                emit_query(a, e, (int)((unsigned)tab[best] >> 24));
-                a.fmin[f] = -1;
-            } else {
-                atomicAdd(a.ctr + kCtrUnresolved, 1);
-            }
-        }
-        __syncthreads();
-    }
-}
-
-// B2 sites found by one CTA, flushed to the global list with one atomic.
-constexpr int kSiteBuf = 1024;
-struct SiteBuf {
-    uint2* e;  // [kSiteBuf] in shared memory
-    int* n;    // shared count
-};
-
-// Appends the B2 sites x0 + j (bit j of nib) of row (y, z): into the CTA's
-// buffer (warp-aggregated), or, when it is full, to the global list.
-__device__ __forceinline__ void append_sites(const RouteArgs& a, const SiteBuf& sb, unsigned nib, int x0, int y, int z)
-{
-    const int lane = threadIdx.x & 31;
-    if (!__ballot_sync(kFull, nib != 0)) return;
-    const int cnt = __popc(nib);
-    int incl = cnt;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const int v = __shfl_up_sync(kFull, incl, d);
-        if (lane >= d) incl += v;
-    }
-    int base = 0;
-    bool global = false;
-    if (lane == 31) {
-        base = atomicAdd(sb.n, incl);
-        if (base + incl > kSiteBuf) {
-            global = true;
-            base = atomicAdd(a.ctr + kCtrB2, incl);
-        }
-    }
-    global = __shfl_sync(kFull, global, 31);
-    base = __shfl_sync(kFull, base, 31) + incl - cnt;
-    uint2* list = global ? reinterpret_cast<uint2*>(a.b2list) : sb.e;
-    const int cap = global ? a.b2cap : kSiteBuf;
-    for (int j = 0; j < 4; ++j) {
-        if (!((nib >> j) & 1u)) continue;
-        if (base < cap) list[base] = make_uint2((uint32_t)(x0 + j) | ((uint32_t)y << 16), (uint32_t)z);
-        ++base;
-    }
-}
-
-__device__ __forceinline__ void flush_sites(const RouteArgs& a, const SiteBuf& sb, int* sbase)
-{
-    __syncthreads();
-    const int n = min(*sb.n, kSiteBuf);
-    if (threadIdx.x == 0) *sbase = n > 0 ? atomicAdd(a.ctr + kCtrB2, n) : 0;
-    __syncthreads();
-    uint2* list = reinterpret_cast<uint2*>(a.b2list);
-    for (int i = threadIdx.x; i < n && *sbase + i < a.b2cap; i += blockDim.x) list[*sbase + i] = sb.e[i];
-}
-
-// The B2 sites, from the signed set: a site has S != 0 or an axis neighbour
-// with S != 0 (GetBoundary(S) compares S across a pair), so every site is a
-// signed point or an axis neighbour of one. Each signed point tests itself and
-// its neighbours with S = 0; a neighbour with S = 0 is tested only by its
-// signed neighbour of smallest linear index, so no site is listed twice.
-// Runs when some query needs the list and the signed set is complete.
-template <int RANK>
-__device__ __forceinline__ void b2_from_field(const RouteArgs& a, const SiteBuf& sb, int vec);
-
-template <int RANK>
-__global__ void __launch_bounds__(256) k_b2sites(RouteArgs a, int vec)
+// The B2 sites, listed from the bitmap (only when some query is left to
+// the search over them): one thread per bitmap word, warp-aggregated appends
+// into a per-CTA buffer, one global atomic per CTA.
+constexpr int kSiteBuf = 2048;
+__global__ void __launch_bounds__(256) k_b2list(RouteArgs a)
 {
     wait_prior_grid();
     volatile int* ctr = a.ctr;
     if (ctr[kCtrDense] || ctr[kCtrUnresolved] == 0) return;
     __shared__ uint2 sbuf[kSiteBuf];
-    __shared__ int sn, sbase;
-    if (threadIdx.x == 0) sn = 0;
+    __shared__ int sn, sfull, sbase;  // sfull: first reservation that did not fit
+    if (threadIdx.x == 0) {
+        sn = 0;
+        sfull = kSiteBuf;
+    }
     __syncthreads();
-    const SiteBuf sb{sbuf, &sn};
-    if (ctr[kCtrSignedOver] || ctr[kCtrSigned] > a.scap) {  // the signed set overflowed its list
-        b2_from_field<RANK>(a, sb, vec);
-        flush_sites(a, sb, &sbase);
-        return;
-    }
-    const int ns = ctr[kCtrSigned], nq = ctr[kCtrQueries];
-    const int plane = a.ny * a.nx;
-    // one thread per signed point p: its candidates are p and its axis
-    // neighbours, and every S they need lies within two axis steps of p, so
-    // all loads of the thread are issued together
-    for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < ns + nq; item += gridDim.x * blockDim.x) {
-        const int p = item < ns ? a.slist[item] : a.qlist[item - ns].idx;
-        int x, y, z;
-        coords(a, p, x, y, z);
-        // S at p + (dz, dy, dx), 0 outside the field (never read there: only
-        // interior candidates are tested, and their neighbours lie inside)
-        auto S = [&](int dz, int dy, int dx) -> int {
-            const bool in = (unsigned)(x + dx) < (unsigned)a.nx && (unsigned)(y + dy) < (unsigned)a.ny &&
-                            (RANK == 2 || (unsigned)(z + dz) < (unsigned)a.nz);
-            return in ? (int)__ldg(a.s + p + dz * plane + dy * a.nx + dx) : 0;
-        };
-        // candidate c: 0 = p, then z-, z+, y-, y+, x-, x+ (rank 2: y-, y+, x-, x+)
-#pragma unroll
-        for (int c = 0; c <= 2 * RANK; ++c) {
-            int cz = 0, cy = 0, cx = 0;
-            if (c > 0) {
-                const int ax = RANK == 3 ? (c - 1) >> 1 : ((c - 1) >> 1) + 1;
-                const int sg = (c - 1) & 1 ? 1 : -1;
-                (ax == 0 ? cz : (ax == 1 ? cy : cx)) = sg;
-            }
-            const int bx = x + cx, by = y + cy, bz = z + cz;
-            const bool inner = (unsigned)(bx - 1) < (unsigned)(a.nx - 2) && (unsigned)(by - 1) < (unsigned)(a.ny - 2) &&
-                               (RANK == 2 || (unsigned)(bz - 1) < (unsigned)(a.nz - 2));
-            if (!inner) continue;
-            const int sb0 = S(cz, cy, cx);
-            // the six axis neighbours of the candidate: z-, z+, y-, y+, x-, x+
-            int nbv[6];
-            nbv[0] = RANK == 3 ? S(cz - 1, cy, cx) : sb0;
-            nbv[1] = RANK == 3 ? S(cz + 1, cy, cx) : sb0;
-            nbv[2] = S(cz, cy - 1, cx);
-            nbv[3] = S(cz, cy + 1, cx);
-            nbv[4] = S(cz, cy, cx - 1);
-            nbv[5] = S(cz, cy, cx + 1);
-            bool own = true;
-            if (c > 0) {
-                // an S = 0 candidate is tested by its signed neighbour of
-                // smallest linear index: p must precede every other one (an
-                // offset precedes 0 in (dz, dy, dx) order exactly when its
-                // point precedes p, for points inside the field)
-                own = sb0 == 0;
-                const int oz[6] = {cz - 1, cz + 1, cz, cz, cz, cz}, oy[6] = {cy, cy, cy - 1, cy + 1, cy, cy},
-                          ox[6] = {cx, cx, cx, cx, cx - 1, cx + 1};
-#pragma unroll
-                for (int k = 0; k < 6; ++k) {
-                    const bool before = oz[k] < 0 || (oz[k] == 0 && (oy[k] < 0 || (oy[k] == 0 && ox[k] < 0)));
-                    if (before && nbv[k] != 0) own = false;
-                }
-            }
-            if (!own) continue;
-            const unsigned em = a.m.b2_rule == 1 ? 0x3Fu
-                                                 : (unsigned)__ldg(a.eqm + p + cz * plane + cy * a.nx + cx);
-            unsigned diff = 0;
-#pragma unroll
-            for (int k = 0; k < 6; ++k) diff |= (unsigned)(nbv[k] != sb0) << k;
-            if (diff & em) {
-                const int kk = atomicAdd(sb.n, 1);
-                const uint2 e = make_uint2((uint32_t)bx | ((uint32_t)by << 16), (uint32_t)bz);
-                if (kk < kSiteBuf) {
-                    sb.e[kk] = e;
-                } else {
-                    const int g = atomicAdd(a.ctr + kCtrB2, 1);
-                    if (g < a.b2cap) reinterpret_cast<uint2*>(a.b2list)[g] = e;
-                }
-            }
-        }
-    }
-    flush_sites(a, sb, &sbase);
-}
-
-__device__ __forceinline__ uint32_t load4_s8(const int8_t* p, int x0, int nx, bool vec)
-{
-    if (vec) return x0 < nx ? __ldg(reinterpret_cast<const uint32_t*>(p + x0)) : 0u;
-    uint32_t w = 0;
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-        if (x0 + j < nx) w |= (uint32_t)(uint8_t)__ldg(p + x0 + j) << (8 * j);
-    return w;
-}
-
-// Every B2 site of the field, for the case where the signed set overflowed
-// its list. One warp per interior row, 128 points per step (4 per lane).
-template <int RANK>
-__device__ __forceinline__ void b2_from_field(const RouteArgs& a, const SiteBuf& sb, int vec)
-{
     const int lane = threadIdx.x & 31;
-    const int rows = a.nz * a.ny;
-    const int plane = a.ny * a.nx;
-    const uint8_t* eqm = a.eqm;
-    const bool literal = a.m.b2_rule == 1;
-    const int wstride = gridDim.x * (blockDim.x >> 5);
-    for (int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += wstride) {
-        const int z = row / a.ny, y = row - z * a.ny;
-        if (y < 1 || y > a.ny - 2 || (RANK == 3 && (z < 1 || z > a.nz - 2))) continue;  // warp-uniform
-        const int8_t* sr = a.s + (int64_t)row * a.nx;
-        const uint8_t* er = eqm + (int64_t)row * a.nx;
-        uint32_t carry = 0;  // S word of the previous step (its byte 3 is the left neighbour)
-        for (int x0s = 0; x0s < a.nx; x0s += 128) {
-            const int x0 = x0s + 4 * lane;
-            const uint32_t cw = load4_s8(sr, x0, a.nx, vec);
-            uint32_t xmw = __shfl_up_sync(kFull, cw, 1);
-            uint32_t xpw = __shfl_down_sync(kFull, cw, 1);
-            const uint32_t last = __shfl_sync(kFull, cw, 31);
-            if (lane == 0) xmw = carry;
-            if (lane == 31) xpw = x0 + 4 < a.nx ? (uint32_t)(uint8_t)__ldg(sr + x0 + 4) : 0u;
-            carry = last;
-            const uint32_t eqw = literal ? 0xFFFFFFFFu : load4_s8(reinterpret_cast<const int8_t*>(er), x0, a.nx, vec);
-            // byte k of sel(bit) = 0xFF if bit `bit` of equal-q mask byte k is set
-            auto sel = [&](int bit) -> uint32_t { return __vcmpne4(eqw & (0x01010101u << bit), 0u); };
-            uint32_t b2 = (__vcmpne4(__byte_perm(xmw, cw, 0x6543), cw) & sel(4)) |
-                          (__vcmpne4(__byte_perm(cw, xpw, 0x4321), cw) & sel(5)) |
-                          (__vcmpne4(load4_s8(sr - a.nx, x0, a.nx, vec), cw) & sel(2)) |
-                          (__vcmpne4(load4_s8(sr + a.nx, x0, a.nx, vec), cw) & sel(3));
-            if (RANK == 3) {
-                b2 |= (__vcmpne4(load4_s8(sr - plane, x0, a.nx, vec), cw) & sel(0)) |
-                      (__vcmpne4(load4_s8(sr + plane, x0, a.nx, vec), cw) & sel(1));
-            }
-            unsigned nib = ((b2 & 0x80808080u) * 0x00204081u) >> 28;
+    const int64_t words = (int64_t)a.nz * a.ny * a.bwpr;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    uint2* glist = reinterpret_cast<uint2*>(a.b2list);
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < words; base += stride) {
+        const int64_t i = base + threadIdx.x;
+        uint32_t w = i < words ? __ldg(a.b2bits + i) : 0u;
+        const int cnt = __popc(w);
+        int incl = cnt;
 #pragma unroll
-            for (int j = 0; j < 4; ++j)  // interior along x; bytes past the row end are not points
-                if (x0 + j < 1 || x0 + j > a.nx - 2) nib &= ~(1u << j);
-            append_sites(a, sb, nib, x0, y, z);
+        for (int d = 1; d < 32; d <<= 1) {
+            const int v = __shfl_up_sync(kFull, incl, d);
+            if (lane >= d) incl += v;
+        }
+        const int total = __shfl_sync(kFull, incl, 31);
+        if (total == 0) continue;
+        int wbase = 0;
+        if (lane == 31) wbase = atomicAdd(&sn, total);
+        wbase = __shfl_sync(kFull, wbase, 31);
+        const bool global = wbase + total > kSiteBuf;
+        if (global && lane == 31) {
+            atomicMin(&sfull, wbase);  // every later reservation fails too (sn only grows)
+            wbase = atomicAdd(a.ctr + kCtrB2, total);
+        }
+        if (global) wbase = __shfl_sync(kFull, wbase, 31);
+        uint2* list = global ? glist : sbuf;
+        const int cap = global ? a.b2cap : kSiteBuf;
+        int pos = wbase + incl - cnt;
+        if (w) {
+            const int64_t row = i / a.bwpr;
+            const int x0 = 32 * (int)(i - row * a.bwpr);
+            const int z = (int)(row / a.ny), y = (int)(row - (int64_t)z * a.ny);
+            for (; w; w &= w - 1, ++pos)
+                if (pos < cap) list[pos] = make_uint2((uint32_t)(x0 + __ffs(w) - 1) | ((uint32_t)y << 16), (uint32_t)z);
         }
     }
+    __syncthreads();
+    const int n = min(sn, sfull);
+    if (threadIdx.x == 0) sbase = n > 0 ? atomicAdd(a.ctr + kCtrB2, n) : 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n && sbase + i < a.b2cap; i += blockDim.x) glist[sbase + i] = sbuf[i];
 }
 
-// Exact Dist2 of each query left by k_query: min over the listed B2 sites.
-// CTA i takes 256 queries (block i % qb) against one slice of the site list
-// (i / qb), staged through shared memory; each thread folds its minimum into
-// fmin with an atomic, and the last CTA to finish writes the outputs.
+// Exact Dist2 of each query left by the shell phases: min over the listed B2
+// sites. CTA i takes 256 queries (block i % qb) against one slice of the site
+// list (i / qb), staged through shared memory; each thread folds its minimum
+// into fmin with an atomic, and the last CTA to finish writes the outputs.
 constexpr int kBruteChunk = 1024;
 __global__ void __launch_bounds__(256) k_brute(RouteArgs a)
 {
     wait_prior_grid();
     volatile int* ctr = a.ctr;
     if (ctr[kCtrDense] || ctr[kCtrUnresolved] == 0) return;
-    const int nf = ctr[kCtrFailed];
+    const int nf = ctr[kCtrUnresolved];
     const int nb = ctr[kCtrB2];
     const int qblocks = (nf + blockDim.x - 1) / blockDim.x;
     if (nf > a.fcap || nb > a.b2cap || (long long)nf * nb > a.brute_budget || qblocks > (int)gridDim.x) {
@@ -609,7 +414,7 @@ __global__ void __launch_bounds__(256) k_brute(RouteArgs a)
                 best = min(best, dz * dz + dy * dy + dx * dx);
             }
         }
-        if (f < nf && best < kDistInf) atomicMin(a.fmin + f, best);  // -1 (done) stays
+        if (f < nf && best < kDistInf) atomicMin(a.fmin + f, best);
     }
     // the last CTA writes every output (no B2 at all: Dist2 = INF, w = 1)
     __threadfence();
@@ -620,16 +425,28 @@ __global__ void __launch_bounds__(256) k_brute(RouteArgs a)
         __threadfence();
         for (int f = threadIdx.x; f < nf; f += blockDim.x) {
             const int32_t d2 = *static_cast<volatile int32_t*>(a.fmin + f);
-            if (d2 < 0) continue;  // the second shell search found it
-            const Query e = a.flist[f];
-            emit_query(a, e, d2);
+            emit_query(a, a.flist[f], d2);
         }
     }
 }
 
+// A grid-stride kernel's grid: every CTA resident at once.
+template <class K>
+int resident(K kern)
+{
+    int dev = 0, sms = 152, per = 1;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, 0) != cudaSuccess || per < 1) per = 1;
+    return sms * per;
+}
+
 }  // namespace
 
-int route_table_r2(int rank) { return rank == 2 ? kTableR2_2 : kTableR2; }
+cudaError_t launch_route_b2map(const RouteArgs& a, cudaStream_t st)
+{
+    auto run = [&](auto kern) { return launch_chained(kern, dim3(resident(kern)), dim3(256), 0, st, a); };
+    return a.rank == 3 ? run(k_b2map<3>) : run(k_b2map<2>);
+}
 
 cudaError_t launch_route_query(const RouteArgs& a, int blocks, cudaStream_t st)
 {
@@ -643,18 +460,9 @@ cudaError_t launch_route_query_mid(const RouteArgs& a, int blocks, cudaStream_t 
                        : launch_chained(k_query_mid<2>, dim3(blocks), dim3(256), 0, st, a);
 }
 
-cudaError_t launch_route_query_far(const RouteArgs& a, int blocks, cudaStream_t st)
+cudaError_t launch_route_b2list(const RouteArgs& a, cudaStream_t st)
 {
-    return a.rank == 3 ? launch_chained(k_query_far<3>, dim3(blocks), dim3(256), 0, st, a)
-                       : launch_chained(k_query_far<2>, dim3(blocks), dim3(256), 0, st, a);
-}
-
-cudaError_t launch_route_b2sites(const RouteArgs& a, int blocks, cudaStream_t st)
-{
-    auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 3) == 0; };
-    const int vec = (a.nx % 4 == 0) && al(a.s) && al(a.eqm);
-    return a.rank == 3 ? launch_chained(k_b2sites<3>, dim3(blocks), dim3(256), 0, st, a, vec)
-                       : launch_chained(k_b2sites<2>, dim3(blocks), dim3(256), 0, st, a, vec);
+    return launch_chained(k_b2list, dim3(resident(k_b2list)), dim3(256), 0, st, a);
 }
 
 cudaError_t launch_route_brute(const RouteArgs& a, int blocks, cudaStream_t st)

@@ -168,10 +168,10 @@ def test_profile_and_launch_count():
     torch.cuda.synchronize()
     stats = qai.profile_read()
     qai.profile_enable(False)
-    assert qai.launch_count() - n0 == 13
-    assert set(stats) == {"detect", "near", "rowpass1", "colpass1_y", "colpass1_z_final", "signed_query",
-                          "signed_query_mid", "signed_query_far", "signed_b2sites", "signed_brute", "rowpass2",
-                          "colpass2_y", "colpass2_z_final"}
+    names = {"detect", "near", "rowpass1", "colpass1_y", "colpass1_z_final", "pack_s", "b2map", "signed_query",
+             "signed_query_mid", "b2list", "signed_brute", "expand", "rowpass2", "colpass2_y", "colpass2_z_final"}
+    assert qai.launch_count() - n0 == len(names)
+    assert set(stats) == names
     assert all(v[0] == 1 and v[1] > 0 for v in stats.values())
 
 
