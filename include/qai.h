@@ -42,7 +42,7 @@ typedef enum {
     QAI_ERR_RANGE = 3,        /* reserved                                          */
     QAI_ERR_CUDA = 4,         /* a CUDA runtime call or launch failed              */
     QAI_ERR_OOM = 5,          /* internal workspace allocation failed              */
-    QAI_ERR_TIMEOUT = 6,      /* reserved for bounded device-side waits            */
+    QAI_ERR_TIMEOUT = 6,      /* a bounded device-side wait ran out                */
     QAI_ERR_INTERNAL = 7
 } qai_status;
 
@@ -147,7 +147,9 @@ qai_status qai_mitigate(const int32_t* d_q, float* d_out, int rank, const int64_
  *           EDT ran because some point had no B1 point within squared
  *           distance 8 (the first EDT's bounded search), else 0
  * Synchronises `stream`. Returns QAI_ERR_SHAPE for rank-1 fields (no such
- * route) or an unsupported shape, QAI_ERR_INVALID_ARG for NULL pointers. */
+ * route) or an unsupported shape, QAI_ERR_INVALID_ARG for NULL pointers, and
+ * QAI_ERR_TIMEOUT (with the counts filled) when a bounded wait inside that
+ * call's kernels ran out, so that its output is not valid. */
 qai_status qai_route_counts(const void* d_ws, int rank, const int64_t* dims, int32_t* counts,
                             cudaStream_t stream);
 
@@ -319,8 +321,8 @@ qai_status qai_quality(const float* d_x, const float* d_y, int rank, const int64
  * no counterpart; it is a deployment convenience of this library.
  *
  * Instead of a workspace it uses one scratch array compiled into the library
- * (a 256-byte aligned __device__ array of 14 * QAI_STATIC_MAX_POINTS + 1 MiB
- * bytes, about 29 MiB). Every GPU on which the library's code is loaded holds
+ * (a 256-byte aligned __device__ array of 15 * QAI_STATIC_MAX_POINTS + 1 MiB
+ * bytes, about 31 MiB). Every GPU on which the library's code is loaded holds
  * that array until the process exits.
  *
  * First call on a device: it looks up the array's device address

@@ -162,6 +162,8 @@ Layout layout_for(const Shape& s, uint32_t flags)
         l.wpr = (s.nx + 15) / 16;
         l.bwpr = (s.nx + 31) / 32;
         l.codes = take(rows * l.wpr * 4);
+        l.nexy = take(rows * l.wpr * 4);
+        l.nez = s.rank == 3 ? take(rows * l.wpr * 4) : 0;
         l.spk = take(rows * l.wpr * 4);
         l.b2bits = take(rows * l.bwpr * 4);
         l.qcap = (int)(N / 128 + 1024);
@@ -304,6 +306,8 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
         la.rank = sh.rank; la.nz = sh.nz; la.ny = sh.ny; la.nx = sh.nx; la.wpr = lay.wpr;
         la.q = d_q; la.out = d_out; la.ctr = ctr; la.dist1 = dist1;
         la.codes = reinterpret_cast<uint32_t*>(ws + lay.codes);
+        la.nexy = reinterpret_cast<uint32_t*>(ws + lay.nexy);
+        la.nez = sh.rank == 3 ? reinterpret_cast<uint32_t*>(ws + lay.nez) : nullptr;
         la.spk = reinterpret_cast<uint32_t*>(ws + lay.spk);
         la.qlist = reinterpret_cast<qai::Query*>(ws + lay.qlist); la.qcap = lay.qcap;
         la.eqm = eqm; la.s = s;
@@ -311,11 +315,15 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
         auto al = [](const void* p, int b) { return (reinterpret_cast<uintptr_t>(p) % b) == 0; };
         la.vec = (sh.nx % 4 == 0) && al(d_q, 16) && al(d_out, 16);
     }
-    if (local) {
-        // Steps A-C by the bounded nearest-site search; the separable passes
-        // below run only if some point has no B1 point within reach.
-        e = timed("detect", N * 8.25, st, [&] { return qai::launch_local_detect(la, st); });
+    if (ctr) {
+        // Step A with the output where Dist2 does not matter and the packed
+        // maps of the route (B1 with S_B, equal neighbours)
+        e = timed("detect", N * (sh.rank == 3 ? 8.75 : 8.5), st, [&] { return qai::launch_local_detect(la, st); });
         if (e != cudaSuccess) return cuda_fail(e, "step A");
+    }
+    if (local) {
+        // Steps B and C by the bounded nearest-site search; the separable
+        // passes below run only if some point has no B1 point within reach.
         e = timed("near", N * 0.5, st, [&] { return qai::launch_local_near(la, st); });
         if (e != cudaSuccess) return cuda_fail(e, "nearest-site search");
     }
@@ -399,7 +407,7 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
         qai::RouteArgs ra{};
         ra.rank = sh.rank; ra.nz = sh.nz; ra.ny = sh.ny; ra.nx = sh.nx;
         ra.wpr = lay.wpr; ra.bwpr = lay.bwpr;
-        ra.q = d_q; ra.spk = la.spk; ra.out = d_out; ra.ctr = ctr;
+        ra.q = d_q; ra.spk = la.spk; ra.nexy = la.nexy; ra.nez = la.nez; ra.out = d_out; ra.ctr = ctr;
         ra.b2bits = reinterpret_cast<uint32_t*>(ws + lay.b2bits);
         ra.qlist = qlist; ra.qcap = lay.qcap;
         ra.mlist = reinterpret_cast<qai::Query*>(ws + lay.mlist);
@@ -411,7 +419,7 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
         ra.brute_budget = 1LL << 28;
         ra.m = m;
         if (route == Route::Dense) ra.qcap = -1;  // every count is over it: hand over at once
-        e = timed("b2map", N * 0.375, st, [&] { return qai::launch_route_b2map(ra, st); });
+        e = timed("b2map", N * (sh.rank == 3 ? 1.125 : 0.875), st, [&] { return qai::launch_route_b2map(ra, st); });
         if (e != cudaSuccess) return cuda_fail(e, "B2 bitmap");
         e = timed("signed_query", 0.0, st, [&] { return qai::launch_route_query(ra, 4 * sms, st); });
         if (e != cudaSuccess) return cuda_fail(e, "signed-point shell search");
@@ -601,8 +609,10 @@ qai_status qai_route_counts(const void* d_ws, int rank, const int64_t* dims, int
     counts[1] = c[qai::kCtrUnresolved];
     counts[2] = c[qai::kCtrB2];
     counts[3] = c[qai::kCtrDense] != 0;
-    counts[4] = c[qai::kCtrSignedOver] ? -1 : c[qai::kCtrSigned];
+    counts[4] = c[qai::kCtrSignedOver] ? -1 : c[c[qai::kCtrWide] ? qai::kCtrSignedExact : qai::kCtrSigned];
     counts[5] = c[qai::kCtrLocalFail] != 0;
+    if (c[qai::kCtrTimeout])
+        return fail(QAI_ERR_TIMEOUT, "a bounded device-side wait of that call ran out: its output is not valid");
     return QAI_OK;
 }
 

@@ -63,6 +63,9 @@ enum RouteCtr : int {
     kCtrSignedOver = 5,// != 0: a tile of the separable pass had more of them than it could buffer
     kCtrBruteDone = 6, // CTAs of the brute-force search that finished
     kCtrMid = 8,       // queries the first (per-thread) shell search left
+    kCtrWide = 12,     // != 0: an index outside the fast path's range: the exact step A ran
+    kCtrSignedExact = 13, // B1 points with S != 0, counted by the exact step A
+    kCtrTimeout = 14,  // != 0: a bounded device-side wait ran out (the call's output is not valid)
     kCtrLocalFail = 15,// != 0: the local first EDT left a point without its site;
                        // the separable first EDT runs (and zeroes the words before)
     kCtrWords = 16
@@ -155,6 +158,8 @@ struct RouteArgs {
     int wpr, bwpr;           // packed words per row: S (16 points), B2 bitmap (32)
     const int32_t* q;
     const uint32_t* spk;     // packed S
+    const uint32_t* nexy;    // packed differ maps of step A
+    const uint32_t* nez;
     uint32_t* b2bits;        // B2 bitmap (written by k_b2map)
     float* out;
     int* ctr;                // RouteCtr words
@@ -181,6 +186,9 @@ struct RouteArgs {
 // row * wpr + (x >> 4), at bits 2 (x & 15) and up.
 //   codes  step A: 0 off B1, 1 + sign code of S_B on B1 (1: S_B = 0,
 //          2: S_B = +1, 3: S_B = -1)
+//   nexy   q != q[x + 1] (low bit) and q != q[y + 1] (high bit) of each
+//          point (not defined where the neighbour does not exist)
+//   nez    q != q[z + 1] (low bit; rank 3)
 //   spk    S (Algorithm 3) as a sign code: 0, 1 (+1), 2 (-1)
 // The B2 bitmap of the route is 1 bit a point, 32 points a word, a row
 // taking bwpr = ceil(nx / 32) words (bits past nx are 0).
@@ -189,6 +197,8 @@ struct LocalArgs {
     int wpr;                 // packed words per row
     const int32_t* q;
     uint32_t* codes;         // packed step-A codes (written by detect)
+    uint32_t* nexy;          // packed q != q[x + 1] (low bit), q != q[y + 1] (high bit)
+    uint32_t* nez;           // packed q != q[z + 1] (low bit; rank 3)
     uint32_t* spk;           // packed S (written by near)
     int32_t* dist1;          // Dist1 at the queries (S != 0 off B1)
     float* out;              // D' + S_B eta eps on B1, D' elsewhere

@@ -24,9 +24,9 @@ struct Layout {
     // signed-point route (rank 2 and 3): counters, queries, queries left to
     // the brute-force search, B2 sites; capacities in entries
     size_t ctr, qlist, slist, mlist, flist, fmin, b2list;
-    // the local first EDT and the route: packed step-A codes and S (wpr
-    // words a row), the B2 bitmap (bwpr words a row)
-    size_t codes, spk, b2bits;
+    // the local first EDT and the route: packed step-A codes, differ maps
+    // and S (wpr words a row), the B2 bitmap (bwpr words a row)
+    size_t codes, nexy, nez, spk, b2bits;
     int wpr, bwpr;
     int qcap, scap, fcap, b2cap;
     size_t total;

@@ -30,6 +30,10 @@
 // first EDT (row pass 1, column passes 1) then runs and rewrites all of it,
 // and k_pack_s packs its S map for the route. k_expand writes the byte maps
 // (equal-q mask, S) that the separable second EDT and the adjoint read.
+#include <algorithm>
+
+#include <cuda.h>
+
 #include "qai_detect.cuh"
 #include "qai_device.cuh"
 #include "qai_launch.h"
@@ -98,7 +102,7 @@ static_assert(group_begin(true, 2) == 6 && group_begin(false, 2) == 4 && group_b
 
 // Minimum resident CTAs per SM the kernels are compiled for (register cap).
 #ifndef QAI_DETECT_MINB
-#define QAI_DETECT_MINB 5
+#define QAI_DETECT_MINB 4
 #endif
 #ifndef QAI_NEAR_MINB
 #define QAI_NEAR_MINB 4
@@ -114,195 +118,370 @@ constexpr int kQueryCta = 2048;
 // The low bit of every nonzero 2-bit field of v.
 __device__ __forceinline__ uint32_t field_lsb(uint32_t v) { return (v | (v >> 1)) & 0x55555555u; }
 
-// Step A on one warp-segment of 128 points (4 per lane) of row `row`.
-// The q values one lane needs for its four points of a segment: the row and
-// its four neighbour rows (zeros off the interior rows), and the value next
-// to the segment for the first lane (x0 - 1) and the last (x0 + 4).
-struct SegQ {
+// The q values one lane needs for its four points x0 .. x0 + 3 of a row:
+// the row, its four neighbour rows (0 where a row does not exist) and the
+// values left and right of the four.
+struct Quad {
     int c[4], yl[4], yr[4], zl[4], zr[4];
-    int edge;
+    int xm, xp;
 };
 
-template <int RANK, bool VEC>
-__device__ __forceinline__ void load_segment(const LocalArgs& a, int row, int z, int y, int x0, SegQ& L)
+// (a ^ c) | (b ^ c) and a | b | c as single three-input logic operations.
+template <unsigned LUT>
+__device__ __forceinline__ unsigned lop3(unsigned a, unsigned b, unsigned c)
 {
-    const int lane = threadIdx.x & 31;
-    const int nx = a.nx;
-    const int64_t rbase = (int64_t)row * nx;
-    const int64_t plane = (int64_t)a.ny * nx;
-    const bool row_inner = y >= 1 && y <= a.ny - 2 && (RANK == 2 || (z >= 1 && z <= a.nz - 2));
-    load4_i32(a.q + rbase, x0, nx, VEC, L.c);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) L.yl[j] = L.yr[j] = L.zl[j] = L.zr[j] = 0;
-    if (row_inner) {
-        load4_i32(a.q + rbase - nx, x0, nx, VEC, L.yl);
-        load4_i32(a.q + rbase + nx, x0, nx, VEC, L.yr);
-        if (RANK == 3) {
-            load4_i32(a.q + rbase - plane, x0, nx, VEC, L.zl);
-            load4_i32(a.q + rbase + plane, x0, nx, VEC, L.zr);
-        }
-    }
-    L.edge = 0;
-    if (lane == 0 && x0 > 0) L.edge = __ldg(a.q + rbase + x0 - 1);
-    if (lane == 31 && x0 + 4 < nx) L.edge = __ldg(a.q + rbase + x0 + 4);
+    unsigned d;
+    asm("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(LUT));
+    return d;
+}
+constexpr unsigned kLutXorOr = 0x7E;  // (a ^ c) | (b ^ c)
+constexpr unsigned kLutOr3 = 0xFE;    // a | b | c
+
+constexpr unsigned kLutXorOrC = 0xBE;  // (a ^ b) | c
+
+// The fast path of step A covers fields whose indices all satisfy
+// |q| < 2^26: then every difference and every sum of six differences is
+// exact in 32 bits. Each lane checks its own four values (every value of the
+// field is some lane's own); a value outside the range sets kCtrWide, and an
+// exact pass then redoes step A over the whole field.
+constexpr unsigned kNarrowBias = 1u << 26;
+__device__ __forceinline__ bool quad_narrow(const Quad& Q)
+{
+    const unsigned acc = lop3<kLutOr3>((unsigned)Q.c[0] + kNarrowBias, (unsigned)Q.c[1] + kNarrowBias,
+                                       ((unsigned)Q.c[2] + kNarrowBias) | ((unsigned)Q.c[3] + kNarrowBias));
+    return acc < 2u * kNarrowBias;
 }
 
-// Step A for the lane's four points: b1 (bit j: point j on B1), sg (2-bit
-// sign code of S_B per point, 0 off B1) and, when MASK, the equal-q mask
-// byte per point (the byte map of the separable passes: bits z-, z+, y-, y+,
-// x-, x+, 0x3F off the interior).
-template <int RANK, bool MASK>
-__device__ __forceinline__ void step_a(const LocalArgs& a, int z, int y, int x0, const SegQ& L, unsigned& b1,
-                                       unsigned& sg, uint32_t& em)
+// Step A (Algorithm 2) for the lane's four points, the sign rule SUM and
+// every index in the fast-path range (see quad_narrow). code: 1 in the 2-bit
+// field of each B1 point (interior, some axis neighbour differs); sg: the
+// sign code of S_B per point (0 off B1 and where the fast-varying test zeroes
+// it); ne: per 2-bit field, q != q[x + 1] (low bit) and q != q[y + 1] (high
+// bit); nz: q != q[z + 1] (low bit). The ne bits of a missing neighbour are
+// not defined (their readers only ask about interior points). Every lane of
+// the warp must take part (warp vote).
+template <int RANK>
+__device__ __forceinline__ void step_a_fast(const MethodArgs& m, bool row_inner, int x0, int nx, const Quad& Q,
+                                            unsigned& code, unsigned& sg, unsigned& ne, unsigned& nz)
 {
-    const int lane = threadIdx.x & 31;
-    const int nx = a.nx;
-    const bool row_inner = y >= 1 && y <= a.ny - 2 && (RANK == 2 || (z >= 1 && z <= a.nz - 2));
-    const int *c = L.c, *yl = L.yl, *yr = L.yr, *zl = L.zl, *zr = L.zr;
-    int xm = __shfl_up_sync(kFull, c[3], 1);
-    int xp = __shfl_down_sync(kFull, c[0], 1);
-    if (lane == 0) xm = L.edge;
-    if (lane == 31) xp = L.edge;
-    b1 = 0;
+    const int *c = Q.c, *yl = Q.yl, *yr = Q.yr, *zl = Q.zl, *zr = Q.zr;
+    const unsigned thm1 = (unsigned)m.grad_threshold - 1u, lim = 2u * thm1;
+    code = 0;
     sg = 0;
-    em = 0x3F3F3F3Fu;
-    if (!row_inner) return;  // warp-uniform: off the interior nothing is on B1
-    // 32-bit sums are exact while every |q| < 2^27; the OR of the raw values
-    // is below 2^27 exactly when all are in [0, 2^27), the common case
-    unsigned acc = (unsigned)xm | (unsigned)xp;
+    ne = 0;
+    nz = 0;
+    unsigned u[4], ukeep = 0xFFFFFFFFu;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc |= (unsigned)c[j] | (unsigned)yl[j] | (unsigned)yr[j] | (unsigned)zl[j] | (unsigned)zr[j];
-    bool narrow = acc < (1u << 27);
-    if (!__all_sync(kFull, narrow)) {
-        acc = (unsigned)(xm ^ (xm >> 31)) | (unsigned)(xp ^ (xp >> 31));
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            acc |= (unsigned)(c[j] ^ (c[j] >> 31)) | (unsigned)(yl[j] ^ (yl[j] >> 31)) |
-                   (unsigned)(yr[j] ^ (yr[j] >> 31)) | (unsigned)(zl[j] ^ (zl[j] >> 31)) |
-                   (unsigned)(zr[j] ^ (zr[j] >> 31));
-        narrow = acc < (1u << 27);
+    for (int j = 0; j < 4; ++j) {
+        const unsigned q0 = (unsigned)c[j];
+        const unsigned l = (unsigned)(j == 0 ? Q.xm : c[j - 1]);
+        const unsigned r = (unsigned)(j == 3 ? Q.xp : c[j + 1]);
+        const unsigned tx = r ^ q0, ty = (unsigned)yr[j] ^ q0;
+        unsigned d, uz = 0u;
+        if (RANK == 3) {
+            const unsigned tz = (unsigned)zr[j] ^ q0;
+            d = lop3<kLutXorOrC>((unsigned)zl[j], q0, lop3<kLutOr3>(tx, ty, tz)) |
+                lop3<kLutXorOr>(l, (unsigned)yl[j], q0);
+            uz = (unsigned)zr[j] - (unsigned)zl[j] + thm1;
+            nz += min(tz, 1u) << (2 * j);
+        } else {
+            d = (tx | ty) | lop3<kLutXorOr>(l, (unsigned)yl[j], q0);
+        }
+        ne += (min(tx, 1u) + 2u * min(ty, 1u)) << (2 * j);
+        // the largest of (q[+1] - q[-1] + thm1) over the axes, unsigned:
+        // above 2 thm1 exactly when some axis is fast-varying
+        u[j] = __vimax3_u32(r - l + thm1, (unsigned)yr[j] - (unsigned)yl[j] + thm1, uz);
+        const unsigned b = min(d, 1u);
+        code += b << (2 * j);
+        ukeep = min(ukeep, u[j] | (b - 1u));  // only B1 points can keep a sign
     }
-    const bool wide = __any_sync(kFull, !narrow);
-    // interior along x: only the first and the last lanes of a row have
-    // points off it
-    const unsigned inner_bits = (x0 >= 1 && x0 + 4 <= nx - 1)
-                                    ? 0xFu
-                                    : ((x0 >= 1 && x0 <= nx - 2) ? 1u : 0u) | ((x0 + 1 >= 1 && x0 + 1 <= nx - 2) ? 2u : 0u) |
-                                          ((x0 + 2 <= nx - 2) ? 4u : 0u) | ((x0 + 3 <= nx - 2) ? 8u : 0u);
-    if (!MASK && !wide && a.m.sign_rule == 0) {
-        // the common case in two steps: B1 and the fast-varying test at
-        // every point, the sign only where a boundary keeps it
-        const int thm1 = a.m.grad_threshold - 1;
-        const unsigned lim = 2u * (unsigned)thm1;
-        unsigned keep = 0;  // bit j: point j is on B1 and not fast-varying
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int q0 = c[j];
-            const int l = j == 0 ? xm : c[j - 1];
-            const int r = j == 3 ? xp : c[j + 1];
-            unsigned d = ((unsigned)l ^ (unsigned)q0) | ((unsigned)r ^ (unsigned)q0) |
-                         ((unsigned)yl[j] ^ (unsigned)q0) | ((unsigned)yr[j] ^ (unsigned)q0);
-            bool fast = (unsigned)(r - l + thm1) > lim || (unsigned)(yr[j] - yl[j] + thm1) > lim;
-            if (RANK == 3) {
-                d |= ((unsigned)zl[j] ^ (unsigned)q0) | ((unsigned)zr[j] ^ (unsigned)q0);
-                fast = fast || (unsigned)(zr[j] - zl[j] + thm1) > lim;
-            }
-            const bool site = ((inner_bits >> j) & 1u) && d != 0u;
-            b1 |= site ? 1u << j : 0u;
-            keep |= (site && !fast) ? 1u << j : 0u;
-        }
-        if (__any_sync(kFull, keep != 0)) {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                if (!((keep >> j) & 1u)) continue;
-                const int l = j == 0 ? xm : c[j - 1];
-                const int r = j == 3 ? xp : c[j + 1];
-                int sum = l + r + yl[j] + yr[j] - 2 * RANK * c[j];
-                if (RANK == 3) sum += zl[j] + zr[j];
-                sg |= (sum > 0 ? 1u : (sum < 0 ? 2u : 0u)) << (2 * j);
-            }
-        }
+    if (!row_inner) {  // warp-uniform: off the interior nothing is on B1
+        code = 0;
         return;
     }
+    // interior along x: x in [1, nx - 2]
+    unsigned inner = x0 == 0 ? 0xFCu : 0xFFu;
+    const int rem = nx - 1 - x0;  // points x0 .. x0 + rem - 1 are below nx - 1
+    if (rem < 4) inner &= rem > 0 ? (1u << (2 * rem)) - 1u : 0u;
+    code &= inner;
+    if (__any_sync(kFull, ukeep <= lim)) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (!((code >> (2 * j)) & 1u) || u[j] > lim) continue;
+            const int l = j == 0 ? Q.xm : c[j - 1];
+            const int r = j == 3 ? Q.xp : c[j + 1];
+            int sum = l + r + yl[j] + yr[j] - 2 * RANK * c[j];
+            if (RANK == 3) sum += zl[j] + zr[j];
+            sg |= (sum > 0 ? 1u : (sum < 0 ? 2u : 0u)) << (2 * j);
+        }
+    }
+}
+
+// Step A for the lane's four points by the general form (any indices, both
+// sign rules; 64-bit sums): code and sg as step_a_fast, the differ bits ne
+// and nz, and em, the equal-q mask byte per point (bits z-, z+, y-, y+, x-,
+// x+; 0x3F off the interior) with the sign code in bits 6-7: the byte map of
+// the separable passes.
+template <int RANK>
+__device__ __forceinline__ void step_a_exact(const MethodArgs& m, bool row_inner, int x0, int nx, const Quad& Q,
+                                             unsigned& code, unsigned& sg, unsigned& ne, unsigned& nz, uint32_t& em)
+{
+    code = 0;
+    sg = 0;
+    ne = 0;
+    nz = 0;
+    em = 0x3F3F3F3Fu;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int r = j == 3 ? Q.xp : Q.c[j + 1];
+        ne |= ((Q.c[j] != r ? 1u : 0u) | (Q.c[j] != Q.yr[j] ? 2u : 0u)) << (2 * j);
+        if (RANK == 3) nz |= (Q.c[j] != Q.zr[j] ? 1u : 0u) << (2 * j);
+    }
+    if (!row_inner) return;
     em = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const bool inner = (inner_bits >> j) & 1u;
-        const int l = j == 0 ? xm : c[j - 1];
-        const int r = j == 3 ? xp : c[j + 1];
+        const bool in = x0 + j >= 1 && x0 + j <= nx - 2;
+        const int l = j == 0 ? Q.xm : Q.c[j - 1];
+        const int r = j == 3 ? Q.xp : Q.c[j + 1];
         unsigned mk;
         bool site;
-        int code;
-        if (!wide) detect_point<RANK, false>(c[j], zl[j], zr[j], yl[j], yr[j], l, r, inner, a.m, mk, site, code);
-        else detect_point<RANK, true>(c[j], zl[j], zr[j], yl[j], yr[j], l, r, inner, a.m, mk, site, code);
-        b1 |= site ? 1u << j : 0u;
-        sg |= (unsigned)code << (2 * j);  // 0 off the interior
-        em |= ((inner ? mk : 0x3Fu) | (unsigned)code << 6) << (8 * j);
+        int cd;
+        detect_point<RANK, true>(Q.c[j], Q.zl[j], Q.zr[j], Q.yl[j], Q.yr[j], l, r, in, m, mk, site, cd);
+        code |= site ? 1u << (2 * j) : 0u;
+        sg |= (unsigned)cd << (2 * j);  // 0 off the interior
+        em |= ((in ? mk : 0x3Fu) | (unsigned)cd << 6) << (8 * j);
     }
 }
 
-// Bits 0, 1, 2, 3 of b to bits 0, 2, 4, 6.
-__device__ __forceinline__ unsigned spread4(unsigned b)
-{
-    return (b & 1u) | ((b & 2u) << 1) | ((b & 4u) << 2) | ((b & 8u) << 3);
-}
-
+// The outputs of step A for the lane's four points of row `row`: D''
+// wherever Dist2 does not matter (D' + S_B eta eps on B1, D' elsewhere: the
+// expressions of compensate(), with C = +0 the fma is the product), the code
+// byte and the differ bytes (up to the row's last packed word).
 template <int RANK, bool VEC>
-__device__ __forceinline__ void detect_segment(const LocalArgs& a, int row, int z, int y, int x0, const SegQ& L,
-                                               unsigned& nsigned)
+__device__ __forceinline__ void store_step_a(const LocalArgs& a, int row, int x0, const Quad& Q, unsigned code,
+                                             unsigned sg, unsigned ne, unsigned nz, unsigned& nsigned)
 {
     const int nx = a.nx;
-    const int64_t rbase = (int64_t)row * nx;
-    unsigned b1, sg;
-    uint32_t em;
-    step_a<RANK, false>(a, z, y, x0, L, b1, sg, em);
-    // outputs where Dist2 does not matter: the expressions of compensate()
-    // (with C = +0 the fma is the product)
+    float* orow = a.out + (int64_t)row * nx;
     float o[4];
     if (__any_sync(kFull, sg != 0)) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const unsigned cd = (sg >> (2 * j)) & 3u;
             const float cc = (cd == 1u ? 1.0f : (cd == 2u ? -1.0f : 0.0f)) * a.m.eta_eb;
-            o[j] = a.m.output_c ? cc : fmaf((float)L.c[j], a.m.two_eb, cc);
+            o[j] = a.m.output_c ? cc : fmaf((float)Q.c[j], a.m.two_eb, cc);
         }
         nsigned += __popc(field_lsb(sg));
     } else {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) o[j] = a.m.output_c ? 0.0f : (float)L.c[j] * a.m.two_eb;
+        for (int j = 0; j < 4; ++j) o[j] = a.m.output_c ? 0.0f : (float)Q.c[j] * a.m.two_eb;
     }
     if (VEC) {
-        if (x0 < nx) *reinterpret_cast<float4*>(a.out + rbase + x0) = make_float4(o[0], o[1], o[2], o[3]);
+        if (x0 < nx) *reinterpret_cast<float4*>(orow + x0) = make_float4(o[0], o[1], o[2], o[3]);
     } else {
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-            if (x0 + j < nx) a.out[rbase + x0 + j] = o[j];
+            if (x0 + j < nx) orow[x0 + j] = o[j];
     }
-    // the code byte of the four points (0 past nx, up to the row's last word)
-    if (x0 < 16 * a.wpr)
-        reinterpret_cast<uint8_t*>(a.codes)[(int64_t)row * 4 * a.wpr + (x0 >> 2)] = (uint8_t)(spread4(b1) + sg);
+    if (x0 < 16 * a.wpr) {
+        const int64_t b = (int64_t)row * 4 * a.wpr + (x0 >> 2);
+        reinterpret_cast<uint8_t*>(a.codes)[b] = (uint8_t)(code + sg);
+        reinterpret_cast<uint8_t*>(a.nexy)[b] = (uint8_t)ne;
+        if (RANK == 3) reinterpret_cast<uint8_t*>(a.nez)[b] = (uint8_t)nz;
+    }
 }
 
+// The Quad of the lane's four points of row `row` from global memory: one
+// 128-bit load per row when VEC (x0 and the rows 16-byte aligned), the x
+// neighbours from the adjacent lanes (the first and the last lane load
+// theirs). Every lane of the warp must take part.
 template <int RANK, bool VEC>
-__global__ void __launch_bounds__(256, QAI_DETECT_MINB) k_detect(LocalArgs a)
+__device__ __forceinline__ void load_quad(const LocalArgs& a, int row, int z, int y, int x0, Quad& Q)
+{
+    const int lane = threadIdx.x & 31;
+    const int nx = a.nx;
+    const int32_t* qr = a.q + (int64_t)row * nx;
+    const int64_t plane = (int64_t)a.ny * nx;
+    load4_i32(qr, x0, nx, VEC, Q.c);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) Q.yl[j] = Q.yr[j] = Q.zl[j] = Q.zr[j] = 0;
+    if (y >= 1) load4_i32(qr - nx, x0, nx, VEC, Q.yl);
+    if (y + 1 < a.ny) load4_i32(qr + nx, x0, nx, VEC, Q.yr);
+    if (RANK == 3) {
+        if (z >= 1) load4_i32(qr - plane, x0, nx, VEC, Q.zl);
+        if (z + 1 < a.nz) load4_i32(qr + plane, x0, nx, VEC, Q.zr);
+    }
+    Q.xm = __shfl_up_sync(kFull, Q.c[3], 1);
+    Q.xp = __shfl_down_sync(kFull, Q.c[0], 1);
+    if (lane == 0) Q.xm = x0 > 0 ? __ldg(qr + x0 - 1) : 0;
+    if (lane == 31) Q.xp = x0 + 4 < nx ? __ldg(qr + x0 + 4) : 0;
+}
+
+// Step A, one warp per row, 128 points per step (the form for 2-D fields, for
+// rows that are not 16-byte multiples and for the exact pass). mode 0: the
+// fast path, flagging a field with an index outside its range; 1: the exact
+// form; 2: the exact form, only when the flag is set.
+template <int RANK, bool VEC>
+__global__ void __launch_bounds__(256, QAI_DETECT_MINB) k_detect(LocalArgs a, int mode)
 {
     wait_prior_grid();
+    if (mode == 2 && *static_cast<const volatile int*>(a.ctr + kCtrWide) == 0) return;
     const int rows = a.nz * a.ny;
     const int wstride = gridDim.x * (blockDim.x >> 5);
     const int lx = 4 * (int)(threadIdx.x & 31);
     unsigned nsigned = 0;
+    bool wide = false;
     for (int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += wstride) {
         const int z = RANK == 3 ? row / a.ny : 0;
         const int y = row - z * a.ny;
+        const bool row_inner = y >= 1 && y <= a.ny - 2 && (RANK == 2 || (z >= 1 && z <= a.nz - 2));
         for (int x0 = lx; x0 - lx < a.nx; x0 += 128) {
-            SegQ b;
-            load_segment<RANK, VEC>(a, row, z, y, x0, b);
-            detect_segment<RANK, VEC>(a, row, z, y, x0, b, nsigned);
+            Quad Q;
+            load_quad<RANK, VEC>(a, row, z, y, x0, Q);
+            unsigned code, sg, ne, nz;
+            if (mode == 0) {
+                wide |= !quad_narrow(Q);
+                step_a_fast<RANK>(a.m, row_inner, x0, a.nx, Q, code, sg, ne, nz);
+            } else {
+                uint32_t em;
+                step_a_exact<RANK>(a.m, row_inner, x0, a.nx, Q, code, sg, ne, nz, em);
+            }
+            store_step_a<RANK, VEC>(a, row, x0, Q, code, sg, ne, nz, nsigned);
         }
     }
     // B1 points with S != 0: one atomic per warp that has any
     nsigned = __reduce_add_sync(kFull, nsigned);
-    if ((threadIdx.x & 31) == 0 && nsigned) atomicAdd(a.ctr + kCtrSigned, (int)nsigned);
+    if ((threadIdx.x & 31) == 0 && nsigned) atomicAdd(a.ctr + (mode == 2 ? kCtrSignedExact : kCtrSigned), (int)nsigned);
+    if (__any_sync(kFull, wide) && (threadIdx.x & 31) == 0) *static_cast<volatile int*>(a.ctr + kCtrWide) = 1;
+}
+
+// ---- step A for 3-D fields on tiles staged by the tensor memory accelerator
+//
+// A CTA walks runs of consecutive z-planes of (x, y) tiles of kTX x kTY
+// points. Each plane of a tile, with a one-point halo in y and a four-point
+// halo in x (the copy starts on a 16-byte boundary), comes into shared memory
+// as one TMA box copy (points outside the field read 0); a ring of four
+// plane buffers holds planes z - 1, z, z + 1 while z + 2 is in flight, so
+// every q value crosses from L2 into the SM once per tile. The steps of all
+// tiles (tile-major, z fastest) are split evenly over the CTAs.
+constexpr int kTX = 128, kTY = 32;
+constexpr int kBoxX = kTX + 8, kBoxY = kTY + 2;
+constexpr int kPlaneInts = kBoxX * kBoxY;
+constexpr int kSlotInts = (kPlaneInts + 31) / 32 * 32;  // 128-byte multiples
+constexpr int kSlots = 4;
+constexpr size_t kTmaSmem = (size_t)kSlots * kSlotInts * 4 + kSlots * 8;
+static_assert((kBoxX * 4) % 16 == 0, "TMA box rows are 16-byte multiples");
+static_assert(kTY % 8 == 0, "eight warps share a tile's rows");
+constexpr unsigned kWaitLimit = 1u << 22;  // polls of a plane's barrier before the kernel gives up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Plane z of tile (x0t, y0t) into the ring slot of z, completing on the
+// slot's barrier (one thread).
+__device__ __forceinline__ void tma_plane(const CUtensorMap* tm, int* slot, uint64_t* bar, int x0t, int y0t, int z)
+{
+    const uint32_t b = smem_u32(bar);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"((uint32_t)(kPlaneInts * 4))
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+            "r"(smem_u32(slot)), "l"(reinterpret_cast<uint64_t>(tm)), "r"(x0t - 4), "r"(y0t - 1), "r"(z), "r"(b)
+        : "memory");
+}
+
+// Waits (bounded) for the current phase of a slot's barrier; false if the
+// limit ran out.
+__device__ __forceinline__ bool wait_plane(uint64_t* bar, uint32_t parity)
+{
+    const uint32_t b = smem_u32(bar);
+    for (unsigned i = 0; i < kWaitLimit; ++i) {
+        uint32_t done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done)
+                     : "r"(b), "r"(parity)
+                     : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(256, 3) k_detect_tma(LocalArgs a, const __grid_constant__ CUtensorMap tm,
+                                                      int tiles_x, int64_t steps)
+{
+    extern __shared__ __align__(1024) int sbuf[];  // the plane ring, then the slots' barriers
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sbuf + kSlots * kSlotInts);
+    wait_prior_grid();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kSlots; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[s])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    uint32_t parity = 0;  // bit s: the phase parity slot s completes next
+    bool timed_out = false, wide = false;
+    unsigned nsigned = 0;
+    const int nz = a.nz;
+    const int64_t s0 = steps * blockIdx.x / gridDim.x, s1 = steps * (blockIdx.x + 1) / gridDim.x;
+    auto slot_of = [](int z) { return ((z % kSlots) + kSlots) % kSlots; };
+    for (int64_t s = s0; s < s1;) {
+        // a run of planes z0 .. z1 - 1 of one tile
+        const int tile = (int)(s / nz);
+        const int z0 = (int)(s - (int64_t)tile * nz);
+        const int z1 = (int)min((int64_t)nz, (int64_t)z0 + (s1 - s));
+        const int x0t = (tile % tiles_x) * kTX, y0t = (tile / tiles_x) * kTY;
+        if (threadIdx.x == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            for (int p = z0 - 1; p <= min(z0 + 2, z1); ++p)
+                tma_plane(&tm, sbuf + slot_of(p) * kSlotInts, &bars[slot_of(p)], x0t, y0t, p);
+        }
+        for (int z = z0; z < z1; ++z) {
+            for (int p = (z == z0 ? z0 - 1 : z + 1); p <= z + 1; ++p) {
+                const int sl = slot_of(p);
+                if (!wait_plane(&bars[sl], (parity >> sl) & 1u)) timed_out = true;
+                parity ^= 1u << sl;
+            }
+            const int* P0 = sbuf + slot_of(z) * kSlotInts;
+            const int* Pm = sbuf + slot_of(z - 1) * kSlotInts;
+            const int* Pp = sbuf + slot_of(z + 1) * kSlotInts;
+            const int x0 = x0t + 4 * lane;
+#pragma unroll 1
+            for (int r = warp; r < kTY; r += 8) {
+                const int y = y0t + r;
+                if (y >= a.ny) break;  // warp-uniform
+                const int o = (r + 1) * kBoxX + 4 + 4 * lane;
+                Quad Q;
+                auto ld4s = [](const int* p, int v[4]) {
+                    const int4 t = *reinterpret_cast<const int4*>(p);
+                    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+                };
+                ld4s(P0 + o, Q.c);
+                ld4s(P0 + o - kBoxX, Q.yl);
+                ld4s(P0 + o + kBoxX, Q.yr);
+                ld4s(Pm + o, Q.zl);
+                ld4s(Pp + o, Q.zr);
+                Q.xm = P0[o - 1];
+                Q.xp = P0[o + 4];
+                const int row = z * a.ny + y;
+                const bool row_inner = y >= 1 && y <= a.ny - 2 && z >= 1 && z <= nz - 2;
+                unsigned code, sg, ne, nzb;
+                wide |= !quad_narrow(Q);
+                step_a_fast<3>(a.m, row_inner, x0, a.nx, Q, code, sg, ne, nzb);
+                store_step_a<3, true>(a, row, x0, Q, code, sg, ne, nzb, nsigned);
+            }
+            __syncthreads();  // every read of plane z - 1 done: its slot takes z + 3
+            if (threadIdx.x == 0 && z + 3 <= z1) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                tma_plane(&tm, sbuf + slot_of(z + 3) * kSlotInts, &bars[slot_of(z + 3)], x0t, y0t, z + 3);
+            }
+        }
+        s += z1 - z0;
+    }
+    nsigned = __reduce_add_sync(kFull, nsigned);
+    if (lane == 0 && nsigned) atomicAdd(a.ctr + kCtrSigned, (int)nsigned);
+    if (timed_out && lane == 0) *static_cast<volatile int*>(a.ctr + kCtrTimeout) = 1;
+    if (__any_sync(kFull, wide) && lane == 0) *static_cast<volatile int*>(a.ctr + kCtrWide) = 1;
 }
 
 // Word k of packed row `prow` (0 past the row, or where ok is false).
@@ -338,8 +517,33 @@ __device__ __forceinline__ void near_flush(const LocalArgs& a, const Query* qbuf
     for (int i = threadIdx.x; i < n && *qbase + i < a.qcap; i += blockDim.x) a.qlist[*qbase + i] = qbuf[i];
 }
 
-// S at every point, Dist1 where S != 0 off B1, and the queries: one warp per
-// row, one packed word (16 points) per lane and step.
+// Squared distance from (z, y, x) to the first B1 point among the table
+// entries of squared length >= 2 (in table order); 0 if none.
+template <int RANK>
+__device__ __forceinline__ int deep_r2(const LocalArgs& a, int z, int y, int x)
+{
+    const int* tab = RANK == 3 ? c_near.off3 : c_near.off2;
+    constexpr int n1 = RANK == 3 ? 6 : 4, ntab = RANK == 3 ? kNearN3 : kNearN2;
+    for (int e = n1; e < ntab; ++e) {
+        const int o = tab[e];
+        const int xx = x + (int)(int8_t)(o & 0xFF), yy = y + (int)(int8_t)((o >> 8) & 0xFF);
+        const int zz = z + (int)(int8_t)((o >> 16) & 0xFF);
+        if ((unsigned)xx >= (unsigned)a.nx || (unsigned)yy >= (unsigned)a.ny || (unsigned)zz >= (unsigned)a.nz) continue;
+        const uint32_t w = __ldg(a.codes + ((int64_t)zz * a.ny + yy) * a.wpr + (xx >> 4));
+        if ((w >> (2 * (xx & 15))) & 3u) return (int)((unsigned)o >> 24);
+    }
+    return 0;
+}
+
+// S at every point, Dist1 where S != 0 off B1, and the queries. A warp takes
+// kNearRows rows of one plane at a time, one packed word (16 points) per
+// lane and step, with the words of all the rows it needs loaded up front.
+// The six neighbours at squared distance 1 are tested for all words at once;
+// a word with a point still unresolved after them is searched by the whole
+// warp, 32 table entries at a time (a lane per entry), the first entry in
+// table order with a site taking each point.
+constexpr int kNearRows = 4;
+
 template <int RANK>
 __global__ void __launch_bounds__(256, QAI_NEAR_MINB) k_near(LocalArgs a)
 {
@@ -349,95 +553,129 @@ __global__ void __launch_bounds__(256, QAI_NEAR_MINB) k_near(LocalArgs a)
     if (threadIdx.x == 0) qn = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const int rows = a.nz * a.ny;
     const int wpr = a.wpr;
     const uint32_t* cm = a.codes;
+    const int yb = (a.ny + kNearRows - 1) / kNearRows;
+    const int items = a.nz * yb;
     const int wstride = gridDim.x * (blockDim.x >> 5);
     const int* tab = RANK == 3 ? c_near.off3 : c_near.off2;
+    constexpr int n1 = RANK == 3 ? 6 : 4, ntab = RANK == 3 ? kNearN3 : kNearN2;
     bool fail = false;
-    for (int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += wstride) {
-        const int z = RANK == 3 ? row / a.ny : 0;
-        const int y = row - z * a.ny;
+    for (int it = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < items; it += wstride) {
+        const int z = RANK == 3 ? it / yb : 0;
+        const int y0 = (it - z * yb) * kNearRows;
+        const int row0 = z * a.ny + y0;
         for (int ks = 0; ks < wpr; ks += 32) {
             const int k = ks + lane;
             const bool in = k < wpr;
-            const uint32_t w = pword(cm, row, k, wpr, true);
+            // rows y0 - 1 .. y0 + kNearRows of this plane; planes z -+ 1
+            uint32_t wy[kNearRows + 2], wzm[kNearRows], wzp[kNearRows];
+#pragma unroll
+            for (int i = 0; i < kNearRows + 2; ++i) {
+                const int y = y0 - 1 + i;
+                wy[i] = pword(cm, (int64_t)row0 - 1 + i, k, wpr, y >= 0 && y < a.ny);
+            }
+#pragma unroll
+            for (int i = 0; i < kNearRows; ++i) {
+                const bool ok = RANK == 3 && y0 + i < a.ny;
+                wzm[i] = pword(cm, (int64_t)row0 + i - a.ny, k, wpr, ok && z > 0);
+                wzp[i] = pword(cm, (int64_t)row0 + i + a.ny, k, wpr, ok && z < a.nz - 1);
+            }
             const int nv = a.nx - 16 * k;  // fields of this word inside the row
             const uint32_t valid = !in ? 0u : (nv >= 16 ? 0xFFFFFFFFu : (1u << (2 * nv)) - 1u);
-            const uint32_t site = field_lsb(w);
-            uint32_t need = ~site & 0x55555555u & valid;  // points off B1
-            uint32_t s = w - site;                        // B1: the code less one is S_B
-            if (__any_sync(kFull, need != 0)) {
-                uint32_t res = 0;     // the code of the site each resolved point took
-                uint32_t grp[kNearR2 + 1];  // points resolved at squared distance r2
-                const uint32_t need0 = need;
-                // squared distance 1, in tie order z-, y-, x-, x+, y+, z+
-                auto take = [&](uint32_t v) {
-                    const uint32_t t = field_lsb(v) & need;
-                    res |= v & (t * 3u);
-                    need &= ~t;
-                };
-                const bool zm = RANK == 3 && z > 0, zp = RANK == 3 && z < a.nz - 1;
-                const uint32_t wzm = pword(cm, row - a.ny, k, wpr, zm);
-                const uint32_t wym = pword(cm, row - 1, k, wpr, y > 0);
-                const uint32_t wyp = pword(cm, row + 1, k, wpr, y < a.ny - 1);
-                const uint32_t wzp = pword(cm, row + a.ny, k, wpr, zp);
-                const uint32_t wxm = pshift(cm, row, k, wpr, true, w, -1);
-                const uint32_t wxp = pshift(cm, row, k, wpr, true, w, 1);
-                if (RANK == 3) take(wzm);
-                take(wym);
-                take(wxm);
-                take(wxp);
-                take(wyp);
-                if (RANK == 3) take(wzp);
-                grp[1] = need0 & ~need;
 #pragma unroll
-                for (int r = 2; r <= kNearR2; ++r) grp[r] = 0;
+            for (int i = 0; i < kNearRows; ++i) {
+                const int y = y0 + i;
+                if (y >= a.ny) break;  // warp-uniform
+                const int row = row0 + i;
+                const uint32_t w = wy[i + 1];
+                const uint32_t site = field_lsb(w);
+                uint32_t need = ~site & 0x55555555u & valid;  // points off B1
+                uint32_t s = w - site;                        // B1: the code less one is S_B
                 if (__any_sync(kFull, need != 0)) {
-                    // squared distances 2..8: the rest of the table in order
+                    uint32_t res = 0;  // the code of the site each resolved point took
+                    const uint32_t need0 = need;
+                    // squared distance 1, in tie order z-, y-, x-, x+, y+, z+
+                    auto take = [&](uint32_t v) {
+                        const uint32_t t = field_lsb(v) & need;
+                        res |= v & (t * 3u);
+                        need &= ~t;
+                    };
+                    const uint32_t wxm = pshift(cm, row, k, wpr, true, w, -1);
+                    const uint32_t wxp = pshift(cm, row, k, wpr, true, w, 1);
+                    if (RANK == 3) take(wzm[i]);
+                    take(wy[i]);
+                    take(wxm);
+                    take(wxp);
+                    take(wy[i + 2]);
+                    if (RANK == 3) take(wzp[i]);
+                    const uint32_t at1 = need0 & ~need;  // resolved at squared distance 1
+                    // squared distances 2..8: the words with a point left, one
+                    // at a time, searched by the warp
+                    for (unsigned needy = __ballot_sync(kFull, need != 0); needy; needy &= needy - 1) {
+                        const int src = __ffs(needy) - 1;
+                        const int kk = __shfl_sync(kFull, k, src);
+                        uint32_t nd = __shfl_sync(kFull, need, src);
+                        uint32_t rs = 0;
+                        for (int base = n1; base < ntab && nd; base += 32) {
+                            const int e = base + lane;
+                            uint32_t t = 0, v = 0;
+                            if (e < ntab) {
+                                const int o = tab[e];
+                                const int dx = (int)(int8_t)(o & 0xFF), dy = (int)(int8_t)((o >> 8) & 0xFF);
+                                const int dz = (int)(int8_t)((o >> 16) & 0xFF);
+                                const bool ok = (unsigned)(y + dy) < (unsigned)a.ny &&
+                                                (RANK == 2 || (unsigned)(z + dz) < (unsigned)a.nz);
+                                const int64_t prow = (int64_t)row + (int64_t)dz * a.ny + dy;
+                                const uint32_t w0 = pword(cm, prow, kk, wpr, ok);
+                                const uint32_t wn = pword(cm, prow, dx > 0 ? kk + 1 : kk - 1, wpr, ok && dx != 0);
+                                v = dx > 0 ? __funnelshift_r(w0, wn, 2 * dx)
+                                           : (dx < 0 ? __funnelshift_l(wn, w0, -2 * dx) : w0);
+                                t = field_lsb(v) & nd;
+                            }
+                            // each point goes to the first entry (lowest lane) with a site
+                            uint32_t incl = t;
 #pragma unroll
-                    for (int r = 2; r <= kNearR2; ++r) {
-                        const uint32_t before = need;
-                        const int e0 = group_begin(RANK == 3, r), e1 = group_begin(RANK == 3, r + 1);
-                        for (int e = e0; e < e1; ++e) {
-                            const int o = tab[e];
-                            const int dx = (int)(int8_t)(o & 0xFF), dy = (int)(int8_t)((o >> 8) & 0xFF);
-                            const int dz = (int)(int8_t)((o >> 16) & 0xFF);
-                            const bool ok = (unsigned)(y + dy) < (unsigned)a.ny &&
-                                            (RANK == 2 || (unsigned)(z + dz) < (unsigned)a.nz);
-                            const int64_t prow = (int64_t)row + (int64_t)dz * a.ny + dy;
-                            const uint32_t wr = pword(cm, prow, k, wpr, ok);
-                            take(pshift(cm, prow, k, wpr, ok, wr, dx));
+                            for (int d = 1; d < 32; d <<= 1) {
+                                const uint32_t x = __shfl_up_sync(kFull, incl, d);
+                                if (lane >= d) incl |= x;
+                            }
+                            uint32_t excl = __shfl_up_sync(kFull, incl, 1);
+                            if (lane == 0) excl = 0;
+                            rs |= v & ((t & ~excl) * 3u);
+                            nd &= ~__shfl_sync(kFull, incl, 31);
                         }
-                        grp[r] = before & ~need;
+                        rs = __reduce_or_sync(kFull, rs);
+                        if (lane == src) {
+                            res |= rs;
+                            need = nd;
+                        }
                     }
                     fail |= need != 0;
-                }
-                const uint32_t resolved = need0 & ~need;
-                const uint32_t soff = res - resolved;  // the site's code less one: S
-                s |= soff;
-                uint32_t qm = field_lsb(soff);         // queries: S != 0 off B1
-                while (qm) {
-                    const int f = __ffs(qm) - 1;
-                    qm &= qm - 1;
-                    int r2 = 1;
-#pragma unroll
-                    for (int r = kNearR2; r >= 1; --r)
-                        if ((grp[r] >> f) & 1u) r2 = r;
-                    const int code = (int)((soff >> f) & 3u);
-                    const int p = row * a.nx + 16 * k + (f >> 1);
-                    a.dist1[p] = r2;
-                    const Query qe{p, (r2 << 2) | code};
-                    const int kq = atomicAdd(&qn, 1);
-                    if (kq < kQueryCta) {
-                        qbuf[kq] = qe;
-                    } else {
-                        const int g = atomicAdd(a.ctr + kCtrQueries, 1);
-                        if (g < a.qcap) a.qlist[g] = qe;
+                    const uint32_t resolved = need0 & ~need;
+                    const uint32_t soff = res - resolved;  // the site's code less one: S
+                    s |= soff;
+                    uint32_t qm = field_lsb(soff);         // queries: S != 0 off B1
+                    while (qm) {
+                        const int f = __ffs(qm) - 1;
+                        qm &= qm - 1;
+                        const int x = 16 * k + (f >> 1);
+                        const int r2 = (at1 >> f) & 1u ? 1 : deep_r2<RANK>(a, z, y, x);
+                        const int code = (int)((soff >> f) & 3u);
+                        const int p = row * a.nx + x;
+                        a.dist1[p] = r2;
+                        const Query qe{p, (r2 << 2) | code};
+                        const int kq = atomicAdd(&qn, 1);
+                        if (kq < kQueryCta) {
+                            qbuf[kq] = qe;
+                        } else {
+                            const int g = atomicAdd(a.ctr + kCtrQueries, 1);
+                            if (g < a.qcap) a.qlist[g] = qe;
+                        }
                     }
                 }
+                if (in) a.spk[(int64_t)row * wpr + k] = s;
             }
-            if (in) a.spk[(int64_t)row * wpr + k] = s;
         }
     }
     near_flush(a, qbuf, &qn, &qbase, fail);
@@ -463,12 +701,13 @@ __global__ void __launch_bounds__(256) k_expand(LocalArgs a, int mode)
         const int z = RANK == 3 ? row / a.ny : 0;
         const int y = row - z * a.ny;
         const int64_t rbase = (int64_t)row * a.nx;
+        const bool row_inner = y >= 1 && y <= a.ny - 2 && (RANK == 2 || (z >= 1 && z <= a.nz - 2));
         for (int x0 = lx; x0 - lx < a.nx; x0 += 128) {
-            SegQ b;
-            load_segment<RANK, VEC>(a, row, z, y, x0, b);
-            unsigned b1, sg;
+            Quad Q;
+            load_quad<RANK, VEC>(a, row, z, y, x0, Q);
+            unsigned code, sg, ne, nz;
             uint32_t em;
-            step_a<RANK, true>(a, z, y, x0, b, b1, sg, em);
+            step_a_exact<RANK>(a.m, row_inner, x0, a.nx, Q, code, sg, ne, nz, em);
             const uint32_t sw = x0 < 16 * a.wpr ? __ldg(a.spk + (int64_t)row * a.wpr + (x0 >> 4)) >> (2 * (x0 & 15)) : 0u;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -516,13 +755,89 @@ int one_wave(K kern, int waves = 1)
 }
 }  // namespace
 
-cudaError_t launch_local_detect(const LocalArgs& a, cudaStream_t st)
+namespace {
+// cuTensorMapEncodeTiled, found once through the runtime (no link-time
+// dependency on the driver library).
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiled encode_tiled()
+{
+    static EncodeTiled fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult qr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &qr) !=
+                cudaSuccess ||
+            qr != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<EncodeTiled>(p);
+    }();
+    return fn;
+}
+
+// The tensor map of q as an (nx, ny, nz) int32 array with kBoxX x kBoxY x 1
+// boxes (points outside the array read 0); false if it cannot be made.
+bool q_tensor_map(const LocalArgs& a, CUtensorMap* tm)
+{
+    EncodeTiled enc = encode_tiled();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)a.nx, (cuuint64_t)a.ny, (cuuint64_t)a.nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)a.nx * 4, (cuuint64_t)a.nx * a.ny * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)kBoxX, (cuuint32_t)kBoxY, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(tm, CU_TENSOR_MAP_DATA_TYPE_INT32, 3, const_cast<int32_t*>(a.q), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+}  // namespace
+
+// The fast path of step A: the tiled form for 3-D fields of 16-byte rows, the
+// row form otherwise.
+static cudaError_t fast_detect(const LocalArgs& a, cudaStream_t st)
 {
     auto run = [&](auto kern) {
-        return launch_chained(kern, dim3(one_wave(kern, QAI_DETECT_WAVES)), dim3(256), 0, st, a);
+        return launch_chained(kern, dim3(one_wave(kern, QAI_DETECT_WAVES)), dim3(256), 0, st, a, 0);
     };
+    if (a.rank == 3 && a.vec) {
+        // the tiled form: rows of 16-byte multiples, 16-byte aligned q and D''
+        CUtensorMap tm;
+        if (q_tensor_map(a, &tm)) {
+            static bool attr = false;
+            if (!attr) {
+                cudaError_t e = cudaFuncSetAttribute(k_detect_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)kTmaSmem);
+                if (e != cudaSuccess) return e;
+                attr = true;
+            }
+            int dev = 0, sms = 152, per = 1;
+            if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_detect_tma, 256, kTmaSmem) != cudaSuccess ||
+                per < 1)
+                per = 1;
+            const int tiles_x = (a.nx + kTX - 1) / kTX, tiles_y = (a.ny + kTY - 1) / kTY;
+            const int64_t steps = (int64_t)tiles_x * tiles_y * a.nz;
+            const int grid = (int)std::min<int64_t>(steps, (int64_t)sms * per);
+            return launch_chained(k_detect_tma, dim3(grid), dim3(256), kTmaSmem, st, a, tm, tiles_x, steps);
+        }
+    }
     if (a.rank == 3) return a.vec ? run(k_detect<3, true>) : run(k_detect<3, false>);
     return a.vec ? run(k_detect<2, true>) : run(k_detect<2, false>);
+}
+
+cudaError_t launch_local_detect(const LocalArgs& a, cudaStream_t st)
+{
+    // the exact pass: after the fast path, gated on its flag; alone under the
+    // sign rule FIRST (no fast path)
+    auto exact = [&](int mode) {
+        auto run = [&](auto kern) {
+            return launch_chained(kern, dim3(one_wave(kern, QAI_DETECT_WAVES)), dim3(256), 0, st, a, mode);
+        };
+        if (a.rank == 3) return a.vec ? run(k_detect<3, true>) : run(k_detect<3, false>);
+        return a.vec ? run(k_detect<2, true>) : run(k_detect<2, false>);
+    };
+    if (a.m.sign_rule != 0) return exact(1);
+    cudaError_t e = fast_detect(a, st);
+    return e != cudaSuccess ? e : exact(2);
 }
 
 cudaError_t launch_local_near(const LocalArgs& a, cudaStream_t st)

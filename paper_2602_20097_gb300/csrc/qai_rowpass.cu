@@ -369,8 +369,9 @@ __global__ void __launch_bounds__(256) k_rowpass(RowArgs a)
     wait_prior_grid();
     // gated launches (signed-point route): run only when the flag is set
     if (a.gate && *static_cast<const volatile int*>(a.gate) == 0) return;
-    // row pass 1 of the route starts its counters (not the local-EDT flag)
-    if (PHASE == 1 && a.route_ctr && blockIdx.x == 0 && threadIdx.x < kCtrLocalFail)
+    // row pass 1 of the route starts its counters again (not the timeout and
+    // local-EDT flags)
+    if (PHASE == 1 && a.route_ctr && blockIdx.x == 0 && threadIdx.x < kCtrTimeout)
         a.route_ctr[threadIdx.x] = 0;
     const int warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
     // one row per warp, or (a grid smaller than the rows: the dense second EDT

@@ -9,9 +9,9 @@
 // give the exact Dist2 of every query, Eq. 2 over the sign-flipping boundary
 // B2 of Algorithm 3:
 //
-//   k_b2map    GetBoundary(S) at every interior point, from the packed S map
-//              (q is read only where two neighbours' S differ, for the
-//              same-q test of the default rule): the B2 bitmap, 1 bit a point.
+//   k_b2map    GetBoundary(S) at every interior point, bit-parallel from the
+//              packed S map and the differ maps of step A: the B2 bitmap, 1
+//              bit a point.
 //   k_query    one thread per query: the 3 x 3 x 3 block of the bitmap around
 //              it (every point within squared distance 3, and no other).
 //   k_query_mid one warp per query the first left: the bitmap rows within
@@ -106,76 +106,103 @@ __device__ __forceinline__ uint32_t sword(const RouteArgs& a, int64_t prow, int 
     return ok && k >= 0 && k < a.wpr ? __ldg(a.spk + prow * a.wpr + k) : 0u;
 }
 
-// GetBoundary(S) (Algorithm 3) for the 16 points of packed S word k of row
-// (z, y): the low bit of each B2 point's field. Every lane of the warp takes
-// part (the x neighbours come from the adjacent lanes).
-template <int RANK>
-__device__ __forceinline__ uint32_t b2_word(const RouteArgs& a, int64_t row, int z, int y, int k, bool in)
+// Packed word k of map m, row `prow` (0 past the row, or where ok is false).
+__device__ __forceinline__ uint32_t mword(const uint32_t* m, int64_t prow, int k, int wpr, bool ok)
 {
-    const int lane = threadIdx.x & 31;
-    const uint32_t w = sword(a, row, k, in);
-    uint32_t wl = __shfl_up_sync(kFull, w, 1), wr = __shfl_down_sync(kFull, w, 1);
-    if (lane == 0) wl = sword(a, row, k - 1, true);
-    if (lane == 31) wr = sword(a, row, k + 1, true);
-    const bool row_inner = y >= 1 && y <= a.ny - 2 && (RANK == 2 || (z >= 1 && z <= a.nz - 2));
-    if (!row_inner || !in) return 0u;
-    // interior along x: fields 16k + i in [1, nx - 2]
-    const int x0 = 16 * k;
-    uint32_t inner = 0xFFFFFFFFu;
-    if (x0 == 0) inner &= ~3u;
-    const int last = a.nx - 2 - x0;  // last inner field
-    if (last < 15) inner &= last < 0 ? 0u : (1u << (2 * (last + 1))) - 1u;
-    // differing neighbours per direction (mask bit order z-, z+, y-, y+, x-, x+)
-    uint32_t d[6];
-    d[4] = field_lsb(__funnelshift_l(wl, w, 2) ^ w);
-    d[5] = field_lsb(__funnelshift_r(w, wr, 2) ^ w);
-    d[2] = field_lsb(sword(a, row - 1, k, true) ^ w);
-    d[3] = field_lsb(sword(a, row + 1, k, true) ^ w);
-    if (RANK == 3) {
-        d[0] = field_lsb(sword(a, row - a.ny, k, true) ^ w);
-        d[1] = field_lsb(sword(a, row + a.ny, k, true) ^ w);
-    } else {
-        d[0] = d[1] = 0u;
-    }
-    const uint32_t cand = (d[0] | d[1] | d[2] | d[3] | d[4] | d[5]) & inner;
-    if (a.m.b2_rule == 1 || cand == 0u) return cand;
-    // the default rule: the differing neighbour must have the same q
-    const int64_t plane = (int64_t)a.ny * a.nx;
-    const int64_t st[6] = {-plane, plane, -(int64_t)a.nx, (int64_t)a.nx, -1, 1};
-    uint32_t b2 = 0;
-    for (uint32_t m = cand; m; m &= m - 1) {
-        const int f = __ffs(m) - 1;
-        const int64_t p = row * a.nx + x0 + (f >> 1);
-        const int qb = __ldg(a.q + p);
-        bool hit = false;
-#pragma unroll
-        for (int j = 0; j < 6; ++j)
-            if ((d[j] >> f) & 1u) hit = hit || __ldg(a.q + p + st[j]) == qb;
-        b2 |= hit ? 1u << f : 0u;
-    }
-    return b2;
+    return ok && k >= 0 && k < wpr ? __ldg(m + prow * wpr + k) : 0u;
 }
 
-// The B2 bitmap: one warp per row, one packed S word (16 points) per lane;
-// pairs of lanes make one bitmap word. Every word is written (the bitmap is
-// not cleared between calls). Nothing to do without queries.
+// Rows of a plane a warp takes at once in the B2 map.
+constexpr int kMapRows = 4;
+
+// The B2 bitmap: GetBoundary(S) (Algorithm 3) at every interior point, 16
+// points (one packed S word) per lane, bit-parallel: a point is on B2 when an
+// axis neighbour has a different S and (the default rule) the same q, which
+// the differ maps of step A give (the -x, -y, -z pairs through the
+// neighbour's +x, +y, +z bit). A warp takes kMapRows rows of a plane with all
+// their words loaded up front; pairs of lanes make one bitmap word. Every
+// word is written (the bitmap is not cleared between calls). Nothing to do
+// without queries.
 template <int RANK>
-__global__ void __launch_bounds__(256) k_b2map(RouteArgs a)
+__global__ void __launch_bounds__(256, 3) k_b2map(RouteArgs a)
 {
     wait_prior_grid();
     const volatile int* ctr = a.ctr;
     if (ctr[kCtrDense] || ctr[kCtrQueries] == 0 || ctr[kCtrQueries] > a.qcap) return;
     const int lane = threadIdx.x & 31;
-    const int rows = a.nz * a.ny;
+    const int wpr = a.wpr;
+    const bool literal = a.m.b2_rule == 1;
+    const int yb = (a.ny + kMapRows - 1) / kMapRows;
+    const int items = a.nz * yb;
     const int wstride = gridDim.x * (blockDim.x >> 5);
-    for (int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += wstride) {
-        const int z = RANK == 3 ? row / a.ny : 0;
-        const int y = row - z * a.ny;
-        for (int ks = 0; ks < a.wpr; ks += 32) {
+    constexpr uint32_t kLo = 0x55555555u;
+    for (int it = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < items; it += wstride) {
+        const int z = RANK == 3 ? it / yb : 0;
+        const int y0 = (it - z * yb) * kMapRows;
+        const int64_t row0 = (int64_t)z * a.ny + y0;
+        for (int ks = 0; ks < wpr; ks += 32) {
             const int k = ks + lane;
-            const uint32_t m16 = even_bits(b2_word<RANK>(a, row, z, y, k, k < a.wpr));
-            const uint32_t hi = __shfl_down_sync(kFull, m16, 1);
-            if (!(lane & 1) && k < a.wpr) a.b2bits[(int64_t)row * a.bwpr + (k >> 1)] = m16 | (hi << 16);
+            // S of rows y0 - 1 .. y0 + kMapRows and of planes z -+ 1; the
+            // differ words of rows y0 - 1 .. y0 + kMapRows - 1 and of plane
+            // z - 1
+            uint32_t sy[kMapRows + 2], szm[kMapRows], szp[kMapRows], ey[kMapRows + 1], ez[kMapRows], ezm[kMapRows];
+#pragma unroll
+            for (int i = 0; i < kMapRows + 2; ++i) {
+                const int y = y0 - 1 + i;
+                sy[i] = mword(a.spk, row0 - 1 + i, k, wpr, y >= 0 && y < a.ny);
+                if (i <= kMapRows && !literal) ey[i] = mword(a.nexy, row0 - 1 + i, k, wpr, y >= 0 && y < a.ny);
+            }
+#pragma unroll
+            for (int i = 0; i < kMapRows; ++i) {
+                const bool ok = RANK == 3 && y0 + i < a.ny;
+                szm[i] = mword(a.spk, row0 + i - a.ny, k, wpr, ok && z > 0);
+                szp[i] = mword(a.spk, row0 + i + a.ny, k, wpr, ok && z < a.nz - 1);
+                if (!literal) {
+                    ez[i] = mword(a.nez, row0 + i, k, wpr, ok);
+                    ezm[i] = mword(a.nez, row0 + i - a.ny, k, wpr, ok && z > 0);
+                }
+            }
+            // interior along x: fields 16k + i in [1, nx - 2]
+            uint32_t inner = k < wpr ? 0xFFFFFFFFu : 0u;
+            if (k == 0) inner &= ~3u;
+            const int last = a.nx - 2 - 16 * k;  // last inner field
+            if (last < 15) inner &= last < 0 ? 0u : (1u << (2 * (last + 1))) - 1u;
+#pragma unroll
+            for (int i = 0; i < kMapRows; ++i) {
+                const int y = y0 + i;
+                if (y >= a.ny) break;  // warp-uniform
+                const uint32_t w = sy[i + 1];
+                uint32_t wl = __shfl_up_sync(kFull, w, 1), wr = __shfl_down_sync(kFull, w, 1);
+                if (lane == 0) wl = mword(a.spk, row0 + i, k - 1, wpr, true);
+                if (lane == 31) wr = mword(a.spk, row0 + i, k + 1, wpr, true);
+                uint32_t exl = 0;
+                if (!literal) {
+                    exl = __shfl_up_sync(kFull, ey[i + 1], 1);
+                    if (lane == 0) exl = mword(a.nexy, row0 + i, k - 1, wpr, true);
+                }
+                const bool row_inner = y >= 1 && y <= a.ny - 2 && (RANK == 2 || (z >= 1 && z <= a.nz - 2));
+                // differing neighbours, per direction
+                const uint32_t dxm = field_lsb(__funnelshift_l(wl, w, 2) ^ w);
+                const uint32_t dxp = field_lsb(__funnelshift_r(w, wr, 2) ^ w);
+                const uint32_t dym = field_lsb(sy[i] ^ w), dyp = field_lsb(sy[i + 2] ^ w);
+                const uint32_t dzm = RANK == 3 ? field_lsb(szm[i] ^ w) : 0u;
+                const uint32_t dzp = RANK == 3 ? field_lsb(szp[i] ^ w) : 0u;
+                uint32_t b2;
+                if (literal) {
+                    b2 = dxm | dxp | dym | dyp | dzm | dzp;
+                } else {
+                    // a pair counts where its differ bit is clear (the same q)
+                    const uint32_t nxy = ey[i + 1];
+                    b2 = (dxp & ~nxy) | (dxm & ~__funnelshift_l(exl, nxy, 2)) | (dyp & ~(nxy >> 1)) |
+                         (dym & ~(ey[i] >> 1));
+                    if (RANK == 3) b2 |= (dzp & ~ez[i]) | (dzm & ~ezm[i]);
+                    b2 &= kLo;
+                }
+                b2 = row_inner ? b2 & inner : 0u;
+                const uint32_t m16 = even_bits(b2);
+                const uint32_t hi = __shfl_down_sync(kFull, m16, 1);
+                if (!(lane & 1) && k < wpr) a.b2bits[(row0 + i) * a.bwpr + (k >> 1)] = m16 | (hi << 16);
+            }
         }
     }
 }

@@ -14,17 +14,18 @@ namespace {
 // Workspace of the largest accepted field: at most 12 bytes per point for
 // the byte maps (the rank-3 layout: equal-q mask 1, Dist1 4, S 1, xwords 2,
 // ywords 4), a uint16 count per column of the last column pass (at most one
-// byte per point, since that pass has at least two rows), the packed step-A
-// codes and S (2 bits a point each) and the B2 bitmap (1 bit), each rounded
-// up to whole words per row, the lists of the signed-point route (two of
-// N / 128 + 1024 queries of 8 bytes, N / 256 + 1024 signed boundary points of
-// 4 bytes, at most 65536 leftover queries at 12 bytes, N / 32 + 4096 B2 sites
-// of 8 bytes) and the 256-byte alignment of its slices: at most 13.7 N +
-// 0.9 MiB for every shape of at most N points with an x extent of 16 or
-// more, inside 14 N + 1 MiB. Narrower x extents round more of each row up and
-// can need more; such shapes are rejected when they do.
+// byte per point, since that pass has at least two rows), four packed maps of
+// 2 bits a point (step-A codes, two equal-neighbour maps, S) and the B2
+// bitmap (1 bit), each rounded up to whole words per row, the lists of the
+// signed-point route (two of N / 128 + 1024 queries of 8 bytes, N / 256 +
+// 1024 signed boundary points of 4 bytes, at most 65536 leftover queries at
+// 12 bytes, N / 32 + 4096 B2 sites of 8 bytes) and the 256-byte alignment of
+// its slices: at most 14.3 N + 0.9 MiB for every shape of at most N points
+// with an x extent of 16 or more, inside 15 N + 1 MiB. Narrower x extents
+// round more of each row up and can need more; such shapes are rejected when
+// they do.
 constexpr int64_t kMaxPoints = QAI_STATIC_MAX_POINTS;
-constexpr size_t kScratchBytes = (size_t)14 * (size_t)kMaxPoints + ((size_t)1 << 20);
+constexpr size_t kScratchBytes = (size_t)15 * (size_t)kMaxPoints + ((size_t)1 << 20);
 
 __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
