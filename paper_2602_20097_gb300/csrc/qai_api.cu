@@ -310,6 +310,7 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
         la.nez = sh.rank == 3 ? reinterpret_cast<uint32_t*>(ws + lay.nez) : nullptr;
         la.spk = reinterpret_cast<uint32_t*>(ws + lay.spk);
         la.qlist = reinterpret_cast<qai::Query*>(ws + lay.qlist); la.qcap = lay.qcap;
+        la.slist = reinterpret_cast<int32_t*>(ws + lay.slist); la.scap = lay.scap;
         la.eqm = eqm; la.s = s;
         la.m = m;
         auto al = [](const void* p, int b) { return (reinterpret_cast<uintptr_t>(p) % b) == 0; };
@@ -320,6 +321,7 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
         // maps of the route (B1 with S_B, equal neighbours)
         e = timed("detect", N * (sh.rank == 3 ? 8.75 : 8.5), st, [&] { return qai::launch_local_detect(la, st); });
         if (e != cudaSuccess) return cuda_fail(e, "step A");
+        if (m.sign_rule == 0) count_launch();  // the exact pass behind the fast one
     }
     if (local) {
         // Steps B and C by the bounded nearest-site search; the separable
@@ -408,6 +410,7 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
         ra.rank = sh.rank; ra.nz = sh.nz; ra.ny = sh.ny; ra.nx = sh.nx;
         ra.wpr = lay.wpr; ra.bwpr = lay.bwpr;
         ra.q = d_q; ra.spk = la.spk; ra.nexy = la.nexy; ra.nez = la.nez; ra.out = d_out; ra.ctr = ctr;
+        ra.slist = reinterpret_cast<const int32_t*>(ws + lay.slist); ra.scap = lay.scap;
         ra.b2bits = reinterpret_cast<uint32_t*>(ws + lay.b2bits);
         ra.qlist = qlist; ra.qcap = lay.qcap;
         ra.mlist = reinterpret_cast<qai::Query*>(ws + lay.mlist);
@@ -419,6 +422,12 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
         ra.brute_budget = 1LL << 28;
         ra.m = m;
         if (route == Route::Dense) ra.qcap = -1;  // every count is over it: hand over at once
+        // the sparse route: B2 sites from the signed set, every query against them
+        e = timed("b2sparse", 0.0, st, [&] { return qai::launch_route_sparse_sites(ra, st); });
+        if (e != cudaSuccess) return cuda_fail(e, "B2 sites of the signed set");
+        e = timed("brute_sparse", 0.0, st, [&] { return qai::launch_route_brute(ra, 2 * sms, true, st); });
+        if (e != cudaSuccess) return cuda_fail(e, "search over the B2 sites");
+        // the bitmap route, when the sparse one could not run
         e = timed("b2map", N * (sh.rank == 3 ? 1.125 : 0.875), st, [&] { return qai::launch_route_b2map(ra, st); });
         if (e != cudaSuccess) return cuda_fail(e, "B2 bitmap");
         e = timed("signed_query", 0.0, st, [&] { return qai::launch_route_query(ra, 4 * sms, st); });
@@ -427,7 +436,7 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
         if (e != cudaSuccess) return cuda_fail(e, "signed-point shell search, second phase");
         e = timed("b2list", 0.0, st, [&] { return qai::launch_route_b2list(ra, st); });
         if (e != cudaSuccess) return cuda_fail(e, "B2 site list");
-        e = timed("signed_brute", 0.0, st, [&] { return qai::launch_route_brute(ra, 2 * sms, st); });
+        e = timed("signed_brute", 0.0, st, [&] { return qai::launch_route_brute(ra, 2 * sms, false, st); });
         if (e != cudaSuccess) return cuda_fail(e, "brute-force search");
         // the byte maps of the separable passes: for the dense second EDT
         // when it takes over, and always for the adjoint's forward

@@ -60,9 +60,10 @@ enum RouteCtr : int {
     kCtrB2 = 2,        // B2 sites listed for that search
     kCtrDense = 3,     // != 0: the dense second EDT must run
     kCtrSigned = 4,    // B1 points with S != 0
-    kCtrSignedOver = 5,// != 0: a tile of the separable pass had more of them than it could buffer
+    kCtrSignedOver = 5,// != 0: the list of them is incomplete (a CTA had more than it could buffer)
     kCtrBruteDone = 6, // CTAs of the brute-force search that finished
     kCtrMid = 8,       // queries the first (per-thread) shell search left
+    kCtrBitmap = 9,    // != 0: the bitmap route runs (the sparse route could not)
     kCtrWide = 12,     // != 0: an index outside the fast path's range: the exact step A ran
     kCtrSignedExact = 13, // B1 points with S != 0, counted by the exact step A
     kCtrTimeout = 14,  // != 0: a bounded device-side wait ran out (the call's output is not valid)
@@ -165,6 +166,8 @@ struct RouteArgs {
     int* ctr;                // RouteCtr words
     const Query* qlist;
     int qcap;
+    const int32_t* slist;    // B1 points with S != 0 (the rest of the signed set), at most scap
+    int scap;
     Query* mlist;            // queries left by the first shell search (qcap entries)
     Query* flist;            // queries left to the brute-force search
     int32_t* fmin;           // their Dist2, min-reduced by the brute-force CTAs
@@ -205,6 +208,8 @@ struct LocalArgs {
     int* ctr;                // RouteCtr words
     Query* qlist;
     int qcap;
+    int32_t* slist;          // B1 points with S != 0 (linear indices), at most scap
+    int scap;
     int vec;                 // 128-bit loads of q usable
     // the byte maps of the separable passes, for the fallbacks: eqm (equal-q
     // mask, bits 0-5, and the sign code of S_B, bits 6-7; 0x3F off the

@@ -66,7 +66,8 @@ cudaError_t launch_route_b2map(const RouteArgs& a, cudaStream_t st);
 cudaError_t launch_route_query(const RouteArgs& a, int blocks, cudaStream_t st);
 cudaError_t launch_route_query_mid(const RouteArgs& a, int blocks, cudaStream_t st);
 cudaError_t launch_route_b2list(const RouteArgs& a, cudaStream_t st);
-cudaError_t launch_route_brute(const RouteArgs& a, int blocks, cudaStream_t st);
+cudaError_t launch_route_brute(const RouteArgs& a, int blocks, bool sparse, cudaStream_t st);
+cudaError_t launch_route_sparse_sites(const RouteArgs& a, cudaStream_t st);
 
 // The local first EDT (qai_local.cu): step A with the pre-written output and
 // the packed codes, then S (packed), Dist1 and the queries by a bounded

@@ -258,9 +258,18 @@ __device__ __forceinline__ void step_a_exact(const MethodArgs& m, bool row_inner
 // wherever Dist2 does not matter (D' + S_B eta eps on B1, D' elsewhere: the
 // expressions of compensate(), with C = +0 the fma is the product), the code
 // byte and the differ bytes (up to the row's last packed word).
+// The B1 points with S != 0 of a CTA, collected in shared memory and
+// appended to the signed list with one atomic when the CTA ends.
+constexpr int kSignedCta = 1024, kSignedTma = 512;
+struct SignedBuf {
+    int32_t* e;
+    int* n;
+    int cap;
+};
+
 template <int RANK, bool VEC>
 __device__ __forceinline__ void store_step_a(const LocalArgs& a, int row, int x0, const Quad& Q, unsigned code,
-                                             unsigned sg, unsigned ne, unsigned nz, unsigned& nsigned)
+                                             unsigned sg, unsigned ne, unsigned nz, const SignedBuf& sb)
 {
     const int nx = a.nx;
     float* orow = a.out + (int64_t)row * nx;
@@ -271,8 +280,11 @@ __device__ __forceinline__ void store_step_a(const LocalArgs& a, int row, int x0
             const unsigned cd = (sg >> (2 * j)) & 3u;
             const float cc = (cd == 1u ? 1.0f : (cd == 2u ? -1.0f : 0.0f)) * a.m.eta_eb;
             o[j] = a.m.output_c ? cc : fmaf((float)Q.c[j], a.m.two_eb, cc);
+            if (cd) {
+                const int k = atomicAdd(sb.n, 1);
+                if (k < sb.cap) sb.e[k] = row * nx + x0 + j;
+            }
         }
-        nsigned += __popc(field_lsb(sg));
     } else {
 #pragma unroll
         for (int j = 0; j < 4; ++j) o[j] = a.m.output_c ? 0.0f : (float)Q.c[j] * a.m.two_eb;
@@ -322,15 +334,35 @@ __device__ __forceinline__ void load_quad(const LocalArgs& a, int row, int z, in
 // rows that are not 16-byte multiples and for the exact pass). mode 0: the
 // fast path, flagging a field with an index outside its range; 1: the exact
 // form; 2: the exact form, only when the flag is set.
+// The CTA's signed points to the list (one atomic); a CTA with more than its
+// buffer holds marks the list incomplete.
+__device__ __forceinline__ void flush_signed(const LocalArgs& a, const SignedBuf& sb, int* base)
+{
+    __syncthreads();
+    const int n = *sb.n;
+    if (threadIdx.x == 0) {
+        *base = -1;
+        if (n > sb.cap) *static_cast<volatile int*>(a.ctr + kCtrSignedOver) = 1;
+        else if (n > 0) *base = atomicAdd(a.ctr + kCtrSigned, n);
+    }
+    __syncthreads();
+    if (*base >= 0)
+        for (int i = threadIdx.x; i < n && *base + i < a.scap; i += blockDim.x) a.slist[*base + i] = sb.e[i];
+}
+
 template <int RANK, bool VEC>
 __global__ void __launch_bounds__(256, QAI_DETECT_MINB) k_detect(LocalArgs a, int mode)
 {
+    __shared__ int32_t sbuf[kSignedCta];
+    __shared__ int sn, sbase;
     wait_prior_grid();
     if (mode == 2 && *static_cast<const volatile int*>(a.ctr + kCtrWide) == 0) return;
+    if (threadIdx.x == 0) sn = 0;
+    __syncthreads();
+    const SignedBuf sb{sbuf, &sn, kSignedCta};
     const int rows = a.nz * a.ny;
     const int wstride = gridDim.x * (blockDim.x >> 5);
     const int lx = 4 * (int)(threadIdx.x & 31);
-    unsigned nsigned = 0;
     bool wide = false;
     for (int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += wstride) {
         const int z = RANK == 3 ? row / a.ny : 0;
@@ -347,13 +379,21 @@ __global__ void __launch_bounds__(256, QAI_DETECT_MINB) k_detect(LocalArgs a, in
                 uint32_t em;
                 step_a_exact<RANK>(a.m, row_inner, x0, a.nx, Q, code, sg, ne, nz, em);
             }
-            store_step_a<RANK, VEC>(a, row, x0, Q, code, sg, ne, nz, nsigned);
+            store_step_a<RANK, VEC>(a, row, x0, Q, code, sg, ne, nz, sb);
         }
     }
-    // B1 points with S != 0: one atomic per warp that has any
-    nsigned = __reduce_add_sync(kFull, nsigned);
-    if ((threadIdx.x & 31) == 0 && nsigned) atomicAdd(a.ctr + (mode == 2 ? kCtrSignedExact : kCtrSigned), (int)nsigned);
     if (__any_sync(kFull, wide) && (threadIdx.x & 31) == 0) *static_cast<volatile int*>(a.ctr + kCtrWide) = 1;
+    if (mode != 2) {
+        flush_signed(a, sb, &sbase);
+    } else {
+        // the exact pass: the fast pass's list may be wrong; the count stands
+        // apart and the list is marked incomplete
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (sn) atomicAdd(a.ctr + kCtrSignedExact, sn);
+            if (blockIdx.x == 0) *static_cast<volatile int*>(a.ctr + kCtrSignedOver) = 1;
+        }
+    }
 }
 
 // ---- step A for 3-D fields on tiles staged by the tensor memory accelerator
@@ -409,19 +449,22 @@ __device__ __forceinline__ bool wait_plane(uint64_t* bar, uint32_t parity)
 __global__ void __launch_bounds__(256, 3) k_detect_tma(LocalArgs a, const __grid_constant__ CUtensorMap tm,
                                                       int tiles_x, int64_t steps)
 {
-    extern __shared__ __align__(1024) int sbuf[];  // the plane ring, then the slots' barriers
+    extern __shared__ __align__(128) int sbuf[];  // the plane ring, then the slots' barriers
     uint64_t* bars = reinterpret_cast<uint64_t*>(sbuf + kSlots * kSlotInts);
+    __shared__ int32_t signed_buf[kSignedTma];
+    __shared__ int sn, sbase;
+    const SignedBuf sb{signed_buf, &sn, kSignedTma};
     wait_prior_grid();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kSlots; ++s)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[s])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        sn = 0;
     }
     __syncthreads();
     uint32_t parity = 0;  // bit s: the phase parity slot s completes next
     bool timed_out = false, wide = false;
-    unsigned nsigned = 0;
     const int nz = a.nz;
     const int64_t s0 = steps * blockIdx.x / gridDim.x, s1 = steps * (blockIdx.x + 1) / gridDim.x;
     auto slot_of = [](int z) { return ((z % kSlots) + kSlots) % kSlots; };
@@ -468,7 +511,7 @@ __global__ void __launch_bounds__(256, 3) k_detect_tma(LocalArgs a, const __grid
                 unsigned code, sg, ne, nzb;
                 wide |= !quad_narrow(Q);
                 step_a_fast<3>(a.m, row_inner, x0, a.nx, Q, code, sg, ne, nzb);
-                store_step_a<3, true>(a, row, x0, Q, code, sg, ne, nzb, nsigned);
+                store_step_a<3, true>(a, row, x0, Q, code, sg, ne, nzb, sb);
             }
             __syncthreads();  // every read of plane z - 1 done: its slot takes z + 3
             if (threadIdx.x == 0 && z + 3 <= z1) {
@@ -478,10 +521,9 @@ __global__ void __launch_bounds__(256, 3) k_detect_tma(LocalArgs a, const __grid
         }
         s += z1 - z0;
     }
-    nsigned = __reduce_add_sync(kFull, nsigned);
-    if (lane == 0 && nsigned) atomicAdd(a.ctr + kCtrSigned, (int)nsigned);
     if (timed_out && lane == 0) *static_cast<volatile int*>(a.ctr + kCtrTimeout) = 1;
     if (__any_sync(kFull, wide) && lane == 0) *static_cast<volatile int*>(a.ctr + kCtrWide) = 1;
+    flush_signed(a, sb, &sbase);
 }
 
 // Word k of packed row `prow` (0 past the row, or where ok is false).
@@ -603,12 +645,22 @@ __global__ void __launch_bounds__(256, QAI_NEAR_MINB) k_near(LocalArgs a)
                     };
                     const uint32_t wxm = pshift(cm, row, k, wpr, true, w, -1);
                     const uint32_t wxp = pshift(cm, row, k, wpr, true, w, 1);
-                    if (RANK == 3) take(wzm[i]);
-                    take(wy[i]);
-                    take(wxm);
-                    take(wxp);
-                    take(wy[i + 2]);
-                    if (RANK == 3) take(wzp[i]);
+                    const uint32_t all6 = (RANK == 3 ? wzm[i] | wzp[i] : 0u) | wy[i] | wy[i + 2] | wxm | wxp;
+                    if (__any_sync(kFull, (need & (all6 >> 1)) != 0)) {
+                        if (RANK == 3) take(wzm[i]);
+                        take(wy[i]);
+                        take(wxm);
+                        take(wxp);
+                        take(wy[i + 2]);
+                        if (RANK == 3) take(wzp[i]);
+                    } else {
+                        // no point off B1 has a signed neighbour at squared
+                        // distance 1 (a code >= 2): whichever of them comes
+                        // first carries S_B = 0 (code 1)
+                        const uint32_t t = field_lsb(all6) & need;
+                        res = t;
+                        need &= ~t;
+                    }
                     const uint32_t at1 = need0 & ~need;  // resolved at squared distance 1
                     // squared distances 2..8: the words with a point left, one
                     // at a time, searched by the warp

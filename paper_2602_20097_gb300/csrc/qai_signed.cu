@@ -9,6 +9,11 @@
 // give the exact Dist2 of every query, Eq. 2 over the sign-flipping boundary
 // B2 of Algorithm 3:
 //
+// Two routes. The sparse one, where the signed points (S != 0) are few enough
+// to be listed: k_b2sparse lists the B2 sites from the signed set and
+// k_brute (sparse) gives every query the minimum over them. The bitmap route,
+// where they are not or the product of queries and sites is over its budget:
+//
 //   k_b2map    GetBoundary(S) at every interior point, bit-parallel from the
 //              packed S map and the differ maps of step A: the B2 bitmap, 1
 //              bit a point.
@@ -128,7 +133,7 @@ __global__ void __launch_bounds__(256, 3) k_b2map(RouteArgs a)
 {
     wait_prior_grid();
     const volatile int* ctr = a.ctr;
-    if (ctr[kCtrDense] || ctr[kCtrQueries] == 0 || ctr[kCtrQueries] > a.qcap) return;
+    if (ctr[kCtrDense] || !ctr[kCtrBitmap]) return;
     const int lane = threadIdx.x & 31;
     const int wpr = a.wpr;
     const bool literal = a.m.b2_rule == 1;
@@ -146,18 +151,36 @@ __global__ void __launch_bounds__(256, 3) k_b2map(RouteArgs a)
             // differ words of rows y0 - 1 .. y0 + kMapRows - 1 and of plane
             // z - 1
             uint32_t sy[kMapRows + 2], szm[kMapRows], szp[kMapRows], ey[kMapRows + 1], ez[kMapRows], ezm[kMapRows];
+            uint32_t any = 0;
 #pragma unroll
             for (int i = 0; i < kMapRows + 2; ++i) {
                 const int y = y0 - 1 + i;
                 sy[i] = mword(a.spk, row0 - 1 + i, k, wpr, y >= 0 && y < a.ny);
-                if (i <= kMapRows && !literal) ey[i] = mword(a.nexy, row0 - 1 + i, k, wpr, y >= 0 && y < a.ny);
+                any |= sy[i];
             }
 #pragma unroll
             for (int i = 0; i < kMapRows; ++i) {
                 const bool ok = RANK == 3 && y0 + i < a.ny;
                 szm[i] = mword(a.spk, row0 + i - a.ny, k, wpr, ok && z > 0);
                 szp[i] = mword(a.spk, row0 + i + a.ny, k, wpr, ok && z < a.nz - 1);
-                if (!literal) {
+                any |= szm[i] | szp[i];
+            }
+            if (!__any_sync(kFull, any != 0)) {
+                // S = 0 around every point of these rows: no B2 point
+#pragma unroll
+                for (int i = 0; i < kMapRows; ++i)
+                    if (y0 + i < a.ny && !(lane & 1) && k < wpr) a.b2bits[(row0 + i) * a.bwpr + (k >> 1)] = 0u;
+                continue;
+            }
+            if (!literal) {
+#pragma unroll
+                for (int i = 0; i <= kMapRows; ++i) {
+                    const int y = y0 - 1 + i;
+                    ey[i] = mword(a.nexy, row0 - 1 + i, k, wpr, y >= 0 && y < a.ny);
+                }
+#pragma unroll
+                for (int i = 0; i < kMapRows; ++i) {
+                    const bool ok = RANK == 3 && y0 + i < a.ny;
                     ez[i] = mword(a.nez, row0 + i, k, wpr, ok);
                     ezm[i] = mword(a.nez, row0 + i - a.ny, k, wpr, ok && z > 0);
                 }
@@ -243,12 +266,8 @@ __global__ void __launch_bounds__(256) k_query(RouteArgs a)
 {
     wait_prior_grid();
     volatile int* ctr = a.ctr;
-    if (ctr[kCtrDense]) return;
+    if (ctr[kCtrDense] || !ctr[kCtrBitmap]) return;
     const int nq = ctr[kCtrQueries];
-    if (nq > a.qcap) {  // the list is incomplete: the dense route takes over
-        if (blockIdx.x == 0 && threadIdx.x == 0) ctr[kCtrDense] = 1;
-        return;
-    }
     __shared__ Query mbuf[kMidBuf];
     __shared__ int mn, mbase;
     if (threadIdx.x == 0) mn = 0;
@@ -297,7 +316,7 @@ __global__ void __launch_bounds__(256) k_query_mid(RouteArgs a)
 {
     wait_prior_grid();
     volatile int* ctr = a.ctr;
-    if (ctr[kCtrDense]) return;
+    if (ctr[kCtrDense] || !ctr[kCtrBitmap]) return;
     const int nm = min((int)ctr[kCtrMid], a.qcap);
     const int lane = threadIdx.x & 31;
     const int wstride = gridDim.x * (blockDim.x >> 5);
@@ -342,7 +361,7 @@ __global__ void __launch_bounds__(256) k_b2list(RouteArgs a)
 {
     wait_prior_grid();
     volatile int* ctr = a.ctr;
-    if (ctr[kCtrDense] || ctr[kCtrUnresolved] == 0) return;
+    if (ctr[kCtrDense] || !ctr[kCtrBitmap] || ctr[kCtrUnresolved] == 0) return;
     __shared__ uint2 sbuf[kSiteBuf];
     __shared__ int sn, sfull, sbase;  // sfull: first reservation that did not fit
     if (threadIdx.x == 0) {
@@ -393,23 +412,193 @@ __global__ void __launch_bounds__(256) k_b2list(RouteArgs a)
     for (int i = threadIdx.x; i < n && sbase + i < a.b2cap; i += blockDim.x) glist[sbase + i] = sbuf[i];
 }
 
-// Exact Dist2 of each query left by the shell phases: min over the listed B2
-// sites. CTA i takes 256 queries (block i % qb) against one slice of the site
-// list (i / qb), staged through shared memory; each thread folds its minimum
-// into fmin with an atomic, and the last CTA to finish writes the outputs.
-constexpr int kBruteChunk = 1024;
-__global__ void __launch_bounds__(256) k_brute(RouteArgs a)
+// S code (0, 1: +1, 2: -1) of point (x, y, z) from the packed S map; 0
+// outside the field.
+__device__ __forceinline__ int s_at(const RouteArgs& a, int x, int y, int z)
+{
+    if ((unsigned)x >= (unsigned)a.nx || (unsigned)y >= (unsigned)a.ny || (unsigned)z >= (unsigned)a.nz) return 0;
+    const uint32_t w = __ldg(a.spk + ((int64_t)z * a.ny + y) * a.wpr + (x >> 4));
+    return (int)((w >> (2 * (x & 15))) & 3u);
+}
+
+// Whether q differs across the pair (x, y, z) -- (x, y, z) + e, e the unit
+// step along axis 0 (z), 1 (y) or 2 (x): the differ bit of the pair's lower
+// point (both points inside the field).
+__device__ __forceinline__ bool q_differs(const RouteArgs& a, int x, int y, int z, int axis)
+{
+    const int64_t w = ((int64_t)z * a.ny + y) * a.wpr + (x >> 4);
+    const int sh = 2 * (x & 15);
+    if (axis == 0) return (__ldg(a.nez + w) >> sh) & 1u;
+    return (__ldg(a.nexy + w) >> (sh + (axis == 1 ? 1 : 0))) & 1u;
+}
+
+// GetBoundary(S) (Algorithm 3) at the interior point (x, y, z) with S code sc:
+// an axis neighbour with a different S and (the default rule) the same q.
+template <int RANK>
+__device__ __forceinline__ bool is_b2(const RouteArgs& a, int x, int y, int z, int sc)
+{
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const int axis = k >> 1;
+        if (RANK == 2 && axis == 0) continue;
+        const int sg = (k & 1) ? 1 : -1;
+        const int nx_ = x + (axis == 2 ? sg : 0), ny_ = y + (axis == 1 ? sg : 0), nz_ = z + (axis == 0 ? sg : 0);
+        if (s_at(a, nx_, ny_, nz_) == sc) continue;
+        if (a.m.b2_rule == 1) return true;
+        // the pair's lower point carries its differ bit
+        if (!(sg > 0 ? q_differs(a, x, y, z, axis) : q_differs(a, nx_, ny_, nz_, axis))) return true;
+    }
+    return false;
+}
+
+// The B2 sites from the signed set -- the listed B1 points with S != 0 and the
+// queries (S != 0 off B1): GetBoundary(S) compares S across a pair, so every
+// B2 site is a signed point or an axis neighbour of one. One thread per
+// signed point p tests p and its axis neighbours with S = 0; such a
+// neighbour is tested only by its signed neighbour of smallest linear index,
+// so no site is listed twice. The sites go to the site list (warp-aggregated
+// appends into a per-CTA buffer, one global atomic per CTA); fmin of every
+// query starts at INF. A signed list that overflowed hands the field to the
+// bitmap route.
+constexpr int kSparseBuf = 2048;
+template <int RANK>
+__global__ void __launch_bounds__(256) k_b2sparse(RouteArgs a)
 {
     wait_prior_grid();
     volatile int* ctr = a.ctr;
-    if (ctr[kCtrDense] || ctr[kCtrUnresolved] == 0) return;
-    const int nf = ctr[kCtrUnresolved];
-    const int nb = ctr[kCtrB2];
-    const int qblocks = (nf + blockDim.x - 1) / blockDim.x;
-    if (nf > a.fcap || nb > a.b2cap || (long long)nf * nb > a.brute_budget || qblocks > (int)gridDim.x) {
+    if (ctr[kCtrDense]) return;
+    const int nq = ctr[kCtrQueries];
+    if (nq > a.qcap) {  // the query list is incomplete: the dense route takes over
         if (blockIdx.x == 0 && threadIdx.x == 0) ctr[kCtrDense] = 1;
         return;
     }
+    if (nq == 0) return;  // no point needs Dist2
+    const int ns = ctr[kCtrSigned];
+    if (ctr[kCtrSignedOver] || ns > a.scap || !a.shell || nq > a.fcap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) ctr[kCtrBitmap] = 1;
+        return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctr[kCtrUnresolved] = nq;  // every query takes the site search
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += gridDim.x * blockDim.x) a.fmin[i] = kDistInf;
+    __shared__ uint2 sbuf[kSparseBuf];
+    __shared__ int sn, sfull, sbase;
+    if (threadIdx.x == 0) {
+        sn = 0;
+        sfull = kSparseBuf;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int plane = a.ny * a.nx;
+    uint2* glist = reinterpret_cast<uint2*>(a.b2list);
+    const int items = ns + nq;
+    for (int base = blockIdx.x * blockDim.x; base < items; base += gridDim.x * blockDim.x) {
+        const int item = base + threadIdx.x;
+        uint2 found[1 + 2 * RANK];
+        int nfound = 0;
+        if (item < items) {
+            const int p = item < ns ? a.slist[item] : a.qlist[item - ns].idx;
+            const int z = p / plane, rem = p - z * plane;
+            const int y = rem / a.nx, x = rem - y * a.nx;
+            // candidate c: 0 = p, then the axis neighbours z-, z+, y-, y+, x-, x+
+#pragma unroll
+            for (int c = 0; c <= 6; ++c) {
+                int cz = 0, cy = 0, cx = 0;
+                if (c > 0) {
+                    const int axis = (c - 1) >> 1;
+                    if (RANK == 2 && axis == 0) continue;
+                    const int sg = (c - 1) & 1 ? 1 : -1;
+                    (axis == 0 ? cz : (axis == 1 ? cy : cx)) = sg;
+                }
+                const int bx = x + cx, by = y + cy, bz = z + cz;
+                const bool inner = (unsigned)(bx - 1) < (unsigned)(a.nx - 2) &&
+                                   (unsigned)(by - 1) < (unsigned)(a.ny - 2) &&
+                                   (RANK == 2 || (unsigned)(bz - 1) < (unsigned)(a.nz - 2));
+                if (!inner) continue;
+                const int sc = s_at(a, bx, by, bz);
+                if (c > 0) {
+                    if (sc != 0) continue;  // a signed point lists itself
+                    // owned by p when no signed neighbour of the candidate
+                    // precedes p: an offset (from p) precedes 0 in (dz, dy,
+                    // dx) order exactly when its point precedes p
+                    bool own = true;
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) {
+                        const int axis = k >> 1;
+                        if (RANK == 2 && axis == 0) continue;
+                        const int sg = (k & 1) ? 1 : -1;
+                        const int oz = cz + (axis == 0 ? sg : 0), oy = cy + (axis == 1 ? sg : 0),
+                                  ox = cx + (axis == 2 ? sg : 0);
+                        const bool before = oz < 0 || (oz == 0 && (oy < 0 || (oy == 0 && ox < 0)));
+                        if (before && s_at(a, x + ox, y + oy, z + oz) != 0) own = false;
+                    }
+                    if (!own) continue;
+                }
+                if (is_b2<RANK>(a, bx, by, bz, sc))
+                    found[nfound++] = make_uint2((uint32_t)bx | ((uint32_t)by << 16), (uint32_t)bz);
+            }
+        }
+        // warp-aggregated append of the found sites
+        int incl = nfound;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int v = __shfl_up_sync(kFull, incl, d);
+            if (lane >= d) incl += v;
+        }
+        const int total = __shfl_sync(kFull, incl, 31);
+        if (total == 0) continue;
+        int wbase = 0;
+        if (lane == 31) wbase = atomicAdd(&sn, total);
+        wbase = __shfl_sync(kFull, wbase, 31);
+        const bool global = wbase + total > kSparseBuf;
+        if (global && lane == 31) {
+            atomicMin(&sfull, wbase);  // every later reservation fails too (sn only grows)
+            wbase = atomicAdd(a.ctr + kCtrB2, total);
+        }
+        if (global) wbase = __shfl_sync(kFull, wbase, 31);
+        uint2* list = global ? glist : sbuf;
+        const int cap = global ? a.b2cap : kSparseBuf;
+        int pos = wbase + incl - nfound;
+        for (int f = 0; f < nfound; ++f, ++pos)
+            if (pos < cap) list[pos] = found[f];
+    }
+    __syncthreads();
+    const int n = min(sn, sfull);
+    if (threadIdx.x == 0) sbase = n > 0 ? atomicAdd(a.ctr + kCtrB2, n) : 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n && sbase + i < a.b2cap; i += blockDim.x) glist[sbase + i] = sbuf[i];
+}
+
+// Exact Dist2 of queries by a search over every listed B2 site: all queries
+// (sparse: the sparse route) or those the shell phases left (the bitmap
+// route). CTA i takes 256 queries (block i % qb) against one slice of the
+// site list (i / qb), staged through shared memory; each thread folds its
+// minimum into fmin with an atomic, and the last CTA to finish writes the
+// outputs. Over the budget, the sparse route hands over to the bitmap route
+// and the bitmap route to the dense second EDT.
+constexpr int kBruteChunk = 1024;
+__global__ void __launch_bounds__(256) k_brute(RouteArgs a, int sparse)
+{
+    wait_prior_grid();
+    volatile int* ctr = a.ctr;
+    if (ctr[kCtrDense]) return;
+    if (sparse ? (ctr[kCtrBitmap] || ctr[kCtrQueries] == 0) : (!ctr[kCtrBitmap] || ctr[kCtrUnresolved] == 0))
+        return;
+    const int nf = sparse ? ctr[kCtrQueries] : ctr[kCtrUnresolved];
+    const int nb = ctr[kCtrB2];
+    const int qblocks = (nf + blockDim.x - 1) / blockDim.x;
+    if (nf > a.fcap || nb > a.b2cap || (long long)nf * nb > a.brute_budget || qblocks > (int)gridDim.x) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            if (sparse) {  // the bitmap route starts its own counts
+                ctr[kCtrUnresolved] = 0;
+                ctr[kCtrB2] = 0;
+                ctr[kCtrBitmap] = 1;
+            } else {
+                ctr[kCtrDense] = 1;
+            }
+        }
+        return;
+    }
+    const Query* src = sparse ? a.qlist : a.flist;
     __shared__ uint2 sites[kBruteChunk];
     __shared__ int last;
     const uint2* list = reinterpret_cast<const uint2*>(a.b2list);
@@ -423,7 +612,7 @@ __global__ void __launch_bounds__(256) k_brute(RouteArgs a)
         const int f = qblk * blockDim.x + threadIdx.x;
         int x = 0, y = 0, z = 0;
         if (f < nf) {
-            const int idx = a.flist[f].idx;
+            const int idx = src[f].idx;
             z = idx / plane;
             const int rem = idx - z * plane;
             y = rem / a.nx;
@@ -452,7 +641,7 @@ __global__ void __launch_bounds__(256) k_brute(RouteArgs a)
         __threadfence();
         for (int f = threadIdx.x; f < nf; f += blockDim.x) {
             const int32_t d2 = *static_cast<volatile int32_t*>(a.fmin + f);
-            emit_query(a, a.flist[f], d2);
+            emit_query(a, src[f], d2);
         }
     }
 }
@@ -492,9 +681,15 @@ cudaError_t launch_route_b2list(const RouteArgs& a, cudaStream_t st)
     return launch_chained(k_b2list, dim3(resident(k_b2list)), dim3(256), 0, st, a);
 }
 
-cudaError_t launch_route_brute(const RouteArgs& a, int blocks, cudaStream_t st)
+cudaError_t launch_route_brute(const RouteArgs& a, int blocks, bool sparse, cudaStream_t st)
 {
-    return launch_chained(k_brute, dim3(blocks), dim3(256), 0, st, a);
+    return launch_chained(k_brute, dim3(blocks), dim3(256), 0, st, a, sparse ? 1 : 0);
+}
+
+cudaError_t launch_route_sparse_sites(const RouteArgs& a, cudaStream_t st)
+{
+    return a.rank == 3 ? launch_chained(k_b2sparse<3>, dim3(resident(k_b2sparse<3>)), dim3(256), 0, st, a)
+                       : launch_chained(k_b2sparse<2>, dim3(resident(k_b2sparse<2>)), dim3(256), 0, st, a);
 }
 
 }  // namespace qai

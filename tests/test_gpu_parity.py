@@ -168,9 +168,11 @@ def test_profile_and_launch_count():
     torch.cuda.synchronize()
     stats = qai.profile_read()
     qai.profile_enable(False)
-    names = {"detect", "near", "rowpass1", "colpass1_y", "colpass1_z_final", "pack_s", "b2map", "signed_query",
-             "signed_query_mid", "b2list", "signed_brute", "expand", "rowpass2", "colpass2_y", "colpass2_z_final"}
-    assert qai.launch_count() - n0 == len(names)
+    names = {"detect", "near", "rowpass1", "colpass1_y", "colpass1_z_final", "pack_s", "b2sparse", "brute_sparse",
+             "b2map", "signed_query", "signed_query_mid", "b2list", "signed_brute", "expand", "rowpass2",
+             "colpass2_y", "colpass2_z_final"}
+    # one launch each, and step A's exact pass (gated, run behind the fast one)
+    assert qai.launch_count() - n0 == len(names) + 1
     assert set(stats) == names
     assert all(v[0] == 1 and v[1] > 0 for v in stats.values())
 
