@@ -264,6 +264,20 @@ int final_pass_blocks(const Shape& sh)
     return qai::colpass_blocks(c, cfg.W);
 }
 
+// The host-memory pipeline of qai_mitigate_host (see there): step A runs in
+// z-slabs as their planes of q arrive, and each slab of D'' goes back while
+// later slabs arrive.
+constexpr int kMaxSlabs = 8;
+struct HostPipe {
+    const int32_t* h_q;
+    float* h_out;          // host buffer, as the caller passed it
+    float* h_out_dev;      // its device (mapped) address
+    int nslab;
+    int zb[kMaxSlabs + 1]; // slab k: planes zb[k] .. zb[k + 1] - 1
+    cudaStream_t sin, sout;
+    cudaEvent_t ev_in[kMaxSlabs], ev_a[kMaxSlabs], ev_out;
+};
+
 // The launch sequence of Algorithm 4 on a validated shape.
 // d2rec (plain calls with the signed-point route only): Dist2 is recorded
 // there, by point, wherever S != 0 off B1 (the adjoint's forward).
@@ -272,7 +286,8 @@ int final_pass_blocks(const Shape& sh)
 // 0 elsewhere); Dist2 is recorded straight into it.
 qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const qai::MethodArgs& m,
                         char* ws, const Layout& lay, cudaStream_t st, const qai_debug_out* dbg,
-                        GradSink* grad = nullptr, int32_t* d2rec = nullptr, const qai_debug_out* saved = nullptr)
+                        GradSink* grad = nullptr, int32_t* d2rec = nullptr, const qai_debug_out* saved = nullptr,
+                        const HostPipe* hp = nullptr)
 {
     if (saved) d2rec = saved->dist2;
     const double N = (double)sh.N;
@@ -316,7 +331,28 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
         auto al = [](const void* p, int b) { return (reinterpret_cast<uintptr_t>(p) % b) == 0; };
         la.vec = (sh.nx % 4 == 0) && al(d_q, 16) && al(d_out, 16);
     }
-    if (ctr) {
+    if (ctr && hp) {
+        // Step A slab by slab as q arrives (slab k needs its planes and the
+        // first plane of slab k + 1), each slab of D'' back to the host as
+        // soon as it is written; then the exact pass behind the slabs
+        const size_t plane = (size_t)sh.ny * sh.nx;
+        for (int k = 0; k < hp->nslab; ++k) {
+            cudaStreamWaitEvent(st, hp->ev_in[k], 0);
+            if (k + 1 < hp->nslab) cudaStreamWaitEvent(st, hp->ev_in[k + 1], 0);
+            const int zb = hp->zb[k], zn = hp->zb[k + 1] - hp->zb[k];
+            e = timed("detect", (double)zn * plane * 8.75, st,
+                      [&] { return qai::launch_local_detect_slab(la, zb, zn, st); });
+            if (e != cudaSuccess) return cuda_fail(e, "step A (slab)");
+            if ((e = cudaEventRecord(hp->ev_a[k], st)) != cudaSuccess) return cuda_fail(e, "event");
+            if ((e = cudaStreamWaitEvent(hp->sout, hp->ev_a[k], 0)) != cudaSuccess) return cuda_fail(e, "event");
+            e = cudaMemcpyAsync(hp->h_out + (size_t)zb * plane, d_out + (size_t)zb * plane,
+                                (size_t)zn * plane * sizeof(float), cudaMemcpyDeviceToHost, hp->sout);
+            if (e != cudaSuccess) return cuda_fail(e, "copy D'' slab to host");
+        }
+        if ((e = cudaEventRecord(hp->ev_out, hp->sout)) != cudaSuccess) return cuda_fail(e, "event");
+        e = timed("detect", 0.0, st, [&] { return qai::launch_local_detect_exact(la, st); });
+        if (e != cudaSuccess) return cuda_fail(e, "step A (exact pass)");
+    } else if (ctr) {
         // Step A with the output where Dist2 does not matter and the packed
         // maps of the route (B1 with S_B, equal neighbours)
         e = timed("detect", N * (sh.rank == 3 ? 8.75 : 8.5), st, [&] { return qai::launch_local_detect(la, st); });
@@ -506,6 +542,12 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
         });
         if (e != cudaSuccess) return cuda_fail(e, "saved state");
     }
+    if (hp) {
+        // after the last slab's copy: what changed since, into the host buffer
+        if ((e = cudaStreamWaitEvent(st, hp->ev_out, 0)) != cudaSuccess) return cuda_fail(e, "event");
+        e = timed("host_fixup", 0.0, st, [&] { return qai::launch_host_fixup(la, hp->h_out_dev, st); });
+        if (e != cudaSuccess) return cuda_fail(e, "host output fix-up");
+    }
     return QAI_OK;
 }
 
@@ -589,6 +631,87 @@ qai_status mitigate_impl(const int32_t* d_q, float* d_out, int rank, const int64
 }
 }  // namespace
 
+namespace {
+// Internal streams and events of the host-memory pipeline, per device; one
+// call enqueues at a time.
+struct PipeRes {
+    bool ready = false;
+    cudaStream_t sin = nullptr, sout = nullptr;
+    cudaEvent_t fork = nullptr, ev_in[kMaxSlabs] = {}, ev_a[kMaxSlabs] = {}, ev_out = nullptr;
+};
+std::mutex g_pipe_mu;
+PipeRes g_pipe[64];
+
+// The pipelined form needs the tiled step A (3-D rows of 16-byte multiples,
+// aligned device buffers, the sign rule SUM), the route of plain calls, at
+// least two slabs of planes, page-locked q and a page-locked, device-mapped
+// output buffer.
+bool host_pipeline_fits(const Shape& sh, const qai_params& p, const int32_t* h_q, const float* h_out,
+                        const int32_t* d_q, const float* d_out)
+{
+    if (sh.rank != 3 || sh.nz < 16 || sh.nx % 4 != 0 || p.sign_rule != 0) return false;
+    if (p.flags & (QAI_FLAG_EDT2_DENSE | QAI_FLAG_EDT1_SEPARABLE)) return false;
+    if ((reinterpret_cast<uintptr_t>(d_q) | reinterpret_cast<uintptr_t>(d_out)) & 15) return false;
+    cudaPointerAttributes aq{}, ao{};
+    if (cudaPointerGetAttributes(&aq, h_q) != cudaSuccess || cudaPointerGetAttributes(&ao, h_out) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return aq.type == cudaMemoryTypeHost && ao.type == cudaMemoryTypeHost && ao.devicePointer != nullptr;
+}
+
+qai_status mitigate_host_pipelined(const int32_t* h_q, float* h_out, const Shape& sh, const qai_params* p, double eb,
+                                   int32_t* d_q, float* d_out, char* ws, size_t ws_bytes, cudaStream_t st)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 64) return cuda_fail(e, "current device");
+    std::lock_guard<std::mutex> lk(g_pipe_mu);
+    PipeRes& r = g_pipe[dev];
+    if (!r.ready) {
+        bool ok = cudaStreamCreateWithFlags(&r.sin, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&r.sout, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&r.fork, cudaEventDisableTiming) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&r.ev_out, cudaEventDisableTiming) == cudaSuccess;
+        for (int k = 0; ok && k < kMaxSlabs; ++k)
+            ok = cudaEventCreateWithFlags(&r.ev_in[k], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&r.ev_a[k], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) return cuda_fail(cudaGetLastError(), "pipeline streams and events");
+        r.ready = true;
+    }
+    cudaPointerAttributes ao{};
+    if ((e = cudaPointerGetAttributes(&ao, h_out)) != cudaSuccess) return cuda_fail(e, "output buffer");
+    HostPipe hp{};
+    hp.h_q = h_q;
+    hp.h_out = h_out;
+    hp.h_out_dev = static_cast<float*>(ao.devicePointer);
+    hp.nslab = std::min(kMaxSlabs, sh.nz / 8);
+    for (int k = 0; k <= hp.nslab; ++k) hp.zb[k] = (int)((int64_t)sh.nz * k / hp.nslab);
+    hp.sin = r.sin;
+    hp.sout = r.sout;
+    for (int k = 0; k < kMaxSlabs; ++k) {
+        hp.ev_in[k] = r.ev_in[k];
+        hp.ev_a[k] = r.ev_a[k];
+    }
+    hp.ev_out = r.ev_out;
+    // both side streams start after the work already on `stream` (the last
+    // call on this workspace may still read q and write D'')
+    if ((e = cudaEventRecord(r.fork, st)) != cudaSuccess) return cuda_fail(e, "event");
+    if ((e = cudaStreamWaitEvent(r.sin, r.fork, 0)) != cudaSuccess) return cuda_fail(e, "event");
+    if ((e = cudaStreamWaitEvent(r.sout, r.fork, 0)) != cudaSuccess) return cuda_fail(e, "event");
+    const size_t plane = (size_t)sh.ny * sh.nx;
+    for (int k = 0; k < hp.nslab; ++k) {
+        const size_t off = (size_t)hp.zb[k] * plane, n = (size_t)(hp.zb[k + 1] - hp.zb[k]) * plane;
+        if ((e = cudaMemcpyAsync(d_q + off, h_q + off, n * 4, cudaMemcpyHostToDevice, r.sin)) != cudaSuccess)
+            return cuda_fail(e, "copy q slab to device");
+        if ((e = cudaEventRecord(r.ev_in[k], r.sin)) != cudaSuccess) return cuda_fail(e, "event");
+    }
+    const Layout lay = layout_for(sh, 0);
+    if (ws_bytes < lay.total) return fail(QAI_ERR_INVALID_ARG, "workspace too small");
+    return run_pipeline(d_q, d_out, sh, method_args(p, eb), ws, lay, st, nullptr, nullptr, nullptr, nullptr, &hp);
+}
+}  // namespace
+
 extern "C" {
 
 qai_status qai_mitigate(const int32_t* d_q, float* d_out, int rank, const int64_t* dims, double eb,
@@ -652,7 +775,20 @@ qai_status qai_mitigate_host(const int32_t* h_q, float* h_out, int rank, const i
     char* base = static_cast<char*>(d_ws);
     int32_t* d_q = reinterpret_cast<int32_t*>(base);
     float* d_out = reinterpret_cast<float*>(base + fb);
-    cudaError_t e = cudaMemcpyAsync(d_q, h_q, (size_t)sh.N * 4, cudaMemcpyHostToDevice, stream);
+    qai_params defaults;
+    qai_default_params(&defaults);
+    const qai_params* p = params ? params : &defaults;
+    if ((s = check_params(p)) != QAI_OK) return s;
+    if (!(eb > 0.0) || !std::isfinite(eb)) return fail(QAI_ERR_INVALID_ARG, "eb must be finite and > 0");
+    cudaError_t e;
+    if (host_pipeline_fits(sh, *p, h_q, h_out, d_q, d_out)) {
+        // the pipelined form: q in slabs on one stream, step A per slab on
+        // `stream` as they land, D'' slabs back on another as soon as step A
+        // wrote them (the link carries both directions at once); the outputs
+        // the later kernels change go straight into the mapped host buffer
+        return mitigate_host_pipelined(h_q, h_out, sh, p, eb, d_q, d_out, base + 2 * fb, ws_bytes - 2 * fb, stream);
+    }
+    e = cudaMemcpyAsync(d_q, h_q, (size_t)sh.N * 4, cudaMemcpyHostToDevice, stream);
     if (e != cudaSuccess) return cuda_fail(e, "copy q to device");
     s = qai_mitigate(d_q, d_out, rank, dims, eb, params, base + 2 * fb, ws_bytes - 2 * fb, stream, nullptr);
     if (s != QAI_OK) return s;

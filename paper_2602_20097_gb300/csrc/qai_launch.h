@@ -75,6 +75,17 @@ cudaError_t launch_route_sparse_sites(const RouteArgs& a, cudaStream_t st);
 // the dense second EDT runs, 2: always) and the packed S from the separable
 // first EDT's int8 S map (gated: when that EDT ran as the fallback).
 cudaError_t launch_local_detect(const LocalArgs& a, cudaStream_t st);
+// Step A in z-slabs (the host-memory pipeline): whether the field takes the
+// tiled fast path, one slab of it (planes zb .. zb + zn - 1, its neighbour
+// planes already in place), and the exact pass behind all the slabs.
+bool local_detect_slabs(const LocalArgs& a);
+cudaError_t launch_local_detect_slab(const LocalArgs& a, int zb, int zn, cudaStream_t st);
+cudaError_t launch_local_detect_exact(const LocalArgs& a, cudaStream_t st);
+// Outputs that changed after step A, written straight into the caller's
+// mapped host buffer: the queries' outputs, or every output when a pass that
+// rewrites more ran (the exact step A, the separable first EDT, the dense
+// second EDT).
+cudaError_t launch_host_fixup(const LocalArgs& a, float* h_out_mapped, cudaStream_t st);
 cudaError_t launch_local_near(const LocalArgs& a, cudaStream_t st);
 cudaError_t launch_local_expand(const LocalArgs& a, int mode, cudaStream_t st);
 cudaError_t launch_local_pack_s(const LocalArgs& a, bool gated, cudaStream_t st);

@@ -447,7 +447,7 @@ __device__ __forceinline__ bool wait_plane(uint64_t* bar, uint32_t parity)
 }
 
 __global__ void __launch_bounds__(256, 3) k_detect_tma(LocalArgs a, const __grid_constant__ CUtensorMap tm,
-                                                      int tiles_x, int64_t steps)
+                                                      int tiles_x, int zb, int zn)
 {
     extern __shared__ __align__(128) int sbuf[];  // the plane ring, then the slots' barriers
     uint64_t* bars = reinterpret_cast<uint64_t*>(sbuf + kSlots * kSlotInts);
@@ -465,14 +465,16 @@ __global__ void __launch_bounds__(256, 3) k_detect_tma(LocalArgs a, const __grid
     __syncthreads();
     uint32_t parity = 0;  // bit s: the phase parity slot s completes next
     bool timed_out = false, wide = false;
+    // planes zb .. zb + zn - 1 of every tile (the whole field, or one slab)
     const int nz = a.nz;
+    const int64_t steps = (int64_t)tiles_x * ((a.ny + kTY - 1) / kTY) * zn;
     const int64_t s0 = steps * blockIdx.x / gridDim.x, s1 = steps * (blockIdx.x + 1) / gridDim.x;
     auto slot_of = [](int z) { return ((z % kSlots) + kSlots) % kSlots; };
     for (int64_t s = s0; s < s1;) {
         // a run of planes z0 .. z1 - 1 of one tile
-        const int tile = (int)(s / nz);
-        const int z0 = (int)(s - (int64_t)tile * nz);
-        const int z1 = (int)min((int64_t)nz, (int64_t)z0 + (s1 - s));
+        const int tile = (int)(s / zn);
+        const int z0 = zb + (int)(s - (int64_t)tile * zn);
+        const int z1 = (int)min((int64_t)zb + zn, (int64_t)z0 + (s1 - s));
         const int x0t = (tile % tiles_x) * kTX, y0t = (tile / tiles_x) * kTY;
         if (threadIdx.x == 0) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -793,6 +795,37 @@ __global__ void __launch_bounds__(256) k_pack_s(LocalArgs a, int gated)
     }
 }
 
+// The host-memory pipeline's last step: step A's slabs went to the host as
+// soon as they were written; the outputs that changed after it go straight
+// into the caller's mapped host buffer -- the queries' outputs (the routes of
+// the second EDT write nothing else), or every output when a pass that
+// rewrites more ran (the exact step A, the separable first EDT, the dense
+// second EDT) or a bounded wait ran out. vec: 16-byte aligned, N a multiple
+// of 4.
+__global__ void __launch_bounds__(256) k_host_fixup(LocalArgs a, float* h_out, int vec)
+{
+    wait_prior_grid();
+    const volatile int* ctr = a.ctr;
+    const bool all = ctr[kCtrWide] || ctr[kCtrLocalFail] || ctr[kCtrDense] || ctr[kCtrTimeout];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (all) {
+        const int64_t N = (int64_t)a.nz * a.ny * a.nx;
+        if (vec) {
+            for (int64_t i = t0; i < N / 4; i += stride)
+                reinterpret_cast<float4*>(h_out)[i] = __ldg(reinterpret_cast<const float4*>(a.out) + i);
+        } else {
+            for (int64_t i = t0; i < N; i += stride) h_out[i] = a.out[i];
+        }
+        return;
+    }
+    const int nq = min((int)ctr[kCtrQueries], a.qcap);
+    for (int64_t i = t0; i < nq; i += stride) {
+        const int p = a.qlist[i].idx;
+        h_out[p] = a.out[p];
+    }
+}
+
 }  // namespace
 
 namespace {
@@ -845,33 +878,51 @@ bool q_tensor_map(const LocalArgs& a, CUtensorMap* tm)
 
 // The fast path of step A: the tiled form for 3-D fields of 16-byte rows, the
 // row form otherwise.
+static bool tma_form(const LocalArgs& a) { return a.rank == 3 && a.vec && encode_tiled() != nullptr; }
+
+// The tiled fast path over planes zb .. zb + zn - 1.
+static cudaError_t fast_detect_planes(const LocalArgs& a, int zb, int zn, cudaStream_t st)
+{
+    CUtensorMap tm;
+    if (!q_tensor_map(a, &tm)) return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_detect_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    int dev = 0, sms = 152, per = 1;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_detect_tma, 256, kTmaSmem) != cudaSuccess || per < 1)
+        per = 1;
+    const int tiles_x = (a.nx + kTX - 1) / kTX, tiles_y = (a.ny + kTY - 1) / kTY;
+    const int64_t steps = (int64_t)tiles_x * tiles_y * zn;
+    const int grid = (int)std::min<int64_t>(steps, (int64_t)sms * per);
+    return launch_chained(k_detect_tma, dim3(grid), dim3(256), kTmaSmem, st, a, tm, tiles_x, zb, zn);
+}
+
 static cudaError_t fast_detect(const LocalArgs& a, cudaStream_t st)
 {
     auto run = [&](auto kern) {
         return launch_chained(kern, dim3(one_wave(kern, QAI_DETECT_WAVES)), dim3(256), 0, st, a, 0);
     };
-    if (a.rank == 3 && a.vec) {
-        // the tiled form: rows of 16-byte multiples, 16-byte aligned q and D''
-        CUtensorMap tm;
-        if (q_tensor_map(a, &tm)) {
-            static bool attr = false;
-            if (!attr) {
-                cudaError_t e = cudaFuncSetAttribute(k_detect_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                     (int)kTmaSmem);
-                if (e != cudaSuccess) return e;
-                attr = true;
-            }
-            int dev = 0, sms = 152, per = 1;
-            if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_detect_tma, 256, kTmaSmem) != cudaSuccess ||
-                per < 1)
-                per = 1;
-            const int tiles_x = (a.nx + kTX - 1) / kTX, tiles_y = (a.ny + kTY - 1) / kTY;
-            const int64_t steps = (int64_t)tiles_x * tiles_y * a.nz;
-            const int grid = (int)std::min<int64_t>(steps, (int64_t)sms * per);
-            return launch_chained(k_detect_tma, dim3(grid), dim3(256), kTmaSmem, st, a, tm, tiles_x, steps);
-        }
-    }
+    if (tma_form(a)) return fast_detect_planes(a, 0, a.nz, st);
+    if (a.rank == 3) return a.vec ? run(k_detect<3, true>) : run(k_detect<3, false>);
+    return a.vec ? run(k_detect<2, true>) : run(k_detect<2, false>);
+}
+
+bool local_detect_slabs(const LocalArgs& a) { return a.m.sign_rule == 0 && tma_form(a); }
+
+cudaError_t launch_local_detect_slab(const LocalArgs& a, int zb, int zn, cudaStream_t st)
+{
+    return fast_detect_planes(a, zb, zn, st);
+}
+
+cudaError_t launch_local_detect_exact(const LocalArgs& a, cudaStream_t st)
+{
+    auto run = [&](auto kern) {
+        return launch_chained(kern, dim3(one_wave(kern, QAI_DETECT_WAVES)), dim3(256), 0, st, a, 2);
+    };
     if (a.rank == 3) return a.vec ? run(k_detect<3, true>) : run(k_detect<3, false>);
     return a.vec ? run(k_detect<2, true>) : run(k_detect<2, false>);
 }
@@ -905,6 +956,13 @@ cudaError_t launch_local_expand(const LocalArgs& a, int mode, cudaStream_t st)
     };
     if (a.rank == 3) return a.vec ? run(k_expand<3, true>) : run(k_expand<3, false>);
     return a.vec ? run(k_expand<2, true>) : run(k_expand<2, false>);
+}
+
+cudaError_t launch_host_fixup(const LocalArgs& a, float* h_out_mapped, cudaStream_t st)
+{
+    const int vec = (a.nx % 4 == 0) && (reinterpret_cast<uintptr_t>(h_out_mapped) & 15) == 0 &&
+                    (reinterpret_cast<uintptr_t>(a.out) & 15) == 0;
+    return launch_chained(k_host_fixup, dim3(one_wave(k_host_fixup)), dim3(256), 0, st, a, h_out_mapped, vec);
 }
 
 cudaError_t launch_local_pack_s(const LocalArgs& a, bool gated, cudaStream_t st)
