@@ -267,7 +267,7 @@ int final_pass_blocks(const Shape& sh)
 // The host-memory pipeline of qai_mitigate_host (see there): step A runs in
 // z-slabs as their planes of q arrive, and each slab of D'' goes back while
 // later slabs arrive.
-constexpr int kMaxSlabs = 8;
+constexpr int kMaxSlabs = 16;
 struct HostPipe {
     const int32_t* h_q;
     float* h_out;          // host buffer, as the caller passed it
@@ -332,14 +332,16 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
         la.vec = (sh.nx % 4 == 0) && al(d_q, 16) && al(d_out, 16);
     }
     if (ctr && hp) {
-        // Step A slab by slab as q arrives (slab k needs its planes and the
-        // first plane of slab k + 1), each slab of D'' back to the host as
-        // soon as it is written; then the exact pass behind the slabs
+        // Step A slab by slab as q arrives, each slab of D'' back to the host
+        // as soon as it is written; then the exact pass behind the slabs.
+        // Step A at a plane needs the plane after it, so the launch after
+        // copy k covers the planes from the last of copy k - 1 to the one
+        // before the last of copy k (the last launch to the end).
         const size_t plane = (size_t)sh.ny * sh.nx;
         for (int k = 0; k < hp->nslab; ++k) {
             cudaStreamWaitEvent(st, hp->ev_in[k], 0);
-            if (k + 1 < hp->nslab) cudaStreamWaitEvent(st, hp->ev_in[k + 1], 0);
-            const int zb = hp->zb[k], zn = hp->zb[k + 1] - hp->zb[k];
+            const int zb = k == 0 ? 0 : hp->zb[k] - 1;
+            const int zn = (k + 1 == hp->nslab ? sh.nz : hp->zb[k + 1] - 1) - zb;
             e = timed("detect", (double)zn * plane * 8.75, st,
                       [&] { return qai::launch_local_detect_slab(la, zb, zn, st); });
             if (e != cudaSuccess) return cuda_fail(e, "step A (slab)");
