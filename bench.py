@@ -402,20 +402,39 @@ def _time_steps(fn, steps, warmup=3):
     return e0.elapsed_time(e1) / steps
 
 
+def _kernel_shares(fn):
+    """Per-kernel device time of one call of ``fn`` (CUDA events around each
+    launch, untimed run)."""
+    from paper_2602_20097_gb300 import qai
+    qai.profile_read()
+    qai.profile_enable(True)
+    fn()
+    stats = qai.profile_read()
+    qai.profile_enable(False)
+    return {k: round(v[1], 4) for k, v in sorted(stats.items(), key=lambda kv: -kv[1][1]) if v[1] > 0}
+
+
 def run_aniso(args):
-    """The anisotropic shapes with a tanh front (one JSON line per shape)."""
+    """The anisotropic shapes with a tanh front, at eb 1e-3 and 1e-2 of the
+    value range (one JSON line per shape and bound): throughput, quality gain,
+    the routes the EDTs took and the per-kernel times."""
     import torch
     from paper_2602_20097_gb300 import qai, synth
-    for shape, seed in (((100, 500, 500), 3), ((256, 384, 384), 4), ((98, 1200, 1200), 5), ((1800, 3600), 6)):
+    for shape, seed in (((1800, 3600), 6), ((256, 384, 384), 4), ((100, 500, 500), 3), ((98, 1200, 1200), 5)):
         x = synth.grf_front(shape, seed=seed, device="cuda")
-        eb = 1e-3 * synth.value_range(x)
-        q = synth.quantize(x, eb)
-        ws = qai.alloc_workspace(qai.workspace_size(tuple(q.shape)))
-        out = torch.empty_like(q, dtype=torch.float32)
-        ms = _time_steps(lambda: qai.mitigate(q, eb, out=out, workspace=ws), args.steps)
-        print(json.dumps({"workload": "front_" + "x".join(map(str, shape)) + "_eb1e-3",
-                          "value": q.numel() * 4 / (ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ms,
-                          **quality_gain(x, q, eb, out)}), flush=True)
+        for rel in (1e-3, 1e-2):
+            eb = rel * synth.value_range(x)
+            q = synth.quantize(x, eb)
+            ws = qai.alloc_workspace(qai.workspace_size(tuple(q.shape)))
+            out = torch.empty_like(q, dtype=torch.float32)
+            ms = _time_steps(lambda: qai.mitigate(q, eb, out=out, workspace=ws), args.steps)
+            routes = qai.route_counts(ws, tuple(q.shape))
+            kernels = _kernel_shares(lambda: qai.mitigate(q, eb, out=out, workspace=ws))
+            print(json.dumps({"workload": "front_" + "x".join(map(str, shape)) + f"_eb{rel:.0e}".replace("e-0", "e-"),
+                              "value": q.numel() * 4 / (ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ms,
+                              **quality_gain(x, q, eb, out), "routes": routes,
+                              "kernels_ms": kernels}), flush=True)
+            del ws, out, q
 
 
 def run_batch96(args):

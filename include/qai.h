@@ -347,6 +347,74 @@ qai_status qai_quality(const float* d_x, const float* d_y, int rank, const int64
 qai_status qai_mitigate_static(const int32_t* d_q, float* d_out, int rank, const int64_t* dims,
                                double eb, const qai_params* params, cudaStream_t stream);
 
+/* ---- Sharded calls (Section VII-B, distributed-memory parallelization) -----
+ * A rank-2 or rank-3 field (every extent >= 2) is cut along axis 0 (z of a
+ * 3-D field, y of a 2-D one) into P contiguous slabs, one per process; slab k
+ * holds the planes [floor(k n0 / P), floor((k + 1) n0 / P)). The processes'
+ * exchanges are host code (paper_2602_20097_gb300/sharded.py over
+ * torch.distributed); these entry points are each process's device work.
+ *
+ *  extended slab  a slab plus the one plane on each side that a neighbour
+ *                 owns (none past the field's ends): ext_dims = {planes, n1}
+ *                 or {planes, n1, n2}, C order. Step A and GetBoundary(S) on
+ *                 it equal the whole field's on the slab's own planes: its
+ *                 first and last planes are not interior to it, and its other
+ *                 planes see their true neighbours.
+ *  band           every line along axis 0 through a range of `width` axis-1
+ *                 indices: band_dims = {n0, width} or {n0, width, n2}, C order
+ *                 (a band of a 3-D field is a z-by-width-by-nx block).
+ *
+ * The exact form (sequentially compliant) runs, on every process,
+ * qai_shard_rows(1) on its extended slab; an all-to-all from slabs to bands;
+ * qai_shard_lines(1) on its band (Dist1 and S = S_B[I1] of the whole field);
+ * S back to the extended slabs; qai_shard_rows(2); an all-to-all to bands;
+ * qai_shard_lines(2) (Dist2 fused with step E); D'' back to the slabs. The
+ * result equals qai_mitigate's on the whole field bit for bit. The
+ * approximate form (the paper's "local communication" strategy) runs both
+ * qai_shard_lines on the extended slab itself, with the neighbours' S planes
+ * copied into it between the two phases: the EDTs see only the slab's own
+ * sites. */
+
+/* Workspace of qai_shard_rows on an extended slab, and the bytes per point of
+ * its output words (2 for rank 2, 4 for rank 3). */
+qai_status qai_shard_sizes(int rank, const int64_t* ext_dims, size_t* ws_bytes, int* word_bytes);
+
+/* Row work on an extended slab: the passes of an EDT along every axis but
+ * axis 0 (Algorithm 1; x, then y for 3-D).
+ *  phase 1  step A (Algorithm 2: B1 and S_B) and the first EDT's passes with
+ *           the sign code of each nearest B1 point carried along; writes the
+ *           equal-q neighbour map d_eqm (1 byte a point) and d_words. d_s is
+ *           unused.
+ *  phase 2  GetBoundary(S) (Algorithm 3: B2 from S and q) and the second
+ *           EDT's passes; reads d_q, d_eqm (from phase 1 on the same slab) and
+ *           d_s (S on the extended slab, int8), writes d_words.
+ * d_words holds word_bytes per point (qai_shard_sizes), d_ws ws_bytes, all
+ * device memory owned by the caller. QAI_ERR_SHAPE for extents beyond the
+ * line limits of qai_mitigate or >= 2^31 points. */
+qai_status qai_shard_rows(int phase, int rank, const int64_t* ext_dims, const int32_t* d_q,
+                          const int8_t* d_s, uint8_t* d_eqm, void* d_words, void* d_ws, size_t ws_bytes,
+                          const qai_params* params, cudaStream_t stream);
+
+/* Line work on a band (or, in the approximate form, on an extended slab
+ * viewed as one band): the last pass of an EDT, along axis 0.
+ *  phase 1  reads the phase-1 words; writes Dist1 (int32 squared distance,
+ *           INT32_MAX where the lines hold no B1 point), S (int8) and
+ *           d_count (uint16 per line: its points with S != 0, saturated).
+ *  phase 2  reads the phase-2 words, d_q, Dist1, S and d_count of the same
+ *           band; writes D'' (float32) = 2 q eps + S w eta eps (step E).
+ * band_dims: the block's extents; dims: the whole field's (they bound the
+ * distances the words can carry; band_dims[a] <= dims[a]). Arrays of the block's points (d_count: one
+ * entry per line), device memory owned by the caller. */
+qai_status qai_shard_lines(int phase, int rank, const int64_t* band_dims, const int64_t* dims,
+                           const void* d_words, const int32_t* d_q, int32_t* d_dist1, int8_t* d_s,
+                           uint16_t* d_count, float* d_out, double eb, const qai_params* params,
+                           cudaStream_t stream);
+
+/* Strided device-to-device block copy for the exchanges: `height` runs of
+ * `width` bytes, `src_pitch` / `dst_pitch` bytes apart (pitches >= width). */
+qai_status qai_shard_copy(void* d_dst, int64_t dst_pitch, const void* d_src, int64_t src_pitch, int64_t width,
+                          int64_t height, cudaStream_t stream);
+
 /* Per-kernel timing. While enabled, every kernel the library launches is
  * bracketed by CUDA events recorded on the launch stream. qai_profile_read
  * waits for the recorded events, then reports, per kernel name, the launch

@@ -15,6 +15,13 @@ Functions (numpy in, numpy out):
 * :func:`boundary_and_sign` -- Algorithm 2 alone.
 * :func:`grad_params` -- adjoint of step E with respect to eta and the IDW
   exponent p, the EDT assignment held fixed (no counterpart in the paper).
+* :func:`boundary_of_s` -- GetBoundary(S) of Algorithm 3 for a given S.
+* :func:`compensate` -- step E alone on given distances and S.
+* :func:`mitigate_approx` -- Section VII-B's approximate parallelization:
+  ghost planes for step A and for GetBoundary(S), both EDTs inside each slab.
+* :func:`mitigate_independent` -- Section VII-B's embarrassingly parallel
+  strategy: Algorithm 4 on each slab alone.
+* :func:`slab_bounds` -- the slab partition both sharded strategies use.
 """
 from __future__ import annotations
 
@@ -76,6 +83,14 @@ def _load():
         lib.qai_oracle_set_threads.restype = None
         lib.qai_oracle_grad_params.argtypes = [P, ctypes.c_int, P, ctypes.c_double,
                                                ctypes.POINTER(_Params), P, P]
+        lib.qai_oracle_boundary_of_s.argtypes = [P, P, ctypes.c_int, P, ctypes.POINTER(_Params), P]
+        lib.qai_oracle_boundary_of_s.restype = ctypes.c_int
+        lib.qai_oracle_compensate.argtypes = [P, P, P, P, ctypes.c_int64, ctypes.c_double,
+                                              ctypes.POINTER(_Params), P]
+        lib.qai_oracle_compensate.restype = ctypes.c_int
+        lib.qai_oracle_mitigate_approx.argtypes = [P, ctypes.c_int, P, ctypes.c_double,
+                                                   ctypes.POINTER(_Params), ctypes.c_int] + [P] * 6
+        lib.qai_oracle_mitigate_approx.restype = ctypes.c_int
         lib.qai_oracle_grad_params.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -172,3 +187,76 @@ def boundary_and_sign(q, grad_threshold=2, sign_rule=SIGN_SUM):
     _load().qai_oracle_boundary_and_sign(_ptr(q), q.ndim, _ptr(_dims(q.shape)),
                                          ctypes.byref(p), _ptr(b), _ptr(s))
     return b, s
+
+
+def boundary_of_s(q, s, grad_threshold=2, b2_rule=B2_SAME_Q):
+    """GetBoundary(S) (second half of Algorithm 3) on interior points: uint8 B2."""
+    q = np.ascontiguousarray(q, dtype=np.int32)
+    s = np.ascontiguousarray(s, dtype=np.int8)
+    if s.shape != q.shape:
+        raise ValueError("s must have q's shape")
+    b2 = np.empty(q.shape, np.uint8)
+    p = _params(0.9, 1.0, grad_threshold, SIGN_SUM, b2_rule)
+    rc = _load().qai_oracle_boundary_of_s(_ptr(q), _ptr(s), q.ndim, _ptr(_dims(q.shape)),
+                                          ctypes.byref(p), _ptr(b2))
+    if rc != 0:
+        raise ValueError(f"oracle rejected the arguments (rc={rc})")
+    return b2
+
+
+def compensate(q, dist1, dist2, s, eb, eta=0.9, idw_power=1.0):
+    """Step E alone: D'' = 2 q eps + S w eta eps (float64), distances squared
+    with INT32_MAX for INF."""
+    q = np.ascontiguousarray(q, dtype=np.int32)
+    d1 = np.ascontiguousarray(dist1, dtype=np.int32)
+    d2 = np.ascontiguousarray(dist2, dtype=np.int32)
+    s = np.ascontiguousarray(s, dtype=np.int8)
+    if not (q.shape == d1.shape == d2.shape == s.shape):
+        raise ValueError("q, dist1, dist2 and s must share a shape")
+    out = np.empty(q.shape, np.float64)
+    p = _params(eta, idw_power, 2, SIGN_SUM, B2_SAME_Q)
+    rc = _load().qai_oracle_compensate(_ptr(q), _ptr(d1), _ptr(d2), _ptr(s), ctypes.c_int64(q.size),
+                                       float(eb), ctypes.byref(p), _ptr(out))
+    if rc != 0:
+        raise ValueError(f"oracle rejected the arguments (rc={rc})")
+    return out
+
+
+def slab_bounds(n0, nparts):
+    """Planes [b, e) of each of the nparts slabs of an axis of extent n0."""
+    return [(k * n0 // nparts, (k + 1) * n0 // nparts) for k in range(nparts)]
+
+
+def _squeezed(shape):
+    kept = tuple(n for n in shape if n > 1)
+    return kept or (1,)
+
+
+def mitigate_approx(q, eb, nparts, eta=0.9, idw_power=1.0, grad_threshold=2,
+                    sign_rule=SIGN_SUM, b2_rule=B2_SAME_Q):
+    """Section VII-B's approximate parallelization over ``nparts`` slabs of the
+    slowest axis (after squeezing extent-1 axes; rank 2 or 3). Returns
+    ``out, dist1, idx1 (whole-field index), s, b2, dist2``."""
+    q = np.ascontiguousarray(q, dtype=np.int32)
+    shp = q.shape
+    res = {"out": np.empty(shp, np.float64), "dist1": np.empty(shp, np.int32),
+           "idx1": np.empty(shp, np.int32), "s": np.empty(shp, np.int8),
+           "b2": np.empty(shp, np.uint8), "dist2": np.empty(shp, np.int32)}
+    p = _params(eta, idw_power, grad_threshold, sign_rule, b2_rule)
+    rc = _load().qai_oracle_mitigate_approx(
+        _ptr(q), q.ndim, _ptr(_dims(shp)), float(eb), ctypes.byref(p), int(nparts), _ptr(res["out"]),
+        _ptr(res["dist1"]), _ptr(res["idx1"]), _ptr(res["s"]), _ptr(res["b2"]), _ptr(res["dist2"]))
+    if rc != 0:
+        raise ValueError(f"oracle rejected the arguments (rc={rc})")
+    return res
+
+
+def mitigate_independent(q, eb, nparts, **kw):
+    """Section VII-B's embarrassingly parallel strategy: Algorithm 4 on each of
+    the ``nparts`` slabs of the slowest axis alone. Returns D'' (float64)."""
+    q = np.ascontiguousarray(q, dtype=np.int32)
+    sq = q.reshape(_squeezed(q.shape))
+    out = np.empty(sq.shape, np.float64)
+    for b, e in slab_bounds(sq.shape[0], nparts):
+        out[b:e] = mitigate(sq[b:e], eb, debug=False, **kw)["out"]
+    return out.reshape(q.shape)

@@ -227,16 +227,11 @@ int qai_oracle_edt(const uint8_t* sites, int rank, const int64_t* dims,
 }
 
 /* ---- Step C: Algorithm 3, PropagateSignsAndConstructSignMap ------------- */
-static void propagate_and_b2(const int32_t* Q, const shape3* s, const qai_oracle_params* p,
-                             const uint8_t* B1, const int8_t* SB, const int64_t* I1,
-                             int8_t* S, uint8_t* B2)
+
+/* GetBoundary(S) with the R4 rule, interior points only (as in Alg. 2). */
+static void boundary_of_s(const int32_t* Q, const shape3* s, const qai_oracle_params* p,
+                          const int8_t* S, uint8_t* B2)
 {
-    memcpy(S, SB, (size_t)s->N);
-    /* In place is safe: S is only read at boundary points, never written there. */
-#pragma omp parallel for schedule(static)
-    for (int64_t i = 0; i < s->N; i++)
-        if (B1[i] != 1) S[i] = (I1[i] >= 0) ? S[I1[i]] : 0;
-    /* GetBoundary(S) with the R4 rule, interior points only (as in Alg. 2). */
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < s->N; i++) {
         B2[i] = 0;
@@ -251,6 +246,28 @@ static void propagate_and_b2(const int32_t* Q, const shape3* s, const qai_oracle
     }
 }
 
+static void propagate_and_b2(const int32_t* Q, const shape3* s, const qai_oracle_params* p,
+                             const uint8_t* B1, const int8_t* SB, const int64_t* I1,
+                             int8_t* S, uint8_t* B2)
+{
+    memcpy(S, SB, (size_t)s->N);
+    /* In place is safe: S is only read at boundary points, never written there. */
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < s->N; i++)
+        if (B1[i] != 1) S[i] = (I1[i] >= 0) ? S[I1[i]] : 0;
+    boundary_of_s(Q, s, p, S, B2);
+}
+
+/* GetBoundary(S) alone (the second half of Algorithm 3) for a given S. */
+int qai_oracle_boundary_of_s(const int32_t* Q, const int8_t* S, int rank, const int64_t* dims,
+                             const qai_oracle_params* p, uint8_t* B2)
+{
+    shape3 s;
+    if (make_shape(rank, dims, &s)) return -1;
+    boundary_of_s(Q, &s, p, S, B2);
+    return 0;
+}
+
 /* ---- Step E: IDW compensation ------------------------------------------- */
 static double idw_weight(int64_t d1, int64_t d2, double pw)
 {
@@ -262,6 +279,35 @@ static double idw_weight(int64_t d1, int64_t d2, double pw)
     /* (1/k1^p) / (1/k1^p + 1/k2^p) written as k2^p / (k1^p + k2^p) */
     double a = pow(k1, pw), b = pow(k2, pw);
     return b / (a + b);
+}
+
+/* Step E at n points: D' = 2 q eps (Eq. 1), C = S w eta eps, out = D' + C. */
+static void compensate(const int32_t* Q, const int64_t* D1, const int64_t* D2, const int8_t* S,
+                       int64_t n, double eb, const qai_oracle_params* p, double* out, double* comp_out)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; i++) {
+        double dprime = 2.0 * (double)Q[i] * eb;
+        double c = (double)S[i] * idw_weight(D1[i], D2[i], p->idw_power) * p->eta * eb;
+        if (out) out[i] = dprime + c;
+        if (comp_out) comp_out[i] = c;
+    }
+}
+
+/* Step E alone on given int32 distances (INT32_MAX = INF) and S. */
+int qai_oracle_compensate(const int32_t* Q, const int32_t* dist1, const int32_t* dist2, const int8_t* S,
+                          int64_t n, double eb, const qai_oracle_params* p, double* out)
+{
+    if (n < 0 || !(eb > 0.0) || !isfinite(eb)) return -1;
+    int64_t* d = (int64_t*)malloc(sizeof(int64_t) * (size_t)(2 * n + 1));
+    if (!d) return -2;
+    for (int64_t i = 0; i < n; i++) {
+        d[i] = dist1[i] == INT32_MAX ? ORC_INF : dist1[i];
+        d[n + i] = dist2[i] == INT32_MAX ? ORC_INF : dist2[i];
+    }
+    compensate(Q, d, d + n, S, n, eb, p, out, NULL);
+    free(d);
+    return 0;
 }
 
 /* Full Algorithm 4. out = D'' (FP64). Every other pointer may be NULL. */
@@ -291,16 +337,100 @@ int qai_oracle_mitigate(const int32_t* Q, int rank, const int64_t* dims, double 
     propagate_and_b2(Q, &s, p, B1, SB, I1, S, B2);                /* step C */
     edt(B2, &s, D2, I2);                                          /* step D */
 
-#pragma omp parallel for schedule(static)
-    for (int64_t i = 0; i < s.N; i++) {                           /* step E */
-        double dprime = 2.0 * (double)Q[i] * eb;                  /* Eq. 1  */
-        double c = (double)S[i] * idw_weight(D1[i], D2[i], p->idw_power) * p->eta * eb;
-        if (out) out[i] = dprime + c;
-        if (comp_out) comp_out[i] = c;
-    }
+    compensate(Q, D1, D2, S, s.N, eb, p, out, comp_out);          /* step E */
     for (int64_t i = 0; i < s.N; i++) {
         if (b1_out) b1_out[i] = B1[i];
         if (sb_out) sb_out[i] = SB[i];
+        if (s_out) s_out[i] = S[i];
+        if (b2_out) b2_out[i] = B2[i];
+        if (dist1_out) dist1_out[i] = D1[i] == ORC_INF ? INT32_MAX : (int32_t)D1[i];
+        if (idx1_out) idx1_out[i] = (int32_t)I1[i];
+        if (dist2_out) dist2_out[i] = D2[i] == ORC_INF ? INT32_MAX : (int32_t)D2[i];
+    }
+done:
+    free(B1); free(SB); free(S); free(B2); free(D1); free(I1); free(D2); free(I2);
+    return rc;
+}
+
+/* ---- Section VII-B, approximate parallelization -------------------------
+ * The field (rank 2 or 3 after R1) is cut along its slowest axis into nparts
+ * slabs, slab k holding the planes [floor(k n0 / P), floor((k + 1) n0 / P)).
+ * Each part exchanges one ghost plane with each neighbour before step A and
+ * again (its S) before the boundary of step C; both EDTs stay inside the
+ * part. So, per part, in the paper's order:
+ *   A  B1, S_B: with q's ghost planes the stencil is the whole field's, so
+ *      they are the whole-field maps restricted to the part;
+ *   B  exact EDT of the part's own B1 points over the part's points only;
+ *   C  S = S_B[I1] with that local I1; then, with S's ghost planes from the
+ *      neighbours' own local S, B2 = GetBoundary(S) with the whole field's
+ *      interior rule;
+ *   D  exact EDT of the part's own B2 points over the part's points only;
+ *   E  as in Algorithm 4.
+ * idx1 is returned as a linear index of the whole field. nparts = 1 is
+ * Algorithm 4 itself. */
+static void slab_range(int k, int nparts, int64_t n0, int64_t* z0, int64_t* z1)
+{
+    *z0 = k * n0 / nparts;
+    *z1 = (k + 1) * n0 / nparts;
+}
+
+static void slab_shape(const shape3* s, int64_t z0, int64_t z1, shape3* sl)
+{
+    *sl = *s;
+    sl->n[3 - s->rank] = z1 - z0;
+    sl->st[2] = 1;
+    sl->st[1] = sl->n[2];
+    sl->st[0] = sl->n[1] * sl->n[2];
+    sl->N = sl->n[0] * sl->n[1] * sl->n[2];
+}
+
+int qai_oracle_mitigate_approx(const int32_t* Q, int rank, const int64_t* dims, double eb,
+                               const qai_oracle_params* p, int nparts, double* out,
+                               int32_t* dist1_out, int32_t* idx1_out, int8_t* s_out,
+                               uint8_t* b2_out, int32_t* dist2_out)
+{
+    shape3 s;
+    if (make_shape(rank, dims, &s)) return -1;
+    if (s.rank < 2 || !(eb > 0.0) || !isfinite(eb)) return -1;
+    const int ax = 3 - s.rank;                       /* the slab axis          */
+    const int64_t n0 = s.n[ax], plane = s.st[ax];
+    if (nparts < 1 || nparts > n0) return -1;
+    size_t N = (size_t)s.N;
+    uint8_t* B1 = (uint8_t*)malloc(N);
+    int8_t* SB = (int8_t*)malloc(N);
+    int8_t* S = (int8_t*)malloc(N);
+    uint8_t* B2 = (uint8_t*)malloc(N);
+    int64_t* D1 = (int64_t*)malloc(N * 8);
+    int64_t* I1 = (int64_t*)malloc(N * 8);
+    int64_t* D2 = (int64_t*)malloc(N * 8);
+    int64_t* I2 = (int64_t*)malloc(N * 8);
+    int rc = 0;
+    if (!B1 || !SB || !S || !B2 || !D1 || !I1 || !D2 || !I2) { rc = -2; goto done; }
+
+    qai_oracle_boundary_and_sign(Q, rank, dims, p, B1, SB);      /* step A */
+    for (int k = 0; k < nparts; k++) {                            /* steps B, C (S) */
+        int64_t z0, z1;
+        slab_range(k, nparts, n0, &z0, &z1);
+        const int64_t off = z0 * plane;
+        shape3 sl;
+        slab_shape(&s, z0, z1, &sl);
+        edt(B1 + off, &sl, D1 + off, I1 + off);
+        for (int64_t i = off; i < off + sl.N; i++) {
+            if (I1[i] >= 0) I1[i] += off;                         /* whole-field index */
+            S[i] = B1[i] ? SB[i] : (I1[i] >= 0 ? SB[I1[i]] : 0);
+        }
+    }
+    boundary_of_s(Q, &s, p, S, B2);                               /* step C (B2) */
+    for (int k = 0; k < nparts; k++) {                            /* step D */
+        int64_t z0, z1;
+        slab_range(k, nparts, n0, &z0, &z1);
+        const int64_t off = z0 * plane;
+        shape3 sl;
+        slab_shape(&s, z0, z1, &sl);
+        edt(B2 + off, &sl, D2 + off, I2 + off);
+    }
+    compensate(Q, D1, D2, S, s.N, eb, p, out, NULL);              /* step E */
+    for (int64_t i = 0; i < s.N; i++) {
         if (s_out) s_out[i] = S[i];
         if (b2_out) b2_out[i] = B2[i];
         if (dist1_out) dist1_out[i] = D1[i] == ORC_INF ? INT32_MAX : (int32_t)D1[i];

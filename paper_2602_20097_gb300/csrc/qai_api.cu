@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -142,6 +143,11 @@ qai_status make_shape(int rank, const int64_t* dims, Shape* s)
 
 // ---- workspace layout -----------------------------------------------------------
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+cudaError_t timed_call(const char* name, double algo_bytes, cudaStream_t st, const std::function<cudaError_t()>& fn)
+{
+    return timed(name, algo_bytes, st, fn);
+}
 
 Layout layout_for(const Shape& s, uint32_t flags)
 {

@@ -3,6 +3,7 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <functional>
 #include <cuda_runtime.h>
 
 #include "qai.h"
@@ -40,6 +41,9 @@ Layout layout_for(const Shape& s, uint32_t flags);
 qai_status check_params(const qai_params* p);
 MethodArgs method_args(const qai_params* p, double eb);
 void count_launch();
+// One launch through fn, counted and, while profiling, timed as kernel `name`
+// with `algo_bytes` algorithmic bytes.
+cudaError_t timed_call(const char* name, double algo_bytes, cudaStream_t st, const std::function<cudaError_t()>& fn);
 
 // qai_mitigate's launch sequence without per-step outputs (a plain call) on a
 // validated shape and a workspace laid out by layout_for(sh, 0).

@@ -93,6 +93,12 @@ SIGNATURES = {
                                             ctypes.c_size_t, P]),
     "qai_autotune_batched": (ctypes.c_int, [ctypes.c_int, P, P, P, P, P, ctypes.POINTER(Params), P,
                                             ctypes.c_size_t, P, ctypes.POINTER(BatchChoice)]),
+    "qai_shard_sizes": (ctypes.c_int, [ctypes.c_int, P, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_int)]),
+    "qai_shard_rows": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, P, P, P, P, P, P, ctypes.c_size_t,
+                                      ctypes.POINTER(Params), P]),
+    "qai_shard_lines": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, P, P, P, P, P, P, P, P, ctypes.c_double,
+                                       ctypes.POINTER(Params), P]),
+    "qai_shard_copy": (ctypes.c_int, [P, ctypes.c_int64, P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, P]),
     "qai_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "qai_profile_read": (ctypes.c_int, [ctypes.POINTER(KernelStat), ctypes.c_int]),
     "qai_profile_select": (ctypes.c_int, [ctypes.c_char_p]),

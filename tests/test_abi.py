@@ -132,3 +132,24 @@ def test_quality_sizes_and_argument_errors():
     rc = lib.qai_quality(ctypes.c_void_p(256), ctypes.c_void_p(256), 3, qai._dims(shape), 7, 2,
                          ctypes.c_void_p(256), None, ctypes.c_void_p(256), 8, None)
     assert rc == 1 and b"workspace" in lib.qai_last_error()
+
+
+def test_shard_entry_points_check_arguments_before_launching():
+    lib = qai.load()
+    fake = 4096        # never dereferenced: every call below fails its checks first
+    dims = qai._dims((4, 5, 6))
+    ws, wb = ctypes.c_size_t(), ctypes.c_int()
+    assert lib.qai_shard_sizes(3, dims, ctypes.byref(ws), ctypes.byref(wb)) == 0
+    assert ws.value >= 4 * 5 * 6 * 2 and wb.value == 4
+    assert lib.qai_shard_sizes(2, qai._dims((4, 5)), ctypes.byref(ws), ctypes.byref(wb)) == 0
+    assert ws.value == 0 and wb.value == 2
+    assert lib.qai_shard_sizes(1, qai._dims((4,)), ctypes.byref(ws), ctypes.byref(wb)) == 2
+    assert lib.qai_shard_sizes(3, qai._dims((4, 5000, 6)), ctypes.byref(ws), ctypes.byref(wb)) == 2
+    assert lib.qai_shard_rows(3, 3, dims, fake, None, fake, fake, fake, 1 << 20, None, None) == 1
+    assert lib.qai_shard_rows(2, 3, dims, fake, None, fake, fake, fake, 1 << 20, None, None) == 1  # no S
+    assert lib.qai_shard_rows(1, 3, dims, fake, None, fake, fake, fake, 1, None, None) == 1        # workspace
+    assert lib.qai_shard_lines(1, 3, qai._dims((5, 5, 6)), dims, fake, None, fake, fake, fake, None, 0.1,
+                               None, None) == 2                                                    # band > field
+    assert lib.qai_shard_lines(2, 3, dims, dims, fake, fake, fake, fake, fake, fake, -1.0, None, None) == 1
+    assert lib.qai_shard_copy(fake, 4, fake, 8, 16, 2, None) == 1                                 # pitch < width
+    assert lib.qai_shard_copy(None, 16, None, 16, 0, 2, None) == 0                                # nothing to copy

@@ -40,6 +40,11 @@ MUTATIONS = {
     "k2_zero_precedence": ("    if (d1 == 0) return 1.0;                /* on a quantization boundary     */\n"
                            "    if (d2 == 0) return 0.0;",
                            "    if (d2 == 0) return 0.0;\n    if (d1 == 0) return 1.0;"),
+    # Section VII-B approximate strategy
+    "approx_index_not_global": ("if (I1[i] >= 0) I1[i] += off;", ""),
+    "approx_slabs_overlap": ("*z1 = (k + 1) * n0 / nparts;", "*z1 = (k + 1) * n0 / nparts + (k + 1 < nparts);"),
+    "approx_edt2_whole_field": ("edt(B2 + off, &sl, D2 + off, I2 + off);", "edt(B2, &s, D2, I2);"),
+    "approx_s_not_propagated": ("S[i] = B1[i] ? SB[i] : (I1[i] >= 0 ? SB[I1[i]] : 0);", "S[i] = SB[i];"),
 }
 
 
@@ -56,6 +61,7 @@ def test_mutation_is_caught(name, tmp_path):
     env = dict(os.environ, QAI_ORACLE_LIB=str(lib), OMP_NUM_THREADS="1")
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", "test_oracle_pins.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_adjoint.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_adjoint.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_sharded.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutation {name} survived the pins:\n{r.stdout[-2000:]}"
