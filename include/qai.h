@@ -232,19 +232,26 @@ qai_status qai_mitigate_backward(const int32_t* d_q, const float* d_grad_out, fl
 /* ---- Batched form (no counterpart in the paper) ---------------------------
  * n independent fields in one call: field i is d_q[i] -> d_out[i] (device
  * buffers), rank ranks[i], extents dims[3*i .. 3*i + ranks[i]) (slowest first),
- * bound eb[i]; params are shared. Rank-2 and rank-3 fields each run the
- * launch sequence of a plain qai_mitigate call, dealt round robin onto a few
- * streams forked from `stream` and joined back (the small fields' kernels
- * overlap); rank-1 fields run as two grouped kernels over all of them. The
- * whole launch sequence is captured into a CUDA graph the first time a batch
- * is seen (keyed by every pointer, extent and parameter) and replayed
- * afterwards: a repeated batch is one graph launch on `stream`. When `stream`
- * is already capturing, the launches are recorded into the caller's graph
- * instead. Results equal those of n qai_mitigate calls. The stream count and
- * the field order come from qai_autotune_batched when it has seen a batch of
- * the same shapes. */
+ * bound eb[i]; params are shared. Rank-2 and rank-3 fields run as persistent
+ * grouped launches: each kernel of a plain qai_mitigate call's sequence runs
+ * once for all of them (fields with the same tile shape share a launch; up to
+ * 64 fields a launch), its resident CTAs taking (field, block) work items
+ * from a device cursor in queue order; a field whose fallback flag is clear
+ * adds no items to the fallback kernels. Rank-1 fields run as two grouped
+ * kernels over all of them. The whole launch sequence (argument tables copied
+ * in from pinned host memory, cursors and route counters cleared, the
+ * grouped kernels) is captured into a CUDA graph the first time a batch is
+ * seen (keyed by every pointer, extent and parameter) and replayed
+ * afterwards: a repeated batch is one graph launch on `stream`. With a
+ * QAI_FLAG_EDT2_* or QAI_FLAG_EDT1_SEPARABLE bit, or when `stream` is already
+ * capturing (the launches are then recorded into the caller's graph), rank-2
+ * and rank-3 fields run their own plain sequences on streams forked from
+ * `stream`. Results equal those of n qai_mitigate calls. The queue order and
+ * tile shapes (and, per field, the stream count) come from
+ * qai_autotune_batched when it has seen a batch of the same shapes. */
 
-/* Device workspace of a batch: the sum of the fields' workspaces. */
+/* Device workspace of a batch: the fields' workspaces and a header for the
+ * grouped launches (argument tables, cursors, route counters). */
 qai_status qai_workspace_size_batched(int n, const int32_t* ranks, const int64_t* dims, size_t* bytes);
 
 qai_status qai_mitigate_batched(int n, const int32_t* const* d_q, float* const* d_out,
@@ -254,18 +261,28 @@ qai_status qai_mitigate_batched(int n, const int32_t* const* d_q, float* const* 
 
 /* Autotuner result for the fields of one rank. */
 typedef struct {
-    int32_t rank;           /* 1, 2 or 3 (0: no field of this rank)           */
+    int32_t rank;             /* 1, 2 or 3 (0: no field of this rank)                 */
     int32_t fields;
-    int32_t streams;        /* streams the fields are dealt onto (rank 1: 1)  */
-    int32_t order;          /* 0: fields as given, 1: largest field first     */
-    float ms;               /* time of the group's launches with this choice  */
+    int32_t streams;          /* per-field form: streams the fields are dealt onto
+                                 (rank 1: 1); grouped form: 0                          */
+    int32_t order;            /* 0: fields as given, 1: largest field first           */
+    float ms;                 /* time of the group's launches with this choice (the
+                                 grouped form: of ranks 2 and 3 together)              */
+    int32_t grouped;          /* 1: persistent grouped launches                       */
+    int32_t tile_w;           /* column-pass tile width (0: the plain call's tiles)   */
+    int32_t rows_per_band;    /* column-pass band height (0: the plain call's tiles)  */
+    int32_t points_per_block; /* points per work item of the grid-stride kernels      */
+    int32_t launches;         /* kernel launches of the grouped form per batch        */
 } qai_batch_choice;
 
-/* Times every candidate stream count (1, 2, 4, 8) and field order on this
- * batch (running its launches several times; the outputs hold a correct
- * result afterwards), keeps the fastest per rank group for later
- * qai_mitigate_batched calls with the same shapes, and reports it in
- * choices[0..2] (ranks 1..3) when non-NULL. Synchronises `stream`. */
+/* Times candidates on this batch itself (running its launches several times;
+ * the outputs hold a correct result afterwards) and keeps the fastest for
+ * later qai_mitigate_batched calls with the same shapes: for the grouped form
+ * (ranks 2 and 3 together), greedily the queue order, then the points per
+ * work item (2^14 .. 2^18), then the column tiles (band height x largest
+ * width); for the per-field form, the stream count (1, 2, 4, 8) and field
+ * order per rank. Reports them in choices[0..2] (ranks 1..3) when non-NULL.
+ * Synchronises `stream`. */
 qai_status qai_autotune_batched(int n, const int32_t* const* d_q, float* const* d_out,
                                 const int32_t* ranks, const int64_t* dims, const double* eb,
                                 const qai_params* params, void* d_ws, size_t ws_bytes,

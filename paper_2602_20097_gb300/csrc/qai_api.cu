@@ -188,6 +188,118 @@ Layout layout_for(const Shape& s, uint32_t flags)
     return l;
 }
 
+bool plain_args(const int32_t* d_q, float* d_out, const Shape& sh, const qai::MethodArgs& m, char* ws,
+                const Layout& lay, int* ctr, PlainArgs* pa)
+{
+    *pa = PlainArgs{};
+    uint8_t* eqm = reinterpret_cast<uint8_t*>(ws + lay.eqm);
+    int32_t* dist1 = reinterpret_cast<int32_t*>(ws + lay.dist1);
+    int8_t* s = reinterpret_cast<int8_t*>(ws + lay.s);
+    uint16_t* xw = reinterpret_cast<uint16_t*>(ws + lay.xw);
+    uint32_t* yw = sh.rank >= 3 ? reinterpret_cast<uint32_t*>(ws + lay.yw) : nullptr;
+    uint16_t* cflag = reinterpret_cast<uint16_t*>(ws + lay.cflag);
+    qai::Query* qlist = reinterpret_cast<qai::Query*>(ws + lay.qlist);
+    const int* local_fail = ctr + qai::kCtrLocalFail;
+    const int* dense = ctr + qai::kCtrDense;
+    const int64_t gx = (int64_t)(sh.nx - 1) * (sh.nx - 1);
+    const int64_t gxy = gx + (int64_t)(sh.ny - 1) * (sh.ny - 1);
+    auto al = [](const void* p, int b) { return (reinterpret_cast<uintptr_t>(p) % b) == 0; };
+
+    qai::LocalArgs& la = pa->la;
+    la.rank = sh.rank; la.nz = sh.nz; la.ny = sh.ny; la.nx = sh.nx; la.wpr = lay.wpr;
+    la.q = d_q; la.out = d_out; la.ctr = ctr; la.dist1 = dist1;
+    la.codes = reinterpret_cast<uint32_t*>(ws + lay.codes);
+    la.nexy = reinterpret_cast<uint32_t*>(ws + lay.nexy);
+    la.nez = sh.rank == 3 ? reinterpret_cast<uint32_t*>(ws + lay.nez) : nullptr;
+    la.spk = reinterpret_cast<uint32_t*>(ws + lay.spk);
+    la.qlist = qlist; la.qcap = lay.qcap;
+    la.slist = reinterpret_cast<int32_t*>(ws + lay.slist); la.scap = lay.scap;
+    la.eqm = eqm; la.s = s; la.m = m;
+    la.vec = (sh.nx % 4 == 0) && al(d_q, 16) && al(d_out, 16);
+
+    qai::RowArgs& r1 = pa->r1;
+    r1.rank = sh.rank; r1.nz = sh.nz; r1.ny = sh.ny; r1.nx = sh.nx;
+    r1.q = d_q; r1.eqm = eqm; r1.m = m;
+    r1.out_pre = d_out; r1.route_ctr = ctr; r1.gate = local_fail;
+    r1.xw = xw;
+    qai::prepare_rowpass(r1);
+
+    auto y_args = [&](const void* in) {
+        qai::ColArgs c{};
+        c.in = in; c.L = sh.ny; c.C = sh.nx; c.P = sh.nz;
+        c.row_stride = sh.nx; c.plane_stride = (int64_t)sh.ny * sh.nx; c.m = m;
+        return c;
+    };
+    auto z_args = [&](const void* in) {
+        qai::ColArgs c{};
+        c.in = in; c.L = sh.nz; c.C = sh.ny * sh.nx; c.P = 1;
+        c.row_stride = (int64_t)sh.ny * sh.nx; c.plane_stride = 0; c.m = m;
+        return c;
+    };
+    auto route_args = [&](qai::ColArgs& c) {
+        c.route_ctr = ctr; c.qlist = qlist; c.qcap = lay.qcap;
+        c.slist = reinterpret_cast<int32_t*>(ws + lay.slist); c.scap = lay.scap;
+        c.gate = local_fail;
+    };
+    auto fuse_e = [&](qai::ColArgs& c) {
+        c.out = d_out; c.q = d_q; c.dist1_in = dist1; c.s_in = s;
+        c.col_count_in = nullptr;  // the local first EDT: B1 from the mask byte
+        c.b1_eqm = eqm;
+        c.route_ctr = ctr;
+        c.gate = dense;
+    };
+    auto prep = [&](qai::ColArgs& c, int in_bytes, bool first_last, qai::ColConfig* cfg, int64_t max_g) {
+        if (!qai::choose_colpass(c.L, in_bytes, cfg, first_last)) return false;
+        qai::prepare_colpass(c, in_bytes, *cfg, max_g);
+        return true;
+    };
+    if (sh.rank == 2) {
+        pa->c1[0] = y_args(xw);
+        pa->c1[0].dist1 = dist1; pa->c1[0].s_out = s; pa->c1[0].col_count_out = cflag;
+        route_args(pa->c1[0]);
+        pa->c2[0] = y_args(xw);
+        fuse_e(pa->c2[0]);
+        if (!prep(pa->c1[0], 2, true, &pa->cfg1[0], gx) || !prep(pa->c2[0], 2, false, &pa->cfg2[0], gx)) return false;
+    } else {
+        pa->c1[0] = y_args(xw);
+        pa->c1[0].out_w = yw; pa->c1[0].gate = local_fail;
+        pa->c1[1] = z_args(yw);
+        pa->c1[1].dist1 = dist1; pa->c1[1].s_out = s; pa->c1[1].col_count_out = cflag;
+        route_args(pa->c1[1]);
+        pa->c2[0] = y_args(xw);
+        pa->c2[0].out_w = yw; pa->c2[0].gate = dense;
+        pa->c2[1] = z_args(yw);
+        fuse_e(pa->c2[1]);
+        if (!prep(pa->c1[0], 2, false, &pa->cfg1[0], gx) || !prep(pa->c1[1], 4, true, &pa->cfg1[1], gxy) ||
+            !prep(pa->c2[0], 2, false, &pa->cfg2[0], gx) || !prep(pa->c2[1], 4, false, &pa->cfg2[1], gxy))
+            return false;
+    }
+
+    qai::RouteArgs& ra = pa->ra;
+    ra.rank = sh.rank; ra.nz = sh.nz; ra.ny = sh.ny; ra.nx = sh.nx;
+    ra.wpr = lay.wpr; ra.bwpr = lay.bwpr;
+    ra.q = d_q; ra.spk = la.spk; ra.nexy = la.nexy; ra.nez = la.nez; ra.out = d_out; ra.ctr = ctr;
+    ra.slist = reinterpret_cast<const int32_t*>(ws + lay.slist); ra.scap = lay.scap;
+    ra.b2bits = reinterpret_cast<uint32_t*>(ws + lay.b2bits);
+    ra.qlist = qlist; ra.qcap = lay.qcap;
+    ra.mlist = reinterpret_cast<qai::Query*>(ws + lay.mlist);
+    ra.flist = reinterpret_cast<qai::Query*>(ws + lay.flist); ra.fcap = lay.fcap;
+    ra.fmin = reinterpret_cast<int32_t*>(ws + lay.fmin);
+    ra.b2list = reinterpret_cast<int32_t*>(ws + lay.b2list); ra.b2cap = lay.b2cap;
+    ra.shell = 1;
+    ra.d2rec = nullptr;
+    ra.brute_budget = 1LL << 28;
+    ra.m = m;
+
+    qai::RowArgs& r2 = pa->r2;
+    r2.rank = sh.rank; r2.nz = sh.nz; r2.ny = sh.ny; r2.nx = sh.nx;
+    r2.q = d_q; r2.eqm = eqm; r2.s_in = s; r2.m = m;
+    r2.xw = xw;
+    r2.gate = dense;
+    qai::prepare_rowpass(r2);
+    return true;
+}
+
 qai_status check_params(const qai_params* p)
 {
     if (!std::isfinite(p->eta) || p->eta < 0) return fail(QAI_ERR_INVALID_ARG, "eta must be finite and >= 0");

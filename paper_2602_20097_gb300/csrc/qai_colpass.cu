@@ -46,7 +46,7 @@ unsigned resident_grid(K kern, dim3 block, size_t smem)
         per = 1;
     return (unsigned)(sms * per);
 }
-constexpr int kScanMax = 5;    // outward-scan fast path: rows settled within 5 rows
+constexpr int kScanMax = 24;   // outward-scan fast path: rows settled within 24 rows
 
 template <int PHASE, int IN>
 __device__ __forceinline__ int gval(uint32_t w)
@@ -128,9 +128,13 @@ __device__ __forceinline__ void emit_point(const ColArgs& a, int idx, int src, i
                     } else {
                         // a full buffer spills to the global list; should the
                         // tile fall back to the envelope path, these entries
-                        // are listed twice (the same query, the same output)
-                        const int g = atomicAdd(a.route_ctr + kCtrQueries, 1);
-                        if (g < a.qcap) a.qlist[g] = Query{idx, (val << 2) | code};
+                        // are listed twice (the same query, the same output).
+                        // Once the list is over its capacity the route hands
+                        // the field over whatever the count: no more atomics.
+                        if (*static_cast<const volatile int*>(a.route_ctr + kCtrQueries) <= a.qcap) {
+                            const int g = atomicAdd(a.route_ctr + kCtrQueries, 1);
+                            if (g < a.qcap) a.qlist[g] = Query{idx, (val << 2) | code};
+                        }
                     }
                 } else {
                     const int k = atomicAdd(qb.sn, 1);
@@ -671,20 +675,27 @@ __device__ __forceinline__ void colpass_tile(const ColArgs& a, const int blk)
 // route and the local first EDT, which mostly find nothing to do) a resident
 // grid that loops over the tiles.
 template <int PHASE, int IN, bool FINAL, bool DEBUG, bool NARROW>
-__global__ void __launch_bounds__(512, IN == 2 ? 3 : 2) k_colpass(ColArgs a)
+__device__ __forceinline__ void k_colpass_body(const ColArgs& a, const int bx, const int gx)
 {
     wait_prior_grid();
     if (!a.gate) {
-        colpass_tile<PHASE, IN, FINAL, DEBUG, NARROW>(a, blockIdx.x);
+        colpass_tile<PHASE, IN, FINAL, DEBUG, NARROW>(a, bx);
         return;
     }
     if (*static_cast<const volatile int*>(a.gate) == 0) return;  // the flag is not set
     const int tiles = ((a.C + (int)blockDim.x - 1) / (int)blockDim.x) * a.P;
-    for (int blk = blockIdx.x; blk < tiles; blk += gridDim.x) {
+    for (int blk = bx; blk < tiles; blk += gx) {
         colpass_tile<PHASE, IN, FINAL, DEBUG, NARROW>(a, blk);
         __syncthreads();
     }
 }
+
+template <int PHASE, int IN, bool FINAL, bool DEBUG, bool NARROW>
+__global__ void __launch_bounds__(512, IN == 2 ? 3 : 2) k_colpass(ColArgs a)
+{
+    k_colpass_body<PHASE, IN, FINAL, DEBUG, NARROW>(a, blockIdx.x, gridDim.x);
+}
+
 
 // The last phase-2 pass in adjoint mode (IN = 2: 2-D fields, 4: 3-D).
 template <int IN, bool NARROW>
@@ -713,10 +724,12 @@ cudaError_t go(ColArgs& a, bool debug, bool narrow, dim3 grid, dim3 block, size_
 
 bool choose_colpass(int L, int in_bytes, ColConfig* cfg, bool first_edt_last_pass)
 {
-    // 32 columns per tile suit the last pass of the first EDT (dense sites,
-    // the scan fast path, wider output rows); 16 suit the envelope-heavy
-    // passes (measured on a 512^3 field); 32 rows per band.
-    const int w = first_edt_last_pass && in_bytes == 4 ? 32 : 16;
+    // Passes over the x-pass words (in_bytes 2: the y passes) take tiles of 8
+    // columns, the z passes 32 (measured on 2-D fronts of 1800-row columns
+    // and on a 98 x 1200 x 1200 front: narrow tiles spread long columns over
+    // more CTAs, the short z columns want wide rows); 32 rows per band.
+    (void)first_edt_last_pass;
+    const int w = in_bytes == 4 ? 32 : 8;
     return choose_colpass_with(L, in_bytes, 32, w, cfg);
 }
 
@@ -770,6 +783,35 @@ cudaError_t launch_colpass(int phase, int in_bytes, bool final_pass, ColArgs& a,
     if (in_bytes == 2) return final_pass ? go<2, 2, true>(a, debug, narrow, grid, block, cfg.smem, st)
                                          : go<2, 2, false>(a, debug, narrow, grid, block, cfg.smem, st);
     return go<2, 4, true>(a, debug, narrow, grid, block, cfg.smem, st);
+}
+
+namespace {
+template <int PHASE, int IN, bool FINAL, bool NARROW>
+__global__ void __launch_bounds__(512, IN == 2 ? 3 : 2) k_colpass_group(const __grid_constant__ GroupQueue q)
+{
+    run_group<ColArgs>(q, [&](const ColArgs& a, int b, int n) { k_colpass_body<PHASE, IN, FINAL, false, NARROW>(a, b, n); });
+}
+}  // namespace
+
+cudaError_t launch_group_colpass(const GroupQueue& q, int phase, int in_bytes, bool final_pass, bool narrow, int W,
+                                 int B, size_t smem, cudaStream_t st)
+{
+    const dim3 block(W, B);
+    auto run = [&](auto kern) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        const int grid = std::min(group_total(q), persistent_grid(kern, W * B, smem));
+        if (grid < 1) return cudaSuccess;
+        return launch_chained(kern, dim3(grid), block, smem, st, q);
+    };
+#define QAI_COLG(P, I, F) (narrow ? run(k_colpass_group<P, I, F, true>) : run(k_colpass_group<P, I, F, false>))
+    if (phase == 1) {
+        if (in_bytes == 2) return final_pass ? QAI_COLG(1, 2, true) : QAI_COLG(1, 2, false);
+        return QAI_COLG(1, 4, true);
+    }
+    if (in_bytes == 2) return final_pass ? QAI_COLG(2, 2, true) : QAI_COLG(2, 2, false);
+    return QAI_COLG(2, 4, true);
+#undef QAI_COLG
 }
 
 }  // namespace qai

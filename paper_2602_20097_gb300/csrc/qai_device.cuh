@@ -230,6 +230,59 @@ struct RowTable {
     RowArgs args[kMaxGroup];
 };
 
+// Persistent grouped launches (the batched form): one launch runs one
+// kernel body over several fields. Field f gets vb[f] virtual blocks (the
+// grid it would get alone, or a share of it); a field whose gate reads 0 when
+// the launch starts gets none (the gates are flags that earlier launches set
+// and no body of this launch changes). The resident CTAs take virtual blocks
+// from a device cursor, in field order, until none is left, and run the body
+// with the field's arguments (a device array) and the virtual block index and
+// count in place of blockIdx.x and gridDim.x. The bodies do not depend on
+// which CTA runs a virtual block, nor on a field's virtual blocks running at
+// the same time.
+constexpr int kGroupMax = 64;
+struct GroupQueue {
+    int n;                         // fields
+    int* cursor;                   // next virtual block (zeroed before the launch)
+    const void* args;              // the fields' argument structs, device memory
+    int vb[kGroupMax];             // virtual blocks of each field
+    const int* gate[kGroupMax];    // NULL, or the field runs only if *gate != 0
+};
+
+template <class Args, class Body>
+__device__ __forceinline__ void run_group(const GroupQueue& q, Body&& body)
+{
+    __shared__ int s_first[kGroupMax + 1];
+    __shared__ int s_item;
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nthr = blockDim.x * blockDim.y * blockDim.z;
+    wait_prior_grid();  // the gates and the fields' inputs come from earlier launches
+    for (int f = tid; f < q.n; f += nthr)
+        s_first[f + 1] = (!q.gate[f] || *static_cast<const volatile int*>(q.gate[f]) != 0) ? q.vb[f] : 0;
+    __syncthreads();
+    if (tid == 0) {
+        s_first[0] = 0;
+        for (int f = 1; f <= q.n; ++f) s_first[f] += s_first[f - 1];
+    }
+    __syncthreads();
+    const int total = s_first[q.n];
+    for (;;) {
+        if (tid == 0) s_item = total > 0 ? atomicAdd(q.cursor, 1) : total;
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();  // s_item is read before the next item overwrites it
+        if (it >= total) return;
+        int lo = 0, hi = q.n - 1;  // the last field starting at or before it (never an empty one)
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_first[mid] <= it) lo = mid;
+            else hi = mid - 1;
+        }
+        const Args a = static_cast<const Args*>(q.args)[lo];
+        body(a, it - s_first[lo], s_first[lo + 1] - s_first[lo]);
+    }
+}
+
 // A float-float value hi + lo: the sum of two of them keeps the rounding
 // error of hi + hi' exactly (Knuth's two-sum), so a tree of such sums loses
 // no more than a few units of 2^-44 of its magnitude without FP64 work.

@@ -8,6 +8,7 @@
 
 #include "qai.h"
 #include "qai_device.cuh"
+#include "qai_launch.h"
 
 namespace qai {
 namespace host {
@@ -49,6 +50,22 @@ cudaError_t timed_call(const char* name, double algo_bytes, cudaStream_t st, con
 // validated shape and a workspace laid out by layout_for(sh, 0).
 qai_status run_plain(const int32_t* d_q, float* d_out, const Shape& sh, const MethodArgs& m, char* ws,
                      const Layout& lay, cudaStream_t st);
+
+// The argument structs of a plain call's kernels on one rank-2 or rank-3
+// field (step A, the local first EDT with its separable fallback, the
+// signed-point route with the dense second EDT behind it), as run_plain
+// launches them, for the batched form's grouped launches. The route counters
+// live at `ctr`. Column passes: c1[0] / c2[0] along y, c1[1] / c2[1] along z
+// (rank 3), prepared for the plain call's tiles (cfg1 / cfg2).
+struct PlainArgs {
+    LocalArgs la;
+    RouteArgs ra;
+    RowArgs r1, r2;
+    ColArgs c1[2], c2[2];
+    ColConfig cfg1[2], cfg2[2];
+};
+bool plain_args(const int32_t* d_q, float* d_out, const Shape& sh, const MethodArgs& m, char* ws,
+                const Layout& lay, int* ctr, PlainArgs* pa);
 
 // While alive, the library's launches on this host thread are counted into
 // *counter and not timed or counted globally (launches recorded into a graph).

@@ -104,6 +104,44 @@ cudaError_t launch_add_dprime(const float* dprime, float* out, int64_t n, cudaSt
 cudaError_t launch_partials_sum(const double* partials, int nblocks, double eb, double eta,
                                 double* grad_params, cudaStream_t st);
 
+// CTAs of `kern` resident on the device at once (at least one per SM): the
+// grid of a persistent grouped launch.
+template <class K>
+int persistent_grid(K kern, int threads, size_t smem)
+{
+    int dev = 0, sms = 152, per = 1;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, smem) != cudaSuccess || per < 1) per = 1;
+    return sms * per;
+}
+inline int group_total(const GroupQueue& q)
+{
+    int t = 0;
+    for (int f = 0; f < q.n; ++f) t += q.vb[f];
+    return t;
+}
+
+// Persistent grouped launches (the batched form; see GroupQueue): q.args
+// holds one argument struct per field, of the type the kernel takes; fields
+// of both ranks (and load widths) share a launch, the body instance picked
+// per work item. LocalArgs: step A (mode as k_detect's), the nearest-site
+// search, the byte maps, the packed S.
+cudaError_t launch_group_detect(const GroupQueue& q, int mode, cudaStream_t st);
+cudaError_t launch_group_near(const GroupQueue& q, cudaStream_t st);
+cudaError_t launch_group_expand(const GroupQueue& q, int mode, cudaStream_t st);
+cudaError_t launch_group_pack_s(const GroupQueue& q, int gated, cudaStream_t st);
+// RouteArgs: the signed-point route's kernels.
+enum RouteKernel { kRouteB2Sparse, kRouteBruteSparse, kRouteB2Map, kRouteQuery, kRouteQueryMid, kRouteB2List,
+                   kRouteBrute };
+cudaError_t launch_group_route(RouteKernel k, const GroupQueue& q, cudaStream_t st);
+// RowArgs (rank 2 and 3, non-final): warps per CTA and the largest x extent.
+cudaError_t launch_group_rowpass(const GroupQueue& q, int phase, int warps, int max_nx, cudaStream_t st);
+// ColArgs prepared for a (W, B) tile: every field of the launch shares W, B,
+// the phase, the input words, finality and narrow arithmetic; smem covers the
+// longest line.
+cudaError_t launch_group_colpass(const GroupQueue& q, int phase, int in_bytes, bool final_pass, bool narrow, int W,
+                                 int B, size_t smem, cudaStream_t st);
+
 // Records `msg` as qai_last_error() of the calling host thread.
 void set_last_error(const char* msg);
 

@@ -26,7 +26,9 @@
 //             there take its code. Queries of the second EDT (S != 0 off B1)
 //             go to the query list with Dist1.
 //
-// A point with no B1 point within that ball sets kCtrLocalFail; the separable
+// A point with no B1 point within that ball (or, in 2-D, a warp whose words
+// needed the search past squared distance 1 more often than one in 16) sets
+// kCtrLocalFail and ends that warp's searches past squared distance 1; the separable
 // first EDT (row pass 1, column passes 1) then runs and rewrites all of it,
 // and k_pack_s packs its S map for the route. k_expand writes the byte maps
 // (equal-q mask, S) that the separable second EDT and the adjoint read.
@@ -351,7 +353,7 @@ __device__ __forceinline__ void flush_signed(const LocalArgs& a, const SignedBuf
 }
 
 template <int RANK, bool VEC>
-__global__ void __launch_bounds__(256, QAI_DETECT_MINB) k_detect(LocalArgs a, int mode)
+__device__ __forceinline__ void k_detect_body(const LocalArgs& a, int mode, const int bx, const int gx)
 {
     __shared__ int32_t sbuf[kSignedCta];
     __shared__ int sn, sbase;
@@ -361,10 +363,10 @@ __global__ void __launch_bounds__(256, QAI_DETECT_MINB) k_detect(LocalArgs a, in
     __syncthreads();
     const SignedBuf sb{sbuf, &sn, kSignedCta};
     const int rows = a.nz * a.ny;
-    const int wstride = gridDim.x * (blockDim.x >> 5);
+    const int wstride = gx * (blockDim.x >> 5);
     const int lx = 4 * (int)(threadIdx.x & 31);
     bool wide = false;
-    for (int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += wstride) {
+    for (int row = bx * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += wstride) {
         const int z = RANK == 3 ? row / a.ny : 0;
         const int y = row - z * a.ny;
         const bool row_inner = y >= 1 && y <= a.ny - 2 && (RANK == 2 || (z >= 1 && z <= a.nz - 2));
@@ -391,10 +393,17 @@ __global__ void __launch_bounds__(256, QAI_DETECT_MINB) k_detect(LocalArgs a, in
         __syncthreads();
         if (threadIdx.x == 0) {
             if (sn) atomicAdd(a.ctr + kCtrSignedExact, sn);
-            if (blockIdx.x == 0) *static_cast<volatile int*>(a.ctr + kCtrSignedOver) = 1;
+            if (bx == 0) *static_cast<volatile int*>(a.ctr + kCtrSignedOver) = 1;
         }
     }
 }
+
+template <int RANK, bool VEC>
+__global__ void __launch_bounds__(256, QAI_DETECT_MINB) k_detect(LocalArgs a, int mode)
+{
+    k_detect_body<RANK, VEC>(a, mode, blockIdx.x, gridDim.x);
+}
+
 
 // ---- step A for 3-D fields on tiles staged by the tensor memory accelerator
 //
@@ -551,9 +560,8 @@ __device__ __forceinline__ uint32_t pshift(const uint32_t* m, int64_t prow, int 
 
 // The CTA's queries to the global list (one atomic), and the flag of a point
 // with no B1 point within reach.
-__device__ __forceinline__ void near_flush(const LocalArgs& a, const Query* qbuf, const int* qn, int* qbase, bool fail)
+__device__ __forceinline__ void near_flush(const LocalArgs& a, const Query* qbuf, const int* qn, int* qbase)
 {
-    if (__any_sync(kFull, fail) && (threadIdx.x & 31) == 0) *static_cast<volatile int*>(a.ctr + kCtrLocalFail) = 1;
     __syncthreads();
     const int n = min(*qn, kQueryCta);
     if (threadIdx.x == 0) *qbase = n > 0 ? atomicAdd(a.ctr + kCtrQueries, n) : 0;
@@ -589,7 +597,7 @@ __device__ __forceinline__ int deep_r2(const LocalArgs& a, int z, int y, int x)
 constexpr int kNearRows = 4;
 
 template <int RANK>
-__global__ void __launch_bounds__(256, QAI_NEAR_MINB) k_near(LocalArgs a)
+__device__ __forceinline__ void k_near_body(const LocalArgs& a, const int bx, const int gx)
 {
     wait_prior_grid();
     __shared__ Query qbuf[kQueryCta];
@@ -601,11 +609,19 @@ __global__ void __launch_bounds__(256, QAI_NEAR_MINB) k_near(LocalArgs a)
     const uint32_t* cm = a.codes;
     const int yb = (a.ny + kNearRows - 1) / kNearRows;
     const int items = a.nz * yb;
-    const int wstride = gridDim.x * (blockDim.x >> 5);
+    const int wstride = gx * (blockDim.x >> 5);
     const int* tab = RANK == 3 ? c_near.off3 : c_near.off2;
     constexpr int n1 = RANK == 3 ? 6 : 4, ntab = RANK == 3 ? kNearN3 : kNearN2;
-    bool fail = false;
-    for (int it = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < items; it += wstride) {
+    // A warp gives up -- sets the flag, after which the separable passes
+    // redo every output, and skips its remaining searches past squared
+    // distance 1 -- at a point without a site within reach, or (2-D fields,
+    // whose separable passes are cheap next to a wide search) when more than
+    // one in 16 of the words it has looked at (plus 16) needed such a
+    // search. The loop reads no shared state, so nothing stalls the loads it
+    // issues up front (warps of a field that fails meet either test soon).
+    bool fail = false;  // warp-uniform
+    int seen = 0, deep = 0;  // warp-uniform: words looked at, words searched past squared distance 1
+    for (int it = bx * (blockDim.x >> 5) + (threadIdx.x >> 5); it < items; it += wstride) {
         const int z = RANK == 3 ? it / yb : 0;
         const int y0 = (it - z * yb) * kNearRows;
         const int row0 = z * a.ny + y0;
@@ -633,6 +649,7 @@ __global__ void __launch_bounds__(256, QAI_NEAR_MINB) k_near(LocalArgs a)
                 if (y >= a.ny) break;  // warp-uniform
                 const int row = row0 + i;
                 const uint32_t w = wy[i + 1];
+                if (RANK == 2) seen += min(32, wpr - ks);
                 const uint32_t site = field_lsb(w);
                 uint32_t need = ~site & 0x55555555u & valid;  // points off B1
                 uint32_t s = w - site;                        // B1: the code less one is S_B
@@ -665,8 +682,21 @@ __global__ void __launch_bounds__(256, QAI_NEAR_MINB) k_near(LocalArgs a)
                     }
                     const uint32_t at1 = need0 & ~need;  // resolved at squared distance 1
                     // squared distances 2..8: the words with a point left, one
-                    // at a time, searched by the warp
-                    for (unsigned needy = __ballot_sync(kFull, need != 0); needy; needy &= needy - 1) {
+                    // at a time, searched by the warp -- within a budget of
+                    // such words for the field (one in 16), past which the
+                    // separable passes are the cheaper first EDT
+                    unsigned needy = __ballot_sync(kFull, need != 0);
+                    if (needy) {
+                        if (RANK == 2) {
+                            deep += __popc(needy);
+                            if (!fail && 16 * deep > seen + 256) {
+                                if (lane == 0) *static_cast<volatile int*>(a.ctr + kCtrLocalFail) = 1;
+                                fail = true;
+                            }
+                        }
+                        if (fail) needy = 0;
+                    }
+                    for (; needy; needy &= needy - 1) {
                         const int src = __ffs(needy) - 1;
                         const int kk = __shfl_sync(kFull, k, src);
                         uint32_t nd = __shfl_sync(kFull, need, src);
@@ -705,7 +735,10 @@ __global__ void __launch_bounds__(256, QAI_NEAR_MINB) k_near(LocalArgs a)
                             need = nd;
                         }
                     }
-                    fail |= need != 0;
+                    if (!fail && __any_sync(kFull, need != 0)) {
+                        if (lane == 0) *static_cast<volatile int*>(a.ctr + kCtrLocalFail) = 1;
+                        fail = true;
+                    }
                     const uint32_t resolved = need0 & ~need;
                     const uint32_t soff = res - resolved;  // the site's code less one: S
                     s |= soff;
@@ -722,7 +755,8 @@ __global__ void __launch_bounds__(256, QAI_NEAR_MINB) k_near(LocalArgs a)
                         const int kq = atomicAdd(&qn, 1);
                         if (kq < kQueryCta) {
                             qbuf[kq] = qe;
-                        } else {
+                        } else if (*static_cast<const volatile int*>(a.ctr + kCtrQueries) <= a.qcap) {
+                            // past the list's capacity the route hands over: no more atomics
                             const int g = atomicAdd(a.ctr + kCtrQueries, 1);
                             if (g < a.qcap) a.qlist[g] = qe;
                         }
@@ -732,8 +766,15 @@ __global__ void __launch_bounds__(256, QAI_NEAR_MINB) k_near(LocalArgs a)
             }
         }
     }
-    near_flush(a, qbuf, &qn, &qbase, fail);
+    near_flush(a, qbuf, &qn, &qbase);
 }
+
+template <int RANK>
+__global__ void __launch_bounds__(256, QAI_NEAR_MINB) k_near(LocalArgs a)
+{
+    k_near_body<RANK>(a, blockIdx.x, gridDim.x);
+}
+
 
 // The byte maps of the separable passes from q and the packed S: the equal-q
 // mask with the sign code of S_B (row pass 1's eqm) and S as int8, after the
@@ -741,7 +782,7 @@ __global__ void __launch_bounds__(256, QAI_NEAR_MINB) k_near(LocalArgs a)
 // 1: only when the separable second EDT takes over (the dense flag set);
 // mode 2: always (the adjoint reads them).
 template <int RANK, bool VEC>
-__global__ void __launch_bounds__(256) k_expand(LocalArgs a, int mode)
+__device__ __forceinline__ void k_expand_body(const LocalArgs& a, int mode, const int bx, const int gx)
 {
     wait_prior_grid();
     {
@@ -749,9 +790,9 @@ __global__ void __launch_bounds__(256) k_expand(LocalArgs a, int mode)
         if (ctr[kCtrLocalFail] != 0 || (mode == 1 && ctr[kCtrDense] == 0)) return;
     }
     const int rows = a.nz * a.ny;
-    const int wstride = gridDim.x * (blockDim.x >> 5);
+    const int wstride = gx * (blockDim.x >> 5);
     const int lx = 4 * (int)(threadIdx.x & 31);
-    for (int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += wstride) {
+    for (int row = bx * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += wstride) {
         const int z = RANK == 3 ? row / a.ny : 0;
         const int y = row - z * a.ny;
         const int64_t rbase = (int64_t)row * a.nx;
@@ -774,15 +815,22 @@ __global__ void __launch_bounds__(256) k_expand(LocalArgs a, int mode)
     }
 }
 
+template <int RANK, bool VEC>
+__global__ void __launch_bounds__(256) k_expand(LocalArgs a, int mode)
+{
+    k_expand_body<RANK, VEC>(a, mode, blockIdx.x, gridDim.x);
+}
+
+
 // The packed S from the int8 S map of the separable first EDT (gated: when
 // the local first EDT fell short; else always).
-__global__ void __launch_bounds__(256) k_pack_s(LocalArgs a, int gated)
+__device__ __forceinline__ void k_pack_s_body(const LocalArgs& a, int gated, const int bx, const int gx)
 {
     wait_prior_grid();
     if (gated && *static_cast<const volatile int*>(a.ctr + kCtrLocalFail) == 0) return;
     const int64_t words = (int64_t)a.nz * a.ny * a.wpr;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += stride) {
+    const int64_t stride = (int64_t)gx * blockDim.x;
+    for (int64_t i = (int64_t)bx * blockDim.x + threadIdx.x; i < words; i += stride) {
         const int64_t row = i / a.wpr;
         const int x0 = 16 * (int)(i - row * a.wpr);
         const int8_t* sr = a.s + row * a.nx;
@@ -794,6 +842,12 @@ __global__ void __launch_bounds__(256) k_pack_s(LocalArgs a, int gated)
         a.spk[i] = w;
     }
 }
+
+__global__ void __launch_bounds__(256) k_pack_s(LocalArgs a, int gated)
+{
+    k_pack_s_body(a, gated, blockIdx.x, gridDim.x);
+}
+
 
 // The host-memory pipeline's last step: step A's slabs went to the host as
 // soon as they were written; the outputs that changed after it go straight
@@ -968,6 +1022,74 @@ cudaError_t launch_host_fixup(const LocalArgs& a, float* h_out_mapped, cudaStrea
 cudaError_t launch_local_pack_s(const LocalArgs& a, bool gated, cudaStream_t st)
 {
     return launch_chained(k_pack_s, dim3(one_wave(k_pack_s)), dim3(256), 0, st, a, gated ? 1 : 0);
+}
+
+namespace {
+// Grouped kernels over fields of either rank (and either load width): the
+// body instance is picked per work item from the field's arguments.
+__global__ void __launch_bounds__(256, QAI_DETECT_MINB) k_detect_group(const __grid_constant__ GroupQueue q, int mode)
+{
+    run_group<LocalArgs>(q, [&](const LocalArgs& a, int b, int n) {
+        if (a.rank == 3) {
+            if (a.vec) k_detect_body<3, true>(a, mode, b, n);
+            else k_detect_body<3, false>(a, mode, b, n);
+        } else {
+            if (a.vec) k_detect_body<2, true>(a, mode, b, n);
+            else k_detect_body<2, false>(a, mode, b, n);
+        }
+    });
+}
+
+__global__ void __launch_bounds__(256, QAI_NEAR_MINB) k_near_group(const __grid_constant__ GroupQueue q)
+{
+    run_group<LocalArgs>(q, [&](const LocalArgs& a, int b, int n) {
+        if (a.rank == 3) k_near_body<3>(a, b, n);
+        else k_near_body<2>(a, b, n);
+    });
+}
+
+__global__ void __launch_bounds__(256) k_expand_group(const __grid_constant__ GroupQueue q, int mode)
+{
+    run_group<LocalArgs>(q, [&](const LocalArgs& a, int b, int n) {
+        if (a.rank == 3) {
+            if (a.vec) k_expand_body<3, true>(a, mode, b, n);
+            else k_expand_body<3, false>(a, mode, b, n);
+        } else {
+            if (a.vec) k_expand_body<2, true>(a, mode, b, n);
+            else k_expand_body<2, false>(a, mode, b, n);
+        }
+    });
+}
+
+__global__ void __launch_bounds__(256) k_pack_s_group(const __grid_constant__ GroupQueue q, int gated)
+{
+    run_group<LocalArgs>(q, [&](const LocalArgs& a, int b, int n) { k_pack_s_body(a, gated, b, n); });
+}
+
+template <class K, class... A>
+cudaError_t run_grouped(K kern, const GroupQueue& q, cudaStream_t st, A... extra)
+{
+    const int grid = std::min(group_total(q), persistent_grid(kern, 256, 0));
+    if (grid < 1) return cudaSuccess;
+    return launch_chained(kern, dim3(grid), dim3(256), 0, st, q, extra...);
+}
+}  // namespace
+
+cudaError_t launch_group_detect(const GroupQueue& q, int mode, cudaStream_t st)
+{
+    return run_grouped(k_detect_group, q, st, mode);
+}
+
+cudaError_t launch_group_near(const GroupQueue& q, cudaStream_t st) { return run_grouped(k_near_group, q, st); }
+
+cudaError_t launch_group_expand(const GroupQueue& q, int mode, cudaStream_t st)
+{
+    return run_grouped(k_expand_group, q, st, mode);
+}
+
+cudaError_t launch_group_pack_s(const GroupQueue& q, int gated, cudaStream_t st)
+{
+    return run_grouped(k_pack_s_group, q, st, gated);
 }
 
 }  // namespace qai

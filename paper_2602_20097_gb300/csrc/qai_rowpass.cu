@@ -363,7 +363,7 @@ __device__ __forceinline__ void rowpass_row(const RowArgs& a, const int row, uns
 }
 
 template <int PHASE, int RANK, bool FINAL, bool DEBUG, bool VEC>
-__global__ void __launch_bounds__(256) k_rowpass(RowArgs a)
+__device__ __forceinline__ void k_rowpass_body(const RowArgs& a, const int bx, const int gx)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     wait_prior_grid();
@@ -371,16 +371,23 @@ __global__ void __launch_bounds__(256) k_rowpass(RowArgs a)
     if (a.gate && *static_cast<const volatile int*>(a.gate) == 0) return;
     // row pass 1 of the route starts its counters again (not the timeout and
     // local-EDT flags)
-    if (PHASE == 1 && a.route_ctr && blockIdx.x == 0 && threadIdx.x < kCtrTimeout)
+    if (PHASE == 1 && a.route_ctr && bx == 0 && threadIdx.x < kCtrTimeout)
         a.route_ctr[threadIdx.x] = 0;
     const int warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
     // one row per warp, or (a grid smaller than the rows: the dense second EDT
     // behind the signed-point route) a loop over them; only warp-level sync
-    for (int row = blockIdx.x * warps + warp; row < a.nz * a.ny; row += gridDim.x * warps) {
+    for (int row = bx * warps + warp; row < a.nz * a.ny; row += gx * warps) {
         rowpass_row<PHASE, RANK, FINAL, DEBUG, VEC>(a, row, smem + (size_t)warp * smem_per_warp(a.nx));
         __syncwarp();
     }
 }
+
+template <int PHASE, int RANK, bool FINAL, bool DEBUG, bool VEC>
+__global__ void __launch_bounds__(256) k_rowpass(RowArgs a)
+{
+    k_rowpass_body<PHASE, RANK, FINAL, DEBUG, VEC>(a, blockIdx.x, gridDim.x);
+}
+
 
 // Several fields in one launch: global row g belongs to field f with
 // first_row[f] <= g < first_row[f + 1]; the table travels by value.
@@ -463,6 +470,37 @@ cudaError_t launch_rowpass_grouped(int phase, bool final_pass, const RowTable& t
     }
     if (final_pass) return run(k_rowpass_grouped<2, 1, true>);
     return rank == 2 ? run(k_rowpass_grouped<2, 2, false>) : run(k_rowpass_grouped<2, 3, false>);
+}
+
+namespace {
+// Grouped row passes of rank-2 and rank-3 fields (non-final): the body
+// instance is picked per work item from the field's arguments.
+template <int PHASE>
+__global__ void __launch_bounds__(256) k_rowpass_group(const __grid_constant__ GroupQueue q)
+{
+    run_group<RowArgs>(q, [&](const RowArgs& a, int b, int n) {
+        if (a.rank == 3) {
+            if (a.vec) k_rowpass_body<PHASE, 3, false, false, true>(a, b, n);
+            else k_rowpass_body<PHASE, 3, false, false, false>(a, b, n);
+        } else {
+            if (a.vec) k_rowpass_body<PHASE, 2, false, false, true>(a, b, n);
+            else k_rowpass_body<PHASE, 2, false, false, false>(a, b, n);
+        }
+    });
+}
+}  // namespace
+
+cudaError_t launch_group_rowpass(const GroupQueue& q, int phase, int warps, int max_nx, cudaStream_t st)
+{
+    const size_t smem = rowpass_smem(max_nx, warps);
+    auto run = [&](auto kern) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        const int grid = std::min(group_total(q), persistent_grid(kern, 32 * warps, smem));
+        if (grid < 1) return cudaSuccess;
+        return launch_chained(kern, dim3(grid), dim3(32 * warps), smem, st, q);
+    };
+    return phase == 1 ? run(k_rowpass_group<1>) : run(k_rowpass_group<2>);
 }
 
 cudaError_t launch_rowpass(int phase, bool final_pass, const RowArgs& a_in, bool debug, cudaStream_t st)

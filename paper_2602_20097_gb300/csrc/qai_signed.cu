@@ -129,7 +129,7 @@ constexpr int kMapRows = 4;
 // word is written (the bitmap is not cleared between calls). Nothing to do
 // without queries.
 template <int RANK>
-__global__ void __launch_bounds__(256, 3) k_b2map(RouteArgs a)
+__device__ __forceinline__ void k_b2map_body(const RouteArgs& a, const int bx, const int gx)
 {
     wait_prior_grid();
     const volatile int* ctr = a.ctr;
@@ -139,9 +139,9 @@ __global__ void __launch_bounds__(256, 3) k_b2map(RouteArgs a)
     const bool literal = a.m.b2_rule == 1;
     const int yb = (a.ny + kMapRows - 1) / kMapRows;
     const int items = a.nz * yb;
-    const int wstride = gridDim.x * (blockDim.x >> 5);
+    const int wstride = gx * (blockDim.x >> 5);
     constexpr uint32_t kLo = 0x55555555u;
-    for (int it = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < items; it += wstride) {
+    for (int it = bx * (blockDim.x >> 5) + (threadIdx.x >> 5); it < items; it += wstride) {
         const int z = RANK == 3 ? it / yb : 0;
         const int y0 = (it - z * yb) * kMapRows;
         const int64_t row0 = (int64_t)z * a.ny + y0;
@@ -230,6 +230,13 @@ __global__ void __launch_bounds__(256, 3) k_b2map(RouteArgs a)
     }
 }
 
+template <int RANK>
+__global__ void __launch_bounds__(256, 3) k_b2map(RouteArgs a)
+{
+    k_b2map_body<RANK>(a, blockIdx.x, gridDim.x);
+}
+
+
 // Bitmap bits x0 .. x0 + 63 of row `prow` (0 outside the row).
 __device__ __forceinline__ uint64_t bwin64(const RouteArgs& a, int64_t prow, int x0)
 {
@@ -262,7 +269,7 @@ struct LeftBuf {
 };
 
 template <int RANK>
-__global__ void __launch_bounds__(256) k_query(RouteArgs a)
+__device__ __forceinline__ void k_query_body(const RouteArgs& a, const int bx, const int gx)
 {
     wait_prior_grid();
     volatile int* ctr = a.ctr;
@@ -272,7 +279,7 @@ __global__ void __launch_bounds__(256) k_query(RouteArgs a)
     __shared__ int mn, mbase;
     if (threadIdx.x == 0) mn = 0;
     __syncthreads();
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += gridDim.x * blockDim.x) {
+    for (int i = bx * blockDim.x + threadIdx.x; i < nq; i += gx * blockDim.x) {
         const Query e = a.qlist[i];
         int found = 0x7FFFFFFF;
         if (a.shell) {
@@ -309,20 +316,27 @@ __global__ void __launch_bounds__(256) k_query(RouteArgs a)
     for (int j = threadIdx.x; j < n && mbase + j < a.qcap; j += blockDim.x) a.mlist[mbase + j] = mbuf[j];
 }
 
+template <int RANK>
+__global__ void __launch_bounds__(256) k_query(RouteArgs a)
+{
+    k_query_body<RANK>(a, blockIdx.x, gridDim.x);
+}
+
+
 // Second phase: one warp per query; the lanes take the bitmap rows within
 // radius R, each row's nearest bit to x in the window x - R .. x + R.
 template <int RANK>
-__global__ void __launch_bounds__(256) k_query_mid(RouteArgs a)
+__device__ __forceinline__ void k_query_mid_body(const RouteArgs& a, const int bx, const int gx)
 {
     wait_prior_grid();
     volatile int* ctr = a.ctr;
     if (ctr[kCtrDense] || !ctr[kCtrBitmap]) return;
     const int nm = min((int)ctr[kCtrMid], a.qcap);
     const int lane = threadIdx.x & 31;
-    const int wstride = gridDim.x * (blockDim.x >> 5);
+    const int wstride = gx * (blockDim.x >> 5);
     constexpr int R = RANK == 3 ? kMidR3 : kMidR2;
     constexpr int nrows = RANK == 3 ? kRows3 : 2 * kMidR2 + 1;
-    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < nm; i += wstride) {
+    for (int i = bx * (blockDim.x >> 5) + (threadIdx.x >> 5); i < nm; i += wstride) {
         const Query e = a.mlist[i];
         int best = 0x7FFFFFFF;
         if (a.shell) {
@@ -353,11 +367,18 @@ __global__ void __launch_bounds__(256) k_query_mid(RouteArgs a)
     }
 }
 
+template <int RANK>
+__global__ void __launch_bounds__(256) k_query_mid(RouteArgs a)
+{
+    k_query_mid_body<RANK>(a, blockIdx.x, gridDim.x);
+}
+
+
 // The B2 sites, listed from the bitmap (only when some query is left to
 // the search over them): one thread per bitmap word, warp-aggregated appends
 // into a per-CTA buffer, one global atomic per CTA.
 constexpr int kSiteBuf = 2048;
-__global__ void __launch_bounds__(256) k_b2list(RouteArgs a)
+__device__ __forceinline__ void k_b2list_body(const RouteArgs& a, const int bx, const int gx)
 {
     wait_prior_grid();
     volatile int* ctr = a.ctr;
@@ -371,9 +392,9 @@ __global__ void __launch_bounds__(256) k_b2list(RouteArgs a)
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t words = (int64_t)a.nz * a.ny * a.bwpr;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t stride = (int64_t)gx * blockDim.x;
     uint2* glist = reinterpret_cast<uint2*>(a.b2list);
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < words; base += stride) {
+    for (int64_t base = (int64_t)bx * blockDim.x; base < words; base += stride) {
         const int64_t i = base + threadIdx.x;
         uint32_t w = i < words ? __ldg(a.b2bits + i) : 0u;
         const int cnt = __popc(w);
@@ -411,6 +432,12 @@ __global__ void __launch_bounds__(256) k_b2list(RouteArgs a)
     __syncthreads();
     for (int i = threadIdx.x; i < n && sbase + i < a.b2cap; i += blockDim.x) glist[sbase + i] = sbuf[i];
 }
+
+__global__ void __launch_bounds__(256) k_b2list(RouteArgs a)
+{
+    k_b2list_body(a, blockIdx.x, gridDim.x);
+}
+
 
 // S code (0, 1: +1, 2: -1) of point (x, y, z) from the packed S map; 0
 // outside the field.
@@ -462,24 +489,24 @@ __device__ __forceinline__ bool is_b2(const RouteArgs& a, int x, int y, int z, i
 // bitmap route.
 constexpr int kSparseBuf = 2048;
 template <int RANK>
-__global__ void __launch_bounds__(256) k_b2sparse(RouteArgs a)
+__device__ __forceinline__ void k_b2sparse_body(const RouteArgs& a, const int bx, const int gx)
 {
     wait_prior_grid();
     volatile int* ctr = a.ctr;
     if (ctr[kCtrDense]) return;
     const int nq = ctr[kCtrQueries];
     if (nq > a.qcap) {  // the query list is incomplete: the dense route takes over
-        if (blockIdx.x == 0 && threadIdx.x == 0) ctr[kCtrDense] = 1;
+        if (bx == 0 && threadIdx.x == 0) ctr[kCtrDense] = 1;
         return;
     }
     if (nq == 0) return;  // no point needs Dist2
     const int ns = ctr[kCtrSigned];
     if (ctr[kCtrSignedOver] || ns > a.scap || !a.shell || nq > a.fcap) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) ctr[kCtrBitmap] = 1;
+        if (bx == 0 && threadIdx.x == 0) ctr[kCtrBitmap] = 1;
         return;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctr[kCtrUnresolved] = nq;  // every query takes the site search
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += gridDim.x * blockDim.x) a.fmin[i] = kDistInf;
+    if (bx == 0 && threadIdx.x == 0) ctr[kCtrUnresolved] = nq;  // every query takes the site search
+    for (int i = bx * blockDim.x + threadIdx.x; i < nq; i += gx * blockDim.x) a.fmin[i] = kDistInf;
     __shared__ uint2 sbuf[kSparseBuf];
     __shared__ int sn, sfull, sbase;
     if (threadIdx.x == 0) {
@@ -491,7 +518,7 @@ __global__ void __launch_bounds__(256) k_b2sparse(RouteArgs a)
     const int plane = a.ny * a.nx;
     uint2* glist = reinterpret_cast<uint2*>(a.b2list);
     const int items = ns + nq;
-    for (int base = blockIdx.x * blockDim.x; base < items; base += gridDim.x * blockDim.x) {
+    for (int base = bx * blockDim.x; base < items; base += gx * blockDim.x) {
         const int item = base + threadIdx.x;
         uint2 found[1 + 2 * RANK];
         int nfound = 0;
@@ -568,6 +595,13 @@ __global__ void __launch_bounds__(256) k_b2sparse(RouteArgs a)
     for (int i = threadIdx.x; i < n && sbase + i < a.b2cap; i += blockDim.x) glist[sbase + i] = sbuf[i];
 }
 
+template <int RANK>
+__global__ void __launch_bounds__(256) k_b2sparse(RouteArgs a)
+{
+    k_b2sparse_body<RANK>(a, blockIdx.x, gridDim.x);
+}
+
+
 // Exact Dist2 of queries by a search over every listed B2 site: all queries
 // (sparse: the sparse route) or those the shell phases left (the bitmap
 // route). CTA i takes 256 queries (block i % qb) against one slice of the
@@ -576,7 +610,7 @@ __global__ void __launch_bounds__(256) k_b2sparse(RouteArgs a)
 // outputs. Over the budget, the sparse route hands over to the bitmap route
 // and the bitmap route to the dense second EDT.
 constexpr int kBruteChunk = 1024;
-__global__ void __launch_bounds__(256) k_brute(RouteArgs a, int sparse)
+__device__ __forceinline__ void k_brute_body(const RouteArgs& a, int sparse, const int bx, const int gx)
 {
     wait_prior_grid();
     volatile int* ctr = a.ctr;
@@ -586,8 +620,8 @@ __global__ void __launch_bounds__(256) k_brute(RouteArgs a, int sparse)
     const int nf = sparse ? ctr[kCtrQueries] : ctr[kCtrUnresolved];
     const int nb = ctr[kCtrB2];
     const int qblocks = (nf + blockDim.x - 1) / blockDim.x;
-    if (nf > a.fcap || nb > a.b2cap || (long long)nf * nb > a.brute_budget || qblocks > (int)gridDim.x) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (nf > a.fcap || nb > a.b2cap || (long long)nf * nb > a.brute_budget || qblocks > (int)gx) {
+        if (bx == 0 && threadIdx.x == 0) {
             if (sparse) {  // the bitmap route starts its own counts
                 ctr[kCtrUnresolved] = 0;
                 ctr[kCtrB2] = 0;
@@ -604,8 +638,8 @@ __global__ void __launch_bounds__(256) k_brute(RouteArgs a, int sparse)
     const uint2* list = reinterpret_cast<const uint2*>(a.b2list);
     const int plane = a.ny * a.nx;
     const int qb = qblocks;
-    const int slices = max(1, (int)gridDim.x / qb);
-    const int qblk = blockIdx.x % qb, slice = blockIdx.x / qb;
+    const int slices = max(1, (int)gx / qb);
+    const int qblk = bx % qb, slice = bx / qb;
     if (slice < slices) {
         const int per = (nb + slices - 1) / slices;
         const int b0 = min(nb, slice * per), b1 = min(nb, b0 + per);
@@ -635,7 +669,7 @@ __global__ void __launch_bounds__(256) k_brute(RouteArgs a, int sparse)
     // the last CTA writes every output (no B2 at all: Dist2 = INF, w = 1)
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(a.ctr + kCtrBruteDone, 1) == (int)gridDim.x - 1;
+    if (threadIdx.x == 0) last = atomicAdd(a.ctr + kCtrBruteDone, 1) == (int)gx - 1;
     __syncthreads();
     if (last) {
         __threadfence();
@@ -645,6 +679,12 @@ __global__ void __launch_bounds__(256) k_brute(RouteArgs a, int sparse)
         }
     }
 }
+
+__global__ void __launch_bounds__(256) k_brute(RouteArgs a, int sparse)
+{
+    k_brute_body(a, sparse, blockIdx.x, gridDim.x);
+}
+
 
 // A grid-stride kernel's grid: every CTA resident at once.
 template <class K>
@@ -684,6 +724,56 @@ cudaError_t launch_route_b2list(const RouteArgs& a, cudaStream_t st)
 cudaError_t launch_route_brute(const RouteArgs& a, int blocks, bool sparse, cudaStream_t st)
 {
     return launch_chained(k_brute, dim3(blocks), dim3(256), 0, st, a, sparse ? 1 : 0);
+}
+
+namespace {
+// Grouped kernels over fields of either rank: the body instance is picked
+// per work item from the field's arguments.
+#define QAI_ROUTE_GROUP(NAME, LB)                                                   \
+    __global__ void __launch_bounds__(LB) NAME##_group(const __grid_constant__ GroupQueue q) \
+    {                                                                               \
+        run_group<RouteArgs>(q, [&](const RouteArgs& a, int b, int n) {             \
+            if (a.rank == 3) NAME##_body<3>(a, b, n);                               \
+            else NAME##_body<2>(a, b, n);                                           \
+        });                                                                         \
+    }
+QAI_ROUTE_GROUP(k_b2map, 256)
+QAI_ROUTE_GROUP(k_query, 256)
+QAI_ROUTE_GROUP(k_query_mid, 256)
+QAI_ROUTE_GROUP(k_b2sparse, 256)
+#undef QAI_ROUTE_GROUP
+
+__global__ void __launch_bounds__(256) k_b2list_group(const __grid_constant__ GroupQueue q)
+{
+    run_group<RouteArgs>(q, [&](const RouteArgs& a, int b, int n) { k_b2list_body(a, b, n); });
+}
+
+__global__ void __launch_bounds__(256) k_brute_group(const __grid_constant__ GroupQueue q, int sparse)
+{
+    run_group<RouteArgs>(q, [&](const RouteArgs& a, int b, int n) { k_brute_body(a, sparse, b, n); });
+}
+
+template <class K, class... A>
+cudaError_t run_grouped(K kern, const GroupQueue& q, cudaStream_t st, A... extra)
+{
+    const int grid = std::min(group_total(q), persistent_grid(kern, 256, 0));
+    if (grid < 1) return cudaSuccess;
+    return launch_chained(kern, dim3(grid), dim3(256), 0, st, q, extra...);
+}
+}  // namespace
+
+cudaError_t launch_group_route(RouteKernel k, const GroupQueue& q, cudaStream_t st)
+{
+    switch (k) {
+    case kRouteB2Sparse: return run_grouped(k_b2sparse_group, q, st);
+    case kRouteBruteSparse: return run_grouped(k_brute_group, q, st, 1);
+    case kRouteB2Map: return run_grouped(k_b2map_group, q, st);
+    case kRouteQuery: return run_grouped(k_query_group, q, st);
+    case kRouteQueryMid: return run_grouped(k_query_mid_group, q, st);
+    case kRouteB2List: return run_grouped(k_b2list_group, q, st);
+    case kRouteBrute: return run_grouped(k_brute_group, q, st, 0);
+    }
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_route_sparse_sites(const RouteArgs& a, cudaStream_t st)

@@ -58,7 +58,9 @@ class DebugOut(ctypes.Structure):
 
 class BatchChoice(ctypes.Structure):
     _fields_ = [("rank", ctypes.c_int32), ("fields", ctypes.c_int32), ("streams", ctypes.c_int32),
-                ("order", ctypes.c_int32), ("ms", ctypes.c_float)]
+                ("order", ctypes.c_int32), ("ms", ctypes.c_float), ("grouped", ctypes.c_int32),
+                ("tile_w", ctypes.c_int32), ("rows_per_band", ctypes.c_int32),
+                ("points_per_block", ctypes.c_int32), ("launches", ctypes.c_int32)]
 
 
 class KernelStat(ctypes.Structure):
@@ -458,8 +460,8 @@ class Batch:
 
 
 def mitigate_batched(batch: Batch, stream=None, **kw):
-    """Algorithm 4 on every field of ``batch`` in one call (the fields' launch
-    sequences on forked streams, replayed from a cached CUDA graph). Returns
+    """Algorithm 4 on every field of ``batch`` in one call (persistent grouped
+    launches over all fields, replayed from a cached CUDA graph). Returns
     ``batch.outs``."""
     p = _params(kw.get("eta", 0.9), kw.get("idw_power", 1.0), kw.get("grad_threshold", 2),
                 kw.get("sign_rule", SIGN_SUM), kw.get("b2_rule", B2_SAME_Q))
@@ -469,14 +471,19 @@ def mitigate_batched(batch: Batch, stream=None, **kw):
 
 
 def autotune_batched(batch: Batch, stream=None, **kw):
-    """Time the stream-count and field-order candidates on ``batch`` and keep
-    the fastest per rank group; returns {rank: (streams, order, ms)}."""
+    """Time the candidates on ``batch`` and keep the fastest: for the grouped
+    launches of the rank-2 and rank-3 fields the queue order, the points per
+    work item and the column tiles; for rank 1 (and the per-field form) the
+    stream count and field order. Returns {rank: {choice: value}}."""
     p = _params(kw.get("eta", 0.9), kw.get("idw_power", 1.0), kw.get("grad_threshold", 2),
                 kw.get("sign_rule", SIGN_SUM), kw.get("b2_rule", B2_SAME_Q))
     ch = (BatchChoice * 3)()
     _check(load().qai_autotune_batched(*batch._args(), ctypes.byref(p), batch.workspace.data_ptr(),
                                        batch.workspace.numel(), _stream(stream), ch))
-    return {c.rank: (c.streams, c.order, c.ms) for c in ch if c.rank}
+    return {c.rank: {"grouped": bool(c.grouped), "order": "largest first" if c.order else "as given",
+                     "streams": c.streams, "ms": c.ms, "tile_w": c.tile_w, "rows_per_band": c.rows_per_band,
+                     "points_per_block": c.points_per_block, "launches": c.launches}
+            for c in ch if c.rank}
 
 
 STATIC_MAX_POINTS = 2097152

@@ -1,6 +1,7 @@
-"""The batched form (the fields' launch sequences on forked streams, in one
-cached CUDA graph) against single qai_mitigate calls (bit-identical: the same
-kernels on the same data) and against the FP64 oracle on a subset."""
+"""The batched form (persistent grouped launches over all fields, in one
+cached CUDA graph; per-field sequences on forked streams inside a caller's
+capture) against single qai_mitigate calls (bit-identical: the same kernel
+bodies on the same data) and against the FP64 oracle on a subset."""
 import numpy as np
 import pytest
 import torch
@@ -46,7 +47,13 @@ def test_batched_matches_oracle_and_autotune_keeps_results():
     qs, ebs, xs = _fields(SHAPES, seed0=300)
     batch = qai.Batch(qs, ebs)
     choice = qai.autotune_batched(batch)
-    assert set(choice) <= {1, 2, 3} and all(v[2] > 0 and v[0] in (1, 2, 4, 8) for v in choice.values())
+    assert set(choice) <= {1, 2, 3} and all(v["ms"] > 0 for v in choice.values())
+    assert choice[1]["streams"] == 1 and not choice[1]["grouped"]
+    for r in (2, 3):
+        c = choice[r]
+        assert c["grouped"] and c["launches"] >= 10 and c["points_per_block"] in (1 << k for k in range(14, 19))
+        assert (c["tile_w"], c["rows_per_band"]) in {(0, 0), (8, 32), (16, 32), (32, 32), (8, 16), (16, 16),
+                                                     (16, 64), (32, 64)}
     outs = qai.mitigate_batched(batch)
     torch.cuda.synchronize()
     for q, eb, x, o in zip(qs, ebs, xs, outs):
@@ -106,3 +113,19 @@ def test_batched_argument_errors():
     batch.ebs[0] = -1.0
     with pytest.raises(qai.QAIError):
         qai.mitigate_batched(batch)
+
+
+def test_more_fields_than_one_launch_holds():
+    """70 fields of one shape share every kernel: the launches split at 64
+    fields; the fronts at eb 1e-2 of the range take the fallbacks."""
+    qs, ebs = [], []
+    for i in range(70):
+        x = synth.grf_front((40, 96), seed=700 + i, device="cuda")
+        eb = (1e-2 if i % 2 else 1e-3) * synth.value_range(x)
+        qs.append(synth.quantize(x, eb))
+        ebs.append(eb)
+    batch = qai.Batch(qs, ebs)
+    outs = qai.mitigate_batched(batch)
+    torch.cuda.synchronize()
+    for i, (q, eb, o) in enumerate(zip(qs, ebs, outs)):
+        assert torch.equal(o, qai.mitigate(q, eb)), i
