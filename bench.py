@@ -420,9 +420,13 @@ def run_aniso(args):
     the routes the EDTs took and the per-kernel times."""
     import torch
     from paper_2602_20097_gb300 import qai, synth
+    only = tuple(int(v) for v in args.shape.split(",")) if args.shape else None
+    rels = tuple(float(v) for v in args.rel_eb.split(",")) if args.rel_eb else (1e-3, 1e-2)
     for shape, seed in (((1800, 3600), 6), ((256, 384, 384), 4), ((100, 500, 500), 3), ((98, 1200, 1200), 5)):
+        if only is not None and shape != only:
+            continue
         x = synth.grf_front(shape, seed=seed, device="cuda")
-        for rel in (1e-3, 1e-2):
+        for rel in rels:
             eb = rel * synth.value_range(x)
             q = synth.quantize(x, eb)
             ws = qai.alloc_workspace(qai.workspace_size(tuple(q.shape)))
@@ -582,7 +586,9 @@ def main():
     ap.add_argument("--impl", choices=["qai", "reference"], default="qai")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--shape", default="", help="Z,Y,X override (profiling of smaller cases)")
+    ap.add_argument("--shape", default="", help="Z,Y,X override (profiling of smaller cases); with --workload "
+                    "aniso: run only the front of this shape")
+    ap.add_argument("--rel-eb", default="", help="with --workload aniso: the bounds (x value range), comma separated")
     ap.add_argument("--workload", default="grf512", choices=["grf512", "aniso", "batch96", "adjoint1024", "quality512"],
                     help="grf512: the headline line; the others print their own lines")
     args = ap.parse_args()
