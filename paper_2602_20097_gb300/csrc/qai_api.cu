@@ -594,11 +594,10 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
         if (e != cudaSuccess) return cuda_fail(e, "B2 site list");
         e = timed("signed_brute", 0.0, st, [&] { return qai::launch_route_brute(ra, 2 * sms, false, st); });
         if (e != cudaSuccess) return cuda_fail(e, "brute-force search");
-        // the byte maps of the separable passes: for the dense second EDT
-        // when it takes over, and always for the adjoint's forward
-        const int mode = (d2rec || saved) ? 2 : 1;
+        // the byte maps of the separable passes, for the dense second EDT
+        // when it takes over (the adjoint reads the packed maps)
         if (local) {
-            e = timed("expand", N * (mode == 2 ? 6.25 : 0.0), st, [&] { return qai::launch_local_expand(la, mode, st); });
+            e = timed("expand", 0.0, st, [&] { return qai::launch_local_expand(la, 1, st); });
             if (e != cudaSuccess) return cuda_fail(e, "byte maps");
         }
     }
@@ -657,8 +656,8 @@ qai_status run_pipeline(const int32_t* d_q, float* d_out, const Shape& sh, const
         if ((st_ = colpass(2, 4, true, cz, "colpass2_z_final", 4 + 4 + 1 + 4 + 4)) != QAI_OK) return st_;
     }
     if (saved && ctr) {
-        e = timed("save", N * 11.0, st, [&] {
-            return qai::launch_save_signed(sh.N, s, eqm, dist1, saved->s, saved->dist1, saved->dist2, st);
+        e = timed("save", N * 9.5, st, [&] {
+            return qai::launch_save_packed(la, saved->s, saved->dist1, saved->dist2, st);
         });
         if (e != cudaSuccess) return cuda_fail(e, "saved state");
     }
@@ -1068,10 +1067,16 @@ qai_status qai_mitigate_backward(const int32_t* d_q, const float* d_grad_out, fl
         int32_t* d2rec = reinterpret_cast<int32_t*>(ws + lay.total + align256((size_t)sh.N * 4));
         s = run_pipeline(d_q, scratch_out, sh, method_args(p, eb), ws, lay, stream, nullptr, nullptr, d2rec);
         if (s != QAI_OK) return s;
-        b.s = reinterpret_cast<int8_t*>(ws + lay.s);
+        b.spk = reinterpret_cast<const uint32_t*>(ws + lay.spk);
+        b.codes = reinterpret_cast<const uint32_t*>(ws + lay.codes);
+        b.wpr = lay.wpr;
+        b.nx = sh.nx;
         b.dist1 = reinterpret_cast<int32_t*>(ws + lay.dist1);
         b.dist2 = d2rec;
-        b.b1_eqm = reinterpret_cast<uint8_t*>(ws + lay.eqm);
+        if (d_grad_dprime &&
+            (e = cudaMemcpyAsync(d_grad_dprime, d_grad_out, (size_t)sh.N * 4, cudaMemcpyDeviceToDevice, stream)))
+            return cuda_fail(e, "copy dL/dD'");
+        b.grad_dprime = nullptr;
     } else if (sh.rank >= 2) {
         // the dense-only route: recompute Dist1, S and the EDT2 words with
         // the dense pipeline; its last column pass sums the adjoint terms in

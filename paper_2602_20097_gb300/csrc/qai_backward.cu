@@ -25,7 +25,24 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-// vec: N a multiple of 4 and every array aligned for 4-point accesses.
+// The 2-bit fields of points i .. i + 3 (one row, 4 | nx) of a packed map
+// with wpr words a row, in the low byte.
+__device__ __forceinline__ unsigned packed4(const uint32_t* m, int wpr, int nx, int i)
+{
+    const int row = i / nx, x0 = i - row * nx;
+    return (__ldg(m + (int64_t)row * wpr + (x0 >> 4)) >> (2 * (x0 & 15))) & 0xFFu;
+}
+// The 2-bit field of point i.
+__device__ __forceinline__ unsigned packed1(const uint32_t* m, int wpr, int nx, int i)
+{
+    const int row = i / nx, x = i - row * nx;
+    return (__ldg(m + (int64_t)row * wpr + (x >> 4)) >> (2 * (x & 15))) & 3u;
+}
+// S as -1, 0, +1 from its 2-bit code (0, 1: +1, 2: -1).
+__device__ __forceinline__ int s_of(unsigned c) { return c == 1u ? 1 : (c == 2u ? -1 : 0); }
+
+// vec: N a multiple of 4 and every array aligned for 4-point accesses (and,
+// with the packed maps, 4 | nx).
 __global__ void __launch_bounds__(256) k_backward(BackArgs a, int vec)
 {
     GradAcc acc;
@@ -33,7 +50,37 @@ __global__ void __launch_bounds__(256) k_backward(BackArgs a, int vec)
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     // Terms vanish where S = 0: Dist1, Dist2 (and G, unless dL/dD' is
     // wanted) are read only for groups of points with some S != 0.
-    if (vec) {
+    if (a.spk) {  // S and B1 from a plain forward's packed maps (dL/dD' copied by the host)
+        if (vec) {
+            for (int64_t i = t0; i < (a.N >> 2); i += stride) {
+                const unsigned sc = packed4(a.spk, a.wpr, a.nx, (int)(4 * i));
+                if (!sc) continue;
+                const unsigned cc = packed4(a.codes, a.wpr, a.nx, (int)(4 * i));
+                const float4 g = __ldg(reinterpret_cast<const float4*>(a.grad_out) + i);
+                const int4 d1 = __ldg(reinterpret_cast<const int4*>(a.dist1) + i);
+                const int4 d2 = __ldg(reinterpret_cast<const int4*>(a.dist2) + i);
+                const float gv[4] = {g.x, g.y, g.z, g.w};
+                const int d1v[4] = {d1.x, d1.y, d1.z, d1.w}, d2v[4] = {d2.x, d2.y, d2.z, d2.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int sv = s_of((sc >> (2 * j)) & 3u);
+                    if (!sv) continue;
+                    float te, tp;
+                    grad_terms(gv[j], sv, ((cc >> (2 * j)) & 3u) ? 0 : d1v[j], d2v[j], a.p, te, tp);
+                    acc.add(te, tp);
+                }
+            }
+        } else {
+            for (int64_t i = t0; i < a.N; i += stride) {
+                const int sv = s_of(packed1(a.spk, a.wpr, a.nx, (int)i));
+                if (!sv) continue;
+                const int d1 = packed1(a.codes, a.wpr, a.nx, (int)i) ? 0 : __ldg(a.dist1 + i);
+                float te, tp;
+                grad_terms(__ldg(a.grad_out + i), sv, d1, __ldg(a.dist2 + i), a.p, te, tp);
+                acc.add(te, tp);
+            }
+        }
+    } else if (vec) {
         const int64_t n4 = a.N >> 2;
         for (int64_t i = t0; i < n4; i += stride) {
             const uint32_t sw = __ldg(reinterpret_cast<const uint32_t*>(a.s) + i);
@@ -158,6 +205,51 @@ __global__ void __launch_bounds__(256) k_save_signed(int64_t N, const int8_t* s,
     }
 }
 
+// The same from a plain forward's packed maps: S from spk (as int8), B1
+// where the step-A code is not 0.
+__global__ void __launch_bounds__(256) k_save_packed(int64_t N, const uint32_t* spk, const uint32_t* codes, int wpr,
+                                                      int nx, const int32_t* dist1, int8_t* s_out, int32_t* d1_out,
+                                                      int32_t* d2, int vec)
+{
+    wait_prior_grid();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (vec) {
+        for (int64_t i = t0; i < (N >> 2); i += stride) {
+            const unsigned sc = packed4(spk, wpr, nx, (int)(4 * i));
+            uint32_t sw = 0;
+            unsigned keep = 0;  // bit j: S != 0 off B1
+            if (sc) {
+                const unsigned cc = packed4(codes, wpr, nx, (int)(4 * i));
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int sv = s_of((sc >> (2 * j)) & 3u);
+                    sw |= (uint32_t)(uint8_t)(int8_t)sv << (8 * j);
+                    if (sv && !((cc >> (2 * j)) & 3u)) keep |= 1u << j;
+                }
+            }
+            reinterpret_cast<uint32_t*>(s_out)[i] = sw;
+            int4 o1 = make_int4(0, 0, 0, 0), o2 = make_int4(0, 0, 0, 0);
+            if (keep) {
+                const int4 a1 = __ldg(reinterpret_cast<const int4*>(dist1) + i);
+                const int4 a2 = reinterpret_cast<const int4*>(d2)[i];
+                o1 = make_int4(keep & 1u ? a1.x : 0, keep & 2u ? a1.y : 0, keep & 4u ? a1.z : 0, keep & 8u ? a1.w : 0);
+                o2 = make_int4(keep & 1u ? a2.x : 0, keep & 2u ? a2.y : 0, keep & 4u ? a2.z : 0, keep & 8u ? a2.w : 0);
+            }
+            reinterpret_cast<int4*>(d1_out)[i] = o1;
+            reinterpret_cast<int4*>(d2)[i] = o2;
+        }
+    } else {
+        for (int64_t i = t0; i < N; i += stride) {
+            const int sv = s_of(packed1(spk, wpr, nx, (int)i));
+            s_out[i] = (int8_t)sv;
+            const bool keep = sv && !packed1(codes, wpr, nx, (int)i);
+            d1_out[i] = keep ? __ldg(dist1 + i) : 0;
+            d2[i] = keep ? d2[i] : 0;
+        }
+    }
+}
+
 // D' = 2 q eps (Eq. 1) in fp32: float(q) * float(2 eps), rounded once, the
 // expression every output of the library starts from.
 __global__ void __launch_bounds__(256) k_dequantize(const int32_t* q, float* out, int64_t n, float two_eb)
@@ -198,6 +290,17 @@ cudaError_t launch_add_dprime(const float* dprime, float* out, int64_t n, cudaSt
     return launch_chained(k_add_dprime, dim3(grid_for(n)), dim3(256), 0, st, dprime, out, n);
 }
 
+cudaError_t launch_save_packed(const LocalArgs& la, int8_t* s_out, int32_t* d1_out, int32_t* d2, cudaStream_t st)
+{
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    auto al = [](const void* p, int b) { return reinterpret_cast<uintptr_t>(p) % b == 0; };
+    const int64_t N = (int64_t)la.nz * la.ny * la.nx;
+    const int vec = la.nx % 4 == 0 && al(s_out, 4) && al(la.dist1, 16) && al(d1_out, 16) && al(d2, 16);
+    return launch_chained(k_save_packed, dim3(sms * 8), dim3(256), 0, st, N, (const uint32_t*)la.spk,
+                          (const uint32_t*)la.codes, la.wpr, la.nx, (const int32_t*)la.dist1, s_out, d1_out, d2, vec);
+}
+
 cudaError_t launch_save_signed(int64_t N, const int8_t* s, const uint8_t* eqm, const int32_t* dist1,
                                int8_t* s_out, int32_t* d1_out, int32_t* d2, cudaStream_t st)
 {
@@ -230,7 +333,7 @@ cudaError_t launch_backward(const BackArgs& a, cudaStream_t st)
     if (blocks < 1) blocks = 1;
     auto al = [](const void* p) { return p == nullptr || reinterpret_cast<uintptr_t>(p) % 16 == 0; };
     const int vec = a.N % 4 == 0 && al(a.grad_out) && al(a.dist1) && al(a.dist2) && al(a.grad_dprime) &&
-                    reinterpret_cast<uintptr_t>(a.s) % 4 == 0;
+                    (a.spk ? a.nx % 4 == 0 : reinterpret_cast<uintptr_t>(a.s) % 4 == 0);
     k_backward<<<(int)blocks, 256, 0, st>>>(a, vec);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

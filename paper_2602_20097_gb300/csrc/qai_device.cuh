@@ -331,6 +331,11 @@ struct BackArgs {
     const int32_t* dist1;    // Dist1 (read only where S != 0)
     const int32_t* dist2;    // Dist2 (idem)
     const uint8_t* b1_eqm;   // NULL, or equal-q mask bytes: Dist1 = 0 where a bit is clear (B1)
+    // or, after a plain forward: S and B1 from its packed maps (s and b1_eqm
+    // unused): S from spk, B1 where the step-A code is not 0 (wpr words a row)
+    const uint32_t* spk;
+    const uint32_t* codes;
+    int wpr, nx;
     float* grad_dprime;      // dL/dD' (= dL/dD''), NULL to skip
     double* grad_params;     // [2]: dL/deta, dL/dp
     double* partials;        // [2 * kBackwardMaxBlocks] block totals (workspace)

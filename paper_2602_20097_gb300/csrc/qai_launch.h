@@ -97,6 +97,9 @@ cudaError_t launch_backward(const BackArgs& a, cudaStream_t st);
 // elsewhere.
 cudaError_t launch_save_signed(int64_t N, const int8_t* s, const uint8_t* eqm, const int32_t* dist1,
                                int8_t* s_out, int32_t* d1_out, int32_t* d2, cudaStream_t st);
+// The same from the packed maps of a plain forward (the local first EDT's
+// arguments `la`: S from spk, B1 from the step-A codes).
+cudaError_t launch_save_packed(const LocalArgs& la, int8_t* s_out, int32_t* d1_out, int32_t* d2, cudaStream_t st);
 // D' = 2 q eps in fp32 (n points), and out = dprime + out (D'' for a given D').
 cudaError_t launch_dequantize(const int32_t* q, float* out, int64_t n, float two_eb, cudaStream_t st);
 cudaError_t launch_add_dprime(const float* dprime, float* out, int64_t n, cudaStream_t st);
