@@ -46,6 +46,14 @@ __host__ __device__ inline size_t smem_per_warp(int nx)
     return ((nseg * 3 * 4 + nseg * 32 * 2) + 15) & ~(size_t)15;
 }
 
+// Shared memory of a CTA that walks one row with all its warps: the warp
+// layout plus, per segment, the last site left of it.
+__host__ __device__ inline size_t smem_coop(int nx)
+{
+    const size_t nseg = (size_t)((nx + kSeg - 1) / kSeg);
+    return ((nseg * 4 * 4 + nseg * 32 * 2) + 15 + 16) & ~(size_t)15;
+}
+
 // A site reference packs the position and the 2-bit sign code.
 __device__ __forceinline__ int make_ref(int pos, int code) { return (pos << 2) | code; }
 
@@ -68,18 +76,27 @@ __device__ __forceinline__ uint32_t load4_u8(const void* base, int x0, int nx, b
 }
 
 // One warp's work: x-row `row` of the field `a`, with `wsm` this warp's
-// shared memory (smem_per_warp of an extent >= a.nx).
-template <int PHASE, int RANK, bool FINAL, bool DEBUG, bool VEC>
+// shared memory (smem_per_warp of an extent >= a.nx). COOP: every warp of
+// the CTA walks the same row (segments dealt round robin; `wsm` is the CTA's
+// smem_coop of an extent >= a.nx): the segments are independent but for the
+// value left of each (loaded directly) and the sites outside them (the
+// segment summaries, combined by one thread between the sweeps). Every
+// thread of the CTA must call it.
+template <int PHASE, int RANK, bool FINAL, bool DEBUG, bool VEC, bool COOP = false>
 __device__ __forceinline__ void rowpass_row(const RowArgs& a, const int row, unsigned char* wsm)
 {
     const int lane = threadIdx.x & 31;
     const int nx = a.nx;
     const int nseg = (nx + kSeg - 1) / kSeg;
+    const int seg0 = COOP ? (int)(threadIdx.x >> 5) : 0;
+    const int segstep = COOP ? (int)(blockDim.x >> 5) : 1;
     RowSmem sm;
     sm.sfirst = reinterpret_cast<int*>(wsm);
     sm.slast = sm.sfirst + nseg;
     sm.nextr = sm.slast + nseg;
-    sm.info = reinterpret_cast<uint16_t*>(sm.nextr + nseg);
+    int* carryl = sm.nextr + nseg;  // COOP: the last site left of each segment
+    sm.info = reinterpret_cast<uint16_t*>(COOP ? carryl + nseg : sm.nextr + nseg);
+    int* s_rowfirst = reinterpret_cast<int*>(sm.info + nseg * 32);  // COOP: the first site of the row
     const int z = row / a.ny;
     const int y = row - z * a.ny;
     const int rbase = row * nx;
@@ -90,9 +107,13 @@ __device__ __forceinline__ void rowpass_row(const RowArgs& a, const int row, uns
 
     // ---- sweep A: sites of each segment ------------------------------------
     int carry_prev = 0;  // value left of the segment (phase 1: q, phase 2: S byte)
-    for (int seg = 0; seg < nseg; ++seg) {
+    for (int seg = seg0; seg < nseg; seg += segstep) {
         const int x0 = seg * kSeg + 4 * lane;
         unsigned nib = 0, codes = 0;
+        if (COOP && lane == 0 && x0 > 0) {  // the value left of the segment, from memory
+            if (PHASE == 1) carry_prev = __ldg(a.q + rbase + x0 - 1);
+            else carry_prev = (int)((uint32_t)__ldg(reinterpret_cast<const uint8_t*>(a.s_in) + rbase + x0 - 1) << 24);
+        }
         if (PHASE == 1) {
             int c[4], yl[4] = {0, 0, 0, 0}, yr[4] = {0, 0, 0, 0}, zl[4] = {0, 0, 0, 0},
                       zr[4] = {0, 0, 0, 0};
@@ -259,21 +280,40 @@ __device__ __forceinline__ void rowpass_row(const RowArgs& a, const int row, uns
             sm.slast[seg] = H ? l : kNoRef;
         }
     }
-    __syncwarp();
     int row_first = kNoRef;  // first site of the row
-    if (lane == 0) {
-        int nxt = kNoRef;
-        for (int seg = nseg - 1; seg >= 0; --seg) {
-            sm.nextr[seg] = nxt;
-            if (sm.sfirst[seg] != kNoRef) nxt = sm.sfirst[seg];
+    if (COOP) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int nxt = kNoRef, prv = kNoRef;
+            for (int seg = nseg - 1; seg >= 0; --seg) {
+                sm.nextr[seg] = nxt;
+                if (sm.sfirst[seg] != kNoRef) nxt = sm.sfirst[seg];
+            }
+            for (int seg = 0; seg < nseg; ++seg) {
+                carryl[seg] = prv;
+                if (sm.slast[seg] != kNoRef) prv = sm.slast[seg];
+            }
+            *s_rowfirst = nxt;
         }
-        row_first = nxt;
+        __syncthreads();
+        row_first = *s_rowfirst;
+    } else {
+        __syncwarp();
+        if (lane == 0) {
+            int nxt = kNoRef;
+            for (int seg = nseg - 1; seg >= 0; --seg) {
+                sm.nextr[seg] = nxt;
+                if (sm.sfirst[seg] != kNoRef) nxt = sm.sfirst[seg];
+            }
+            row_first = nxt;
+        }
+        __syncwarp();
+        row_first = __shfl_sync(kFull, row_first, 0);
     }
-    __syncwarp();
     // a row without sites (common for the sparse sign flips of the second
     // EDT) is INF everywhere: no sweep B
-    if (!FINAL && !DEBUG && __shfl_sync(kFull, row_first, 0) == kNoRef) {
-        for (int seg = 0; seg < nseg; ++seg) {
+    if (!FINAL && !DEBUG && row_first == kNoRef) {
+        for (int seg = seg0; seg < nseg; seg += segstep) {
             const int x0 = seg * kSeg + 4 * lane;
             if (VEC) {
                 if (x0 < nx) *reinterpret_cast<uint2*>(a.xw + rbase + x0) = make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
@@ -290,8 +330,9 @@ __device__ __forceinline__ void rowpass_row(const RowArgs& a, const int row, uns
     const unsigned lt = (1u << lane) - 1u;
     const unsigned gt = ~((2u << lane) - 1u);
     int carry_l = kNoRef;
-    for (int seg = 0; seg < nseg; ++seg) {
+    for (int seg = seg0; seg < nseg; seg += segstep) {
         const int x0 = seg * kSeg + 4 * lane;
+        if (COOP) carry_l = carryl[seg];
         const unsigned v = sm.info[seg * 32 + lane];
         const unsigned nib = v & 15u, codes = v >> 4;
         const unsigned H = __ballot_sync(kFull, nib != 0);
@@ -388,6 +429,22 @@ __global__ void __launch_bounds__(256) k_rowpass(RowArgs a)
     k_rowpass_body<PHASE, RANK, FINAL, DEBUG, VEC>(a, blockIdx.x, gridDim.x);
 }
 
+// Long rows and few of them (2-D fields, 1-D fields): a CTA per row, all its
+// warps on that row.
+template <int PHASE, int RANK, bool FINAL, bool DEBUG, bool VEC>
+__global__ void __launch_bounds__(512) k_rowpass_coop(RowArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    wait_prior_grid();
+    if (a.gate && *static_cast<const volatile int*>(a.gate) == 0) return;
+    if (PHASE == 1 && a.route_ctr && blockIdx.x == 0 && threadIdx.x < kCtrTimeout)
+        a.route_ctr[threadIdx.x] = 0;
+    for (int row = blockIdx.x; row < a.nz * a.ny; row += gridDim.x) {
+        rowpass_row<PHASE, RANK, FINAL, DEBUG, VEC, true>(a, row, smem);
+        __syncthreads();
+    }
+}
+
 
 // Several fields in one launch: global row g belongs to field f with
 // first_row[f] <= g < first_row[f + 1]; the table travels by value.
@@ -410,10 +467,44 @@ __global__ void __launch_bounds__(256) k_rowpass_grouped(const __grid_constant__
     else rowpass_row<PHASE, RANK, FINAL, false, false>(a, g - t.first_row[lo], wsm);
 }
 
+// A CTA of 16 warps per row when the rows are long and too few for one warp
+// each to fill the GPU.
+constexpr int kCoopWarps = 16;
+bool use_coop(const RowArgs& a, int sms)
+{
+    const int nseg = (a.nx + kSeg - 1) / kSeg;
+    return nseg >= 8 && (int64_t)a.nz * a.ny < (int64_t)sms * 32;
+}
+
+template <int PHASE, int RANK, bool FINAL>
+cudaError_t go_coop(const RowArgs& a, bool debug, bool vec, int sms, cudaStream_t st)
+{
+    const size_t smem = smem_coop(a.nx);
+    auto run = [&](auto kern) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int per = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 32 * kCoopWarps, smem) != cudaSuccess || per < 1)
+            per = 1;
+        const int rows = a.nz * a.ny;
+        const int grid = std::max(1, std::min(rows, sms * per));
+        return launch_chained(kern, dim3(grid), dim3(32 * kCoopWarps), smem, st, a);
+    };
+    if (debug) return vec ? run(k_rowpass_coop<PHASE, RANK, FINAL, true, true>)
+                          : run(k_rowpass_coop<PHASE, RANK, FINAL, true, false>);
+    return vec ? run(k_rowpass_coop<PHASE, RANK, FINAL, false, true>)
+               : run(k_rowpass_coop<PHASE, RANK, FINAL, false, false>);
+}
+
 template <int PHASE, int RANK, bool FINAL>
 cudaError_t go(const RowArgs& a, bool debug, bool vec, dim3 grid, dim3 block, size_t smem,
                cudaStream_t st)
 {
+    {
+        int dev = 0, sms = 152;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (use_coop(a, sms)) return go_coop<PHASE, RANK, FINAL>(a, debug, vec, sms, st);
+    }
     auto run = [&](auto kern) -> cudaError_t {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
