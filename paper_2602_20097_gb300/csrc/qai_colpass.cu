@@ -104,6 +104,7 @@ struct QueryBuf {
     int* n;     // shared count (may pass kQueryBuf: the route then gives up)
     int32_t* se;// [kSignedBuf]
     int* sn;    // shared count (may pass kSignedBuf: that list is then incomplete)
+    int* full;  // shared flag: the global query list is over its capacity
 };
 
 template <int PHASE, int IN, bool FINAL, bool DEBUG, bool GRAD, class Word>
@@ -122,18 +123,25 @@ __device__ __forceinline__ void emit_point(const ColArgs& a, int idx, int src, i
                 // point off B1 there is a query of the second EDT
                 a.dist1[idx] = val;
                 if (val > 0) {
-                    const int k = atomicAdd(qb.n, 1);
-                    if (k < kQueryBuf) {
-                        qb.e[k] = Query{idx, (val << 2) | code};
-                    } else {
-                        // a full buffer spills to the global list; should the
-                        // tile fall back to the envelope path, these entries
-                        // are listed twice (the same query, the same output).
-                        // Once the list is over its capacity the route hands
-                        // the field over whatever the count: no more atomics.
-                        if (*static_cast<const volatile int*>(a.route_ctr + kCtrQueries) <= a.qcap) {
-                            const int g = atomicAdd(a.route_ctr + kCtrQueries, 1);
-                            if (g < a.qcap) a.qlist[g] = Query{idx, (val << 2) | code};
+                    // once the global list is over its capacity the route
+                    // hands the field over whatever the count: the CTA stops
+                    // collecting (its flag, then the shared count it leaves)
+                    if (*static_cast<volatile int*>(qb.full) == 0) {
+                        const int k = atomicAdd(qb.n, 1);
+                        if (k < kQueryBuf) {
+                            qb.e[k] = Query{idx, (val << 2) | code};
+                        } else {
+                            // a full buffer spills to the global list; should
+                            // the tile fall back to the envelope path, these
+                            // entries are listed twice (the same query, the
+                            // same output)
+                            bool over = *static_cast<const volatile int*>(a.route_ctr + kCtrQueries) > a.qcap;
+                            if (!over) {
+                                const int g = atomicAdd(a.route_ctr + kCtrQueries, 1);
+                                if (g < a.qcap) a.qlist[g] = Query{idx, (val << 2) | code};
+                                else over = true;
+                            }
+                            if (over) *static_cast<volatile int*>(qb.full) = 1;
                         }
                     }
                 } else {
@@ -201,9 +209,9 @@ __device__ __forceinline__ void colpass_tile(const ColArgs& a, const int blk)
     constexpr bool kQueries = PHASE == 1 && FINAL;
     __shared__ Query s_qbuf[kQueries ? kQueryBuf : 1];
     __shared__ int32_t s_sbuf[kQueries ? kSignedBuf : 1];
-    __shared__ int s_qn, s_qbase, s_sn, s_sbase;
-    const QueryBuf qb{s_qbuf, &s_qn, s_sbuf, &s_sn};
-    if (tid == 0) s_fail = s_total = s_qn = s_sn = 0;
+    __shared__ int s_qn, s_qbase, s_sn, s_sbase, s_qfull;
+    const QueryBuf qb{s_qbuf, &s_qn, s_sbuf, &s_sn, &s_qfull};
+    if (tid == 0) s_fail = s_total = s_qn = s_sn = s_qfull = 0;
     if (PHASE == 1 && FINAL && tid < W) s_sign[tid] = 0;
     int any_sign = 0;  // phase 1 final: this thread's points with S != 0
 
