@@ -172,7 +172,11 @@ Layout layout_for(const Shape& s, uint32_t flags)
         l.nez = s.rank == 3 ? take(rows * l.wpr * 4) : 0;
         l.spk = take(rows * l.wpr * 4);
         l.b2bits = take(rows * l.bwpr * 4);
-        l.qcap = (int)(N / 128 + 1024);
+        // the query lists: past them the dense second EDT takes over, which
+        // in 3-D costs three passes over the field and the byte maps of the
+        // separable passes -- about what the route spends on 3 % of the
+        // points as queries; in 2-D its passes are cheap next to the route
+        l.qcap = (int)(s.rank == 3 ? N / 32 + 1024 : N / 128 + 1024);
         l.scap = (int)(N / 256 + 1024);
         l.fcap = std::min(l.qcap, 1 << 16);
         l.b2cap = (int)(N / 32 + 4096);  // B2 sites up to ~3 % of the points

@@ -282,7 +282,8 @@ __device__ __forceinline__ void store_step_a(const LocalArgs& a, int row, int x0
             const unsigned cd = (sg >> (2 * j)) & 3u;
             const float cc = (cd == 1u ? 1.0f : (cd == 2u ? -1.0f : 0.0f)) * a.m.eta_eb;
             o[j] = a.m.output_c ? cc : fmaf((float)Q.c[j], a.m.two_eb, cc);
-            if (cd) {
+            // past the CTA's buffer the list is incomplete whatever the count
+            if (cd && *static_cast<volatile int*>(sb.n) <= sb.cap) {
                 const int k = atomicAdd(sb.n, 1);
                 if (k < sb.cap) sb.e[k] = row * nx + x0 + j;
             }
@@ -742,7 +743,10 @@ __device__ __forceinline__ void k_near_body(const LocalArgs& a, const int bx, co
                     const uint32_t resolved = need0 & ~need;
                     const uint32_t soff = res - resolved;  // the site's code less one: S
                     s |= soff;
-                    uint32_t qm = field_lsb(soff);         // queries: S != 0 off B1
+                    // queries: S != 0 off B1 (none once a warp of a 2-D
+                    // field gave up: the separable passes then redo Dist1
+                    // and the list)
+                    uint32_t qm = RANK == 2 && fail ? 0u : field_lsb(soff);
                     while (qm) {
                         const int f = __ffs(qm) - 1;
                         qm &= qm - 1;

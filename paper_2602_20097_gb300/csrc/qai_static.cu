@@ -17,11 +17,13 @@ namespace {
 // byte per point, since that pass has at least two rows), four packed maps of
 // 2 bits a point (step-A codes, two equal-neighbour maps, S) and the B2
 // bitmap (1 bit), each rounded up to whole words per row, the lists of the
-// signed-point route (two of N / 128 + 1024 queries of 8 bytes, N / 256 +
+// signed-point route (two of N / 32 + 1024 queries of 8 bytes (N / 128 +
+// 1024 in 2-D), N / 256 +
 // 1024 signed boundary points of 4 bytes, at most 65536 leftover queries at
 // 12 bytes, N / 32 + 4096 B2 sites of 8 bytes) and the 256-byte alignment of
-// its slices: at most 14.3 N + 0.9 MiB for every shape of at most N points
-// with an x extent of 16 or more, inside 15 N + 1 MiB. Narrower x extents
+// its slices: at most 15 N + 0.71 MiB for every shape of at most N points
+// with an x extent of 16 or more (the worst is an x extent of 17, whose
+// packed rows are nearly half padding), inside 15 N + 1 MiB. Narrower x extents
 // round more of each row up and can need more; such shapes are rejected when
 // they do.
 constexpr int64_t kMaxPoints = QAI_STATIC_MAX_POINTS;
