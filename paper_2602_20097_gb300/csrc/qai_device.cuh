@@ -62,6 +62,7 @@ enum RouteCtr : int {
     kCtrSigned = 4,    // B1 points with S != 0
     kCtrSignedOver = 5,// != 0: the list of them is incomplete (a CTA had more than it could buffer)
     kCtrBruteDone = 6, // CTAs of the brute-force search that finished
+    kCtrNearItems = 7, // items of the nearest-site search handed out (one-field launch)
     kCtrMid = 8,       // queries the first (per-thread) shell search left
     kCtrBitmap = 9,    // != 0: the bitmap route runs (the sparse route could not)
     kCtrWide = 12,     // != 0: an index outside the fast path's range: the exact step A ran
@@ -217,6 +218,7 @@ struct LocalArgs {
     uint8_t* eqm;
     int8_t* s;
     MethodArgs m;
+    int near_stride;         // one-field near launch: the t-th item taken is t * near_stride mod items
 };
 
 // Grouped launches: several fields in one kernel, the per-field arguments

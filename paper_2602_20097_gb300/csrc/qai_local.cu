@@ -597,7 +597,17 @@ __device__ __forceinline__ int deep_r2(const LocalArgs& a, int z, int y, int x)
 // table order with a site taking each point.
 constexpr int kNearRows = 4;
 
-template <int RANK>
+// DYN (the one-field launch, when near_stride is set): after its first item
+// the warp takes the next from a counter in the route words, fetched while it
+// works on the current one -- the cost of an item varies with the searches
+// it needs, and over many rounds a fixed split leaves a few SMs working long
+// after the rest. The t-th item handed out is t * near_stride mod items (a
+// stride prime to the count), so that the items in work at one time are
+// spread over the field, as the fixed split spreads them. The fixed split
+// keeps the eight warps of a CTA on adjacent rows (their shared halo rows hit
+// in L1), which wins when each warp has few items; the grouped launch keeps
+// it always.
+template <int RANK, bool DYN = false>
 __device__ __forceinline__ void k_near_body(const LocalArgs& a, const int bx, const int gx)
 {
     wait_prior_grid();
@@ -622,7 +632,13 @@ __device__ __forceinline__ void k_near_body(const LocalArgs& a, const int bx, co
     // issues up front (warps of a field that fails meet either test soon).
     bool fail = false;  // warp-uniform
     int seen = 0, deep = 0;  // warp-uniform: words looked at, words searched past squared distance 1
-    for (int it = bx * (blockDim.x >> 5) + (threadIdx.x >> 5); it < items; it += wstride) {
+    // the first item of every warp is fixed (no burst of atomics at the start)
+    constexpr bool dyn = DYN;
+    int t = bx * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    while (t < items) {
+        int next = 0;  // dyn: the warp's next item, fetched ahead
+        if (dyn && lane == 0) next = wstride + atomicAdd(a.ctr + kCtrNearItems, 1);
+        const int it = dyn ? (int)((int64_t)t * a.near_stride % items) : t;
         const int z = RANK == 3 ? it / yb : 0;
         const int y0 = (it - z * yb) * kNearRows;
         const int row0 = z * a.ny + y0;
@@ -769,14 +785,15 @@ __device__ __forceinline__ void k_near_body(const LocalArgs& a, const int bx, co
                 if (in) a.spk[(int64_t)row * wpr + k] = s;
             }
         }
+        t = dyn ? __shfl_sync(kFull, next, 0) : t + wstride;
     }
     near_flush(a, qbuf, &qn, &qbase);
 }
 
-template <int RANK>
+template <int RANK, bool DYN>
 __global__ void __launch_bounds__(256, QAI_NEAR_MINB) k_near(LocalArgs a)
 {
-    k_near_body<RANK>(a, blockIdx.x, gridDim.x);
+    k_near_body<RANK, DYN>(a, blockIdx.x, gridDim.x);
 }
 
 
@@ -1001,10 +1018,26 @@ cudaError_t launch_local_detect(const LocalArgs& a, cudaStream_t st)
     return e != cudaSuccess ? e : exact(2);
 }
 
-cudaError_t launch_local_near(const LocalArgs& a, cudaStream_t st)
+cudaError_t launch_local_near(const LocalArgs& a_in, cudaStream_t st)
 {
+    LocalArgs a = a_in;
+    // items handed out from the counter when every warp has eight or more
+    // (measured: 13 a warp on 512^3 gains 13 %, 6 on 98 x 1200^2 loses 14 %),
+    // in the order of a stride prime to the count near its golden section;
+    // the fixed split is a kernel of its own (the counter's code in the
+    // kernel slows the fixed split by as much)
+    const int64_t items = (int64_t)a.nz * ((a.ny + kNearRows - 1) / kNearRows);
+    const int grid = a.rank == 3 ? one_wave(k_near<3, false>) : one_wave(k_near<2, false>);
+    a.near_stride = 0;
+    if (items >= (int64_t)8 * grid * 8) {
+        int64_t sd = std::max<int64_t>(1, (int64_t)(0.6180339887 * (double)items)) | 1;
+        auto gcd = [](int64_t u, int64_t v) { while (v) { const int64_t r = u % v; u = v; v = r; } return u; };
+        while (gcd(sd, items) != 1) sd += 2;
+        a.near_stride = (int)(sd % items);
+    }
     auto run = [&](auto kern) { return launch_chained(kern, dim3(one_wave(kern)), dim3(256), 0, st, a); };
-    return a.rank == 3 ? run(k_near<3>) : run(k_near<2>);
+    if (a.near_stride) return a.rank == 3 ? run(k_near<3, true>) : run(k_near<2, true>);
+    return a.rank == 3 ? run(k_near<3, false>) : run(k_near<2, false>);
 }
 
 cudaError_t launch_local_expand(const LocalArgs& a, int mode, cudaStream_t st)

@@ -480,8 +480,8 @@ __device__ __forceinline__ bool is_b2(const RouteArgs& a, int x, int y, int z, i
 
 // The B2 sites from the signed set -- the listed B1 points with S != 0 and the
 // queries (S != 0 off B1): GetBoundary(S) compares S across a pair, so every
-// B2 site is a signed point or an axis neighbour of one. One thread per
-// signed point p tests p and its axis neighbours with S = 0; such a
+// B2 site is a signed point or an axis neighbour of one. Each signed point p
+// has a thread for itself and one for each axis neighbour with S = 0; such a
 // neighbour is tested only by its signed neighbour of smallest linear index,
 // so no site is listed twice. The sites go to the site list (warp-aggregated
 // appends into a per-CTA buffer, one global atomic per CTA); fmin of every
@@ -518,36 +518,39 @@ __device__ __forceinline__ void k_b2sparse_body(const RouteArgs& a, const int bx
     const int plane = a.ny * a.nx;
     uint2* glist = reinterpret_cast<uint2*>(a.b2list);
     const int items = ns + nq;
-    for (int base = bx * blockDim.x; base < items; base += gx * blockDim.x) {
-        const int item = base + threadIdx.x;
-        uint2 found[1 + 2 * RANK];
+    // eight threads per signed point, one per candidate: c = 0 the point
+    // itself, c = 1 .. 6 its axis neighbours z-, z+, y-, y+, x-, x+ (c = 7
+    // idle), so that the chains of dependent loads run side by side
+    const int64_t slots = (int64_t)items * 8;
+    for (int64_t base = (int64_t)bx * blockDim.x; base < slots; base += (int64_t)gx * blockDim.x) {
+        const int64_t slot = base + threadIdx.x;
+        const int item = (int)(slot >> 3), c = (int)(slot & 7);
+        uint2 found[1];
         int nfound = 0;
-        if (item < items) {
+        const bool live = slot < slots && c <= 6 && !(RANK == 2 && (c == 1 || c == 2));
+        if (live) {
             const int p = item < ns ? a.slist[item] : a.qlist[item - ns].idx;
             const int z = p / plane, rem = p - z * plane;
             const int y = rem / a.nx, x = rem - y * a.nx;
-            // candidate c: 0 = p, then the axis neighbours z-, z+, y-, y+, x-, x+
-#pragma unroll
-            for (int c = 0; c <= 6; ++c) {
-                int cz = 0, cy = 0, cx = 0;
+            int cz = 0, cy = 0, cx = 0;
+            if (c > 0) {
+                const int axis = (c - 1) >> 1;
+                const int sg = (c - 1) & 1 ? 1 : -1;
+                (axis == 0 ? cz : (axis == 1 ? cy : cx)) = sg;
+            }
+            const int bx_ = x + cx, by = y + cy, bz = z + cz;
+            const bool inner = (unsigned)(bx_ - 1) < (unsigned)(a.nx - 2) &&
+                               (unsigned)(by - 1) < (unsigned)(a.ny - 2) &&
+                               (RANK == 2 || (unsigned)(bz - 1) < (unsigned)(a.nz - 2));
+            if (inner) {
+                const int sc = s_at(a, bx_, by, bz);
+                bool test = true;
                 if (c > 0) {
-                    const int axis = (c - 1) >> 1;
-                    if (RANK == 2 && axis == 0) continue;
-                    const int sg = (c - 1) & 1 ? 1 : -1;
-                    (axis == 0 ? cz : (axis == 1 ? cy : cx)) = sg;
-                }
-                const int bx = x + cx, by = y + cy, bz = z + cz;
-                const bool inner = (unsigned)(bx - 1) < (unsigned)(a.nx - 2) &&
-                                   (unsigned)(by - 1) < (unsigned)(a.ny - 2) &&
-                                   (RANK == 2 || (unsigned)(bz - 1) < (unsigned)(a.nz - 2));
-                if (!inner) continue;
-                const int sc = s_at(a, bx, by, bz);
-                if (c > 0) {
-                    if (sc != 0) continue;  // a signed point lists itself
-                    // owned by p when no signed neighbour of the candidate
-                    // precedes p: an offset (from p) precedes 0 in (dz, dy,
-                    // dx) order exactly when its point precedes p
-                    bool own = true;
+                    // a signed point lists itself; an S = 0 neighbour is
+                    // owned by p when no signed neighbour of it precedes p:
+                    // an offset (from p) precedes 0 in (dz, dy, dx) order
+                    // exactly when its point precedes p
+                    test = sc == 0;
 #pragma unroll
                     for (int k = 0; k < 6; ++k) {
                         const int axis = k >> 1;
@@ -556,12 +559,11 @@ __device__ __forceinline__ void k_b2sparse_body(const RouteArgs& a, const int bx
                         const int oz = cz + (axis == 0 ? sg : 0), oy = cy + (axis == 1 ? sg : 0),
                                   ox = cx + (axis == 2 ? sg : 0);
                         const bool before = oz < 0 || (oz == 0 && (oy < 0 || (oy == 0 && ox < 0)));
-                        if (before && s_at(a, x + ox, y + oy, z + oz) != 0) own = false;
+                        if (test && before && s_at(a, x + ox, y + oy, z + oz) != 0) test = false;
                     }
-                    if (!own) continue;
                 }
-                if (is_b2<RANK>(a, bx, by, bz, sc))
-                    found[nfound++] = make_uint2((uint32_t)bx | ((uint32_t)by << 16), (uint32_t)bz);
+                if (test && is_b2<RANK>(a, bx_, by, bz, sc))
+                    found[nfound++] = make_uint2((uint32_t)bx_ | ((uint32_t)by << 16), (uint32_t)bz);
             }
         }
         // warp-aggregated append of the found sites

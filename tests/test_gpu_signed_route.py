@@ -69,6 +69,25 @@ def test_routes_match_the_dense_evaluation(route, first_edt, name, shape, rel_eb
                 assert counts["list_searched"] == want
 
 
+@pytest.mark.parametrize("rel_eb", [1e-3, 1e-2])
+def test_near_items_from_the_counter_match_the_dense_evaluation(rel_eb):
+    """640 x 256 x 64: 40 960 items of four rows for the bounded nearest-site
+    search, more than eight per warp of a resident grid on a 152-SM GB300, so
+    the warps take their items from the route counter in the strided order
+    (the fixed split runs below that). The plain call must give the bits of
+    the debug call's dense evaluation."""
+    shape = (640, 256, 64)
+    x = synth.grf(shape, slope=11.0 / 3.0, seed=77, device="cuda")
+    eb = rel_eb * synth.value_range(x)
+    q = synth.quantize(x, eb).contiguous()
+    plain, full, maps, counts = _plain_and_debug(q, eb, "auto")
+    assert torch.equal(plain, full), f"{(plain != full).sum().item()} points differ"
+    if rel_eb == 1e-3:
+        assert not counts["separable_first_edt"]  # the search's own output stands
+    if not counts["dense"]:
+        assert counts["queries"] == int(((maps["s"] != 0) & (maps["dist1"] > 0)).sum().item())
+
+
 @pytest.mark.parametrize("route", ["auto", "brute"])
 @pytest.mark.parametrize("shape", [(17, 33), (64, 100), (180, 360), (3, 4, 5), (7, 9, 33), (16, 16, 16),
                                    (33, 17, 65), (20, 70, 31), (9, 130, 47)], ids=str)
